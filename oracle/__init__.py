@@ -1,0 +1,159 @@
+"""CPU oracle for Hartree-Fock exchange construction (plain FP64 C via ctypes).
+
+TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the benchmark's
+CPU-baseline leg are the only callers.  The product library never imports,
+links or runs anything here, and this package imports nothing from the
+product.  ``build()`` compiles ``hfx_oracle.c`` with gcc into
+``liboracle.so`` next to it.
+
+Functions (each cites the passage it follows):
+  boys            -- Boys function F_m(x) (auxiliary of the analytic ERIs)
+  normalize       -- axial normalisation of contracted Cartesian shells
+  quartets        -- contracted shell-quartet ERIs, Sec. 2 (full-range ERI
+                     definition; Eq. ERI-SR for erfc; erf for the complement)
+  schwarz         -- Q_IJ = sqrt(max |(ij|ij)|), Sec. 2 Eq. schwarz
+  build_K         -- K_ij = sum_kl (ik|jl) P_kl, Eq. H-HFX (without the -1/2),
+                     Schwarz and density screening (Eq. dmscreening), either by
+                     the 8-fold permutation symmetry or by brute force
+  exchange_energy -- E_x = -1/2 sum_ij P_ij K_ij
+
+Parity status: every function is pinned by tests in ``tests/test_oracle_*.py``
+(closed forms, special functions from scipy/mpmath, brute-force numerical
+quadrature of the six-dimensional integral, symmetry and invariance
+identities); none is "parity unpinned".
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hfx_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+KERNEL_COULOMB, KERNEL_ERFC, KERNEL_ERF = 0, 1, 2
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, OpenMP).  Returns the library path."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-D_GNU_SOURCE",
+               _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        D = ctypes.c_double
+        I = ctypes.c_int
+        P = ctypes.c_void_p
+        lib.oracle_boys.argtypes = [I, D, P]
+        lib.oracle_normalize.argtypes = [I, P, P, P, P, P]
+        lib.oracle_quartets.argtypes = [I, P, P, P, P, P, P, I, P, I, D, P, P]
+        lib.oracle_schwarz.argtypes = [I, P, P, P, P, P, P, I, D, P]
+        lib.oracle_build_K.argtypes = [I, P, P, P, P, P, P, P, I, D, I, D, I, D, I, I, I, I, P]
+        lib.oracle_build_K.restype = ctypes.c_longlong
+        lib.oracle_max_threads.restype = I
+        _lib = lib
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def max_threads() -> int:
+    return int(_load().oracle_max_threads())
+
+
+def boys(mmax: int, x: float) -> np.ndarray:
+    out = np.zeros(mmax + 1)
+    _load().oracle_boys(int(mmax), float(x), _p(out))
+    return out
+
+
+class Basis:
+    """Flat arrays of a ``synth.System`` as the oracle consumes them."""
+
+    def __init__(self, sysobj):
+        self.sys = sysobj
+        self.n_shells = sysobj.n_shells
+        self.xyz = np.ascontiguousarray(sysobj.atom_xyz[sysobj.shell_atom], dtype=np.float64)
+        self.l = np.ascontiguousarray(sysobj.shell_l, dtype=np.int32)
+        self.prim_off = np.ascontiguousarray(sysobj.prim_off, dtype=np.int32)
+        self.alpha = np.ascontiguousarray(sysobj.alpha, dtype=np.float64)
+        self.coef = normalize(sysobj)
+        self.func_off = np.ascontiguousarray(sysobj.func_off, dtype=np.int64)
+        self.nbf = int(self.func_off[-1])
+
+    def args(self):
+        return (self.n_shells, _p(self.xyz), _p(self.l), _p(self.prim_off), _p(self.alpha),
+                _p(self.coef), _p(self.func_off))
+
+
+def normalize(sysobj) -> np.ndarray:
+    out = np.zeros_like(sysobj.coef, dtype=np.float64)
+    raw = np.ascontiguousarray(sysobj.coef, dtype=np.float64)
+    l = np.ascontiguousarray(sysobj.shell_l, dtype=np.int32)
+    off = np.ascontiguousarray(sysobj.prim_off, dtype=np.int32)
+    al = np.ascontiguousarray(sysobj.alpha, dtype=np.float64)
+    _load().oracle_normalize(int(sysobj.n_shells), _p(l), _p(off), _p(al), _p(raw), _p(out))
+    return out
+
+
+def _basis(b):
+    return b if isinstance(b, Basis) else Basis(b)
+
+
+def quartets(basis, quads, kernel: int = KERNEL_COULOMB, omega: float = 0.11):
+    """Contracted integrals of shell quartets (I J | K L); returns a list of
+    arrays shaped (nI, nJ, nK, nL), Cartesian components in x,y,z /
+    xx,xy,xz,yy,yz,zz order."""
+    b = _basis(basis)
+    q = np.ascontiguousarray(np.asarray(quads, dtype=np.int32).reshape(-1, 4))
+    nf = np.diff(b.func_off)
+    sizes = np.prod(nf[q], axis=1).astype(np.int64)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    out = np.zeros(int(off[-1]))
+    _load().oracle_quartets(*b.args(), int(q.shape[0]), _p(q), int(kernel), float(omega),
+                            _p(off), _p(out))
+    return [out[off[i]:off[i + 1]].reshape(tuple(int(x) for x in nf[q[i]])) for i in range(q.shape[0])]
+
+
+def schwarz(basis, kernel: int = KERNEL_COULOMB, omega: float = 0.11) -> np.ndarray:
+    b = _basis(basis)
+    Q = np.zeros((b.n_shells, b.n_shells))
+    _load().oracle_schwarz(*b.args(), int(kernel), float(omega), _p(Q))
+    return Q
+
+
+def build_K(basis, P, kernel: int = KERNEL_COULOMB, omega: float = 0.11, screen: bool = False,
+            tau: float = 1e-8, density_screen: bool = False, eps: float = 1e-8,
+            brute: bool = False, bra_stride: int = 1, bra_offset: int = 0,
+            nthreads: int | None = None):
+    """K_ij = sum_kl (ik|jl) P_kl (dense FP64) and the number of surviving
+    shell quartets (canonical, or ordered when ``brute``)."""
+    b = _basis(basis)
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    assert P.shape == (b.nbf, b.nbf)
+    K = np.zeros_like(P)
+    nt = max_threads() if nthreads is None else int(nthreads)
+    n = _load().oracle_build_K(*b.args(), _p(P), int(kernel), float(omega), int(bool(screen)),
+                               float(tau), int(bool(density_screen)), float(eps), int(bool(brute)),
+                               int(bra_stride), int(bra_offset), nt, _p(K))
+    return K, int(n)
+
+
+def exchange_energy(P, K) -> float:
+    """E_x = -1/2 sum_ij P_ij K_ij."""
+    return float(-0.5 * np.sum(np.asarray(P) * np.asarray(K)))

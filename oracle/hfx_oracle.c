@@ -1,0 +1,479 @@
+/*
+ * hfx_oracle.c -- plain FP64 CPU oracle for Hartree-Fock exchange construction.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load this library.  It shares no code,
+ * header, table or constant with the CUDA library.
+ *
+ * What it computes (paper Sec. 2):
+ *   - contracted Cartesian Gaussian shells, axial normalisation;
+ *   - electron repulsion integrals (ERIs) with the full Coulomb kernel 1/r
+ *     (Sec. 2, full-range ERI definition) and the screened kernels
+ *     erf(w r)/r and erfc(w r)/r (Sec. 2, Eq. ERI-SR, w = 0.11 bohr^-1);
+ *   - Schwarz bounds Q_IJ = sqrt(max |(ij|ij)|)  (Sec. 2, Eq. schwarz);
+ *   - density screening  P_scr * Q_IJ * Q_KL <= eps  (Sec. 2, Eq. dmscreening);
+ *   - the exchange matrix K_ij = sum_kl (ik|jl) P_kl (Eq. H-HFX without -1/2),
+ *     either from canonical shell quartets and the 8-fold permutation symmetry
+ *     (Sec. 2) or by brute force over all ordered shell quartets.
+ *
+ * The ERI method is the McMurchie-Davidson Hermite scheme (Hermite expansion
+ * coefficients E_t^{ij} and Hermite Coulomb integrals R_{tuv}); the Boys
+ * function is a long-double power series (argument < 35) or erf plus upward
+ * recursion (argument >= 35), then downward recursion.  This is a different
+ * route from the GPU path on purpose.
+ *
+ * Attenuated kernels: the erf(w r)/r integral equals the Coulomb one with the
+ * Hermite exponent alpha replaced by alpha' = alpha w^2/(alpha + w^2) and an
+ * overall factor sqrt(alpha'/alpha); erfc = Coulomb - erf, applied at the base
+ * R^n_{000} values (the Hermite recursion is linear in them).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define LMAX 2             /* s, p, d */
+#define LTOT (4 * LMAX)    /* highest total angular momentum of a quartet */
+#define MAXC 6             /* Cartesian components of a d shell */
+
+static const long double PI_L = 3.141592653589793238462643383279502884L;
+
+static int ncart(int l) { return (l + 1) * (l + 2) / 2; }
+
+/* Cartesian exponents of component k of a shell of angular momentum l,
+ * lexicographic order: x, y, z; xx, xy, xz, yy, yz, zz. */
+static void cart(int l, int k, int e[3]) {
+  int idx = 0;
+  for (int lx = l; lx >= 0; --lx)
+    for (int ly = l - lx; ly >= 0; --ly) {
+      if (idx == k) { e[0] = lx; e[1] = ly; e[2] = l - lx - ly; return; }
+      ++idx;
+    }
+}
+
+static double dfact(int n) { /* n!! for n >= -1 */
+  double r = 1.0;
+  for (int k = n; k > 1; k -= 2) r *= k;
+  return r;
+}
+
+/* ---------------------------------------------------------------- Boys */
+/* F_m(x) = int_0^1 t^{2m} exp(-x t^2) dt, m = 0..mmax.
+ * x < 35: F_mmax from the series e^{-x} sum_k (2x)^k / ((2m+1)(2m+3)...(2m+2k+1)),
+ *         all terms positive, evaluated in long double; then downward
+ *         F_m = (2x F_{m+1} + e^{-x}) / (2m+1).
+ * x >= 35: F_0 = sqrt(pi/x) erf(sqrt x) / 2, upward F_{m+1} = ((2m+1) F_m - e^{-x}) / (2x). */
+void oracle_boys(int mmax, double xd, double *F) {
+  long double x = xd;
+  if (x < 35.0L) {
+    long double term = 1.0L / (2 * mmax + 1), sum = term;
+    for (int k = 1; k < 2000; ++k) {
+      term *= 2.0L * x / (2 * mmax + 2 * k + 1);
+      sum += term;
+      if (term < 1e-22L * sum) break;
+    }
+    long double ex = expl(-x);
+    long double f = ex * sum;
+    F[mmax] = (double)f;
+    for (int m = mmax - 1; m >= 0; --m) {
+      f = (2.0L * x * f + ex) / (2 * m + 1);
+      F[m] = (double)f;
+    }
+  } else {
+    long double ex = expl(-x);
+    long double f = 0.5L * sqrtl(PI_L / x) * erfl(sqrtl(x));
+    F[0] = (double)f;
+    for (int m = 0; m < mmax; ++m) {
+      f = ((2 * m + 1) * f - ex) / (2.0L * x);
+      F[m + 1] = (double)f;
+    }
+  }
+}
+
+/* ------------------------------------------------------- normalisation */
+/* Axial primitive normalisation N(a) = (2a/pi)^{3/4} (4a)^{l/2} / sqrt((2l-1)!!),
+ * then the contracted axial component x^l is scaled to unit self-overlap. */
+void oracle_normalize(int n_shells, const int *l, const int *prim_off, const double *alpha,
+                      const double *coef_raw, double *coef_out) {
+  for (int s = 0; s < n_shells; ++s) {
+    int L = l[s], p0 = prim_off[s], p1 = prim_off[s + 1];
+    double df = dfact(2 * L - 1);
+    for (int k = p0; k < p1; ++k) {
+      double a = alpha[k];
+      coef_out[k] = coef_raw[k] * pow(2.0 * a / M_PI, 0.75) * pow(4.0 * a, 0.5 * L) / sqrt(df);
+    }
+    double S = 0.0;
+    for (int k = p0; k < p1; ++k)
+      for (int m = p0; m < p1; ++m) {
+        double g = alpha[k] + alpha[m];
+        S += coef_out[k] * coef_out[m] * df / pow(2.0 * g, L) * pow(M_PI / g, 1.5);
+      }
+    double sc = 1.0 / sqrt(S);
+    for (int k = p0; k < p1; ++k) coef_out[k] *= sc;
+  }
+}
+
+/* ------------------------------------------ Hermite expansion coefficients */
+/* E[i][j][t] for one Cartesian axis, i <= la, j <= lb, t <= i + j, for the
+ * Gaussian product of exponents a (centre A) and b (centre B):
+ *   E^{00}_0 = exp(-ab/(a+b) X_AB^2)
+ *   E^{i+1,j}_t = E^{ij}_{t-1}/(2p) + X_PA E^{ij}_t + (t+1) E^{ij}_{t+1}
+ *   E^{i,j+1}_t = E^{ij}_{t-1}/(2p) + X_PB E^{ij}_t + (t+1) E^{ij}_{t+1}   */
+typedef double ecoef_t[LMAX + 1][LMAX + 1][2 * LMAX + 2];
+
+static void hermite_E(int la, int lb, double a, double b, double Ax, double Bx, ecoef_t E) {
+  double p = a + b, Px = (a * Ax + b * Bx) / p, XPA = Px - Ax, XPB = Px - Bx, XAB = Ax - Bx;
+  memset(E, 0, sizeof(ecoef_t));
+  E[0][0][0] = exp(-a * b / p * XAB * XAB);
+  for (int i = 0; i <= la; ++i)
+    for (int j = 0; j <= lb; ++j) {
+      if (i == 0 && j == 0) continue;
+      for (int t = 0; t <= i + j; ++t) {
+        double v = 0.0;
+        if (i > 0) {
+          if (t > 0) v += E[i - 1][j][t - 1] / (2.0 * p);
+          if (t <= i - 1 + j) v += XPA * E[i - 1][j][t];
+          if (t + 1 <= i - 1 + j) v += (t + 1) * E[i - 1][j][t + 1];
+        } else {
+          if (t > 0) v += E[i][j - 1][t - 1] / (2.0 * p);
+          if (t <= i + j - 1) v += XPB * E[i][j - 1][t];
+          if (t + 1 <= i + j - 1) v += (t + 1) * E[i][j - 1][t + 1];
+        }
+        E[i][j][t] = v;
+      }
+    }
+}
+
+/* ----------------------------------------------- Hermite Coulomb integrals */
+/* R[t][u][v] = R^0_{tuv}, t+u+v <= Ltot, from the base values R^n_{000}:
+ *   R^n_{t+1,u,v} = t R^{n+1}_{t-1,u,v} + X_PQ R^{n+1}_{t,u,v}  (same for u, v). */
+typedef double rtab_t[LTOT + 1][LTOT + 1][LTOT + 1];
+
+static void hermite_R(int Ltot, const double *base, double X, double Y, double Z, rtab_t R) {
+  static __thread double Rn[LTOT + 1][LTOT + 1][LTOT + 1][LTOT + 1];
+  for (int n = 0; n <= Ltot; ++n) Rn[n][0][0][0] = base[n];
+  for (int N = 1; N <= Ltot; ++N)
+    for (int n = 0; n <= Ltot - N; ++n)
+      for (int t = N; t >= 0; --t)
+        for (int u = N - t; u >= 0; --u) {
+          int v = N - t - u;
+          double r;
+          if (t > 0)
+            r = (t > 1 ? (t - 1) * Rn[n + 1][t - 2][u][v] : 0.0) + X * Rn[n + 1][t - 1][u][v];
+          else if (u > 0)
+            r = (u > 1 ? (u - 1) * Rn[n + 1][t][u - 2][v] : 0.0) + Y * Rn[n + 1][t][u - 1][v];
+          else
+            r = (v > 1 ? (v - 1) * Rn[n + 1][t][u][v - 2] : 0.0) + Z * Rn[n + 1][t][u][v - 1];
+          Rn[n][t][u][v] = r;
+        }
+  for (int t = 0; t <= Ltot; ++t)
+    for (int u = 0; u <= Ltot - t; ++u)
+      for (int v = 0; v <= Ltot - t - u; ++v) R[t][u][v] = Rn[0][t][u][v];
+}
+
+/* ----------------------------------------------------------- the basis */
+typedef struct {
+  int n_shells;
+  const double *xyz;    /* n_shells x 3 shell centres */
+  const int *l;         /* n_shells */
+  const int *prim_off;  /* n_shells + 1 */
+  const double *alpha;  /* exponents */
+  const double *coef;   /* normalised contraction coefficients */
+  const long long *func_off; /* n_shells + 1 */
+  int nbf;
+} basis_t;
+
+enum { KERNEL_COULOMB = 0, KERNEL_ERFC = 1, KERNEL_ERF = 2 };
+
+/* Base values R^n_{000}, n = 0..Ltot, for Hermite exponent alpha, squared
+ * distance R2, for the selected kernel. */
+static void base_values(int Ltot, int kernel, double omega, double alpha, double R2, double *base) {
+  double F[LTOT + 1], Fw[LTOT + 1];
+  double full[LTOT + 1], att[LTOT + 1];
+  if (kernel != KERNEL_ERF) {
+    oracle_boys(Ltot, alpha * R2, F);
+    double m2a = 1.0;
+    for (int n = 0; n <= Ltot; ++n) { full[n] = m2a * F[n]; m2a *= -2.0 * alpha; }
+  }
+  if (kernel != KERNEL_COULOMB) {
+    double w2 = omega * omega, ap = alpha * w2 / (alpha + w2), sc = sqrt(ap / alpha);
+    oracle_boys(Ltot, ap * R2, Fw);
+    double m2a = 1.0;
+    for (int n = 0; n <= Ltot; ++n) { att[n] = sc * m2a * Fw[n]; m2a *= -2.0 * ap; }
+  }
+  for (int n = 0; n <= Ltot; ++n) {
+    if (kernel == KERNEL_COULOMB) base[n] = full[n];
+    else if (kernel == KERNEL_ERF) base[n] = att[n];
+    else base[n] = full[n] - att[n];
+  }
+}
+
+/* Contracted shell-quartet integrals (IJ|KL), out[((a*nJ + b)*nK + c)*nL + d]. */
+static void shell_quartet(const basis_t *B, int I, int J, int K, int L, int kernel, double omega,
+                          double *out) {
+  const int sh[4] = {I, J, K, L};
+  int l[4], n[4], comp[4][MAXC][3];
+  for (int s = 0; s < 4; ++s) {
+    l[s] = B->l[sh[s]];
+    n[s] = ncart(l[s]);
+    for (int k = 0; k < n[s]; ++k) cart(l[s], k, comp[s][k]);
+  }
+  const double *A = B->xyz + 3 * I, *Bc = B->xyz + 3 * J, *C = B->xyz + 3 * K, *D = B->xyz + 3 * L;
+  int Lab = l[0] + l[1], Lcd = l[2] + l[3], Ltot = Lab + Lcd;
+  int ntot = n[0] * n[1] * n[2] * n[3];
+  memset(out, 0, sizeof(double) * ntot);
+
+  ecoef_t Eab[3], Ecd[3];
+  rtab_t R;
+  double base[LTOT + 1];
+  /* W[c][d][t][u][v]: ket-side contraction with R for fixed ket components */
+  static __thread double W[MAXC][MAXC][2 * LMAX + 1][2 * LMAX + 1][2 * LMAX + 1];
+
+  for (int ia = B->prim_off[I]; ia < B->prim_off[I + 1]; ++ia)
+    for (int ib = B->prim_off[J]; ib < B->prim_off[J + 1]; ++ib) {
+      double a = B->alpha[ia], b = B->alpha[ib], p = a + b;
+      double cab = B->coef[ia] * B->coef[ib];
+      double P[3];
+      for (int x = 0; x < 3; ++x) {
+        P[x] = (a * A[x] + b * Bc[x]) / p;
+        hermite_E(l[0], l[1], a, b, A[x], Bc[x], Eab[x]);
+      }
+      for (int ic = B->prim_off[K]; ic < B->prim_off[K + 1]; ++ic)
+        for (int id = B->prim_off[L]; id < B->prim_off[L + 1]; ++id) {
+          double c = B->alpha[ic], d = B->alpha[id], q = c + d;
+          double ccd = B->coef[ic] * B->coef[id];
+          double Q[3];
+          for (int x = 0; x < 3; ++x) {
+            Q[x] = (c * C[x] + d * D[x]) / q;
+            hermite_E(l[2], l[3], c, d, C[x], D[x], Ecd[x]);
+          }
+          double alpha = p * q / (p + q);
+          double X = P[0] - Q[0], Y = P[1] - Q[1], Z = P[2] - Q[2];
+          base_values(Ltot, kernel, omega, alpha, X * X + Y * Y + Z * Z, base);
+          hermite_R(Ltot, base, X, Y, Z, R);
+          double pref = 2.0 * pow(M_PI, 2.5) / (p * q * sqrt(p + q)) * cab * ccd;
+
+          for (int kc = 0; kc < n[2]; ++kc)
+            for (int kd = 0; kd < n[3]; ++kd) {
+              const int *ec = comp[2][kc], *ed = comp[3][kd];
+              int tx = ec[0] + ed[0], ty = ec[1] + ed[1], tz = ec[2] + ed[2];
+              for (int t = 0; t <= Lab; ++t)
+                for (int u = 0; u <= Lab - t; ++u)
+                  for (int v = 0; v <= Lab - t - u; ++v) {
+                    double s = 0.0;
+                    for (int tau = 0; tau <= tx; ++tau)
+                      for (int nu = 0; nu <= ty; ++nu)
+                        for (int phi = 0; phi <= tz; ++phi) {
+                          double e = Ecd[0][ec[0]][ed[0]][tau] * Ecd[1][ec[1]][ed[1]][nu] *
+                                     Ecd[2][ec[2]][ed[2]][phi];
+                          double sgn = ((tau + nu + phi) & 1) ? -1.0 : 1.0;
+                          s += sgn * e * R[t + tau][u + nu][v + phi];
+                        }
+                    W[kc][kd][t][u][v] = s;
+                  }
+            }
+          for (int ka = 0; ka < n[0]; ++ka)
+            for (int kb = 0; kb < n[1]; ++kb) {
+              const int *ea = comp[0][ka], *eb = comp[1][kb];
+              for (int kc = 0; kc < n[2]; ++kc)
+                for (int kd = 0; kd < n[3]; ++kd) {
+                  double s = 0.0;
+                  for (int t = 0; t <= ea[0] + eb[0]; ++t)
+                    for (int u = 0; u <= ea[1] + eb[1]; ++u)
+                      for (int v = 0; v <= ea[2] + eb[2]; ++v)
+                        s += Eab[0][ea[0]][eb[0]][t] * Eab[1][ea[1]][eb[1]][u] *
+                             Eab[2][ea[2]][eb[2]][v] * W[kc][kd][t][u][v];
+                  out[((ka * n[1] + kb) * n[2] + kc) * n[3] + kd] += pref * s;
+                }
+            }
+        }
+    }
+}
+
+static void fill_basis(basis_t *B, int n_shells, const double *xyz, const int *l, const int *prim_off,
+                       const double *alpha, const double *coef, const long long *func_off) {
+  B->n_shells = n_shells; B->xyz = xyz; B->l = l; B->prim_off = prim_off;
+  B->alpha = alpha; B->coef = coef; B->func_off = func_off;
+  B->nbf = (int)func_off[n_shells];
+}
+
+/* Integrals of a list of shell quartets; quartet q's block starts at out_off[q]. */
+void oracle_quartets(int n_shells, const double *xyz, const int *l, const int *prim_off,
+                     const double *alpha, const double *coef, const long long *func_off,
+                     int n_q, const int *quartets /* n_q x 4 */, int kernel, double omega,
+                     const long long *out_off, double *out) {
+  basis_t B;
+  fill_basis(&B, n_shells, xyz, l, prim_off, alpha, coef, func_off);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int q = 0; q < n_q; ++q) {
+    const int *s = quartets + 4 * q;
+    shell_quartet(&B, s[0], s[1], s[2], s[3], kernel, omega, out + out_off[q]);
+  }
+}
+
+/* Schwarz bounds Q[I*ns + J] = sqrt(max_{i in I, j in J} |(ij|ij)|), run's kernel. */
+void oracle_schwarz(int n_shells, const double *xyz, const int *l, const int *prim_off,
+                    const double *alpha, const double *coef, const long long *func_off, int kernel,
+                    double omega, double *Q) {
+  basis_t B;
+  fill_basis(&B, n_shells, xyz, l, prim_off, alpha, coef, func_off);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int I = 0; I < n_shells; ++I) {
+    double buf[MAXC * MAXC * MAXC * MAXC];
+    for (int J = 0; J <= I; ++J) {
+      shell_quartet(&B, I, J, I, J, kernel, omega, buf);
+      int nI = ncart(l[I]), nJ = ncart(l[J]);
+      double mx = 0.0;
+      for (int a = 0; a < nI; ++a)
+        for (int b = 0; b < nJ; ++b) {
+          double v = fabs(buf[((a * nJ + b) * nI + a) * nJ + b]);
+          if (v > mx) mx = v;
+        }
+      Q[I * n_shells + J] = Q[J * n_shells + I] = sqrt(mx);
+    }
+  }
+}
+
+/* Pmax[I*ns + J] = max_{i in I, j in J} |P_ij|  (Sec. 2, density screening). */
+static void shell_pmax(const basis_t *B, const double *P, double *Pm) {
+  int ns = B->n_shells, nbf = B->nbf;
+  for (int I = 0; I < ns; ++I)
+    for (int J = 0; J < ns; ++J) {
+      double mx = 0.0;
+      for (long long i = B->func_off[I]; i < B->func_off[I + 1]; ++i)
+        for (long long j = B->func_off[J]; j < B->func_off[J + 1]; ++j) {
+          double v = fabs(P[i * nbf + j]);
+          if (v > mx) mx = v;
+        }
+      Pm[I * ns + J] = mx;
+    }
+}
+
+/* Survival of shell quartet (A B | C D) (bra A,B; ket C,D).
+ * screen = 0: everything survives.  screen = 1: Q_AB Q_CD > tau, and
+ * P_scr = max(Pmax_AC, Pmax_AD, Pmax_BC, Pmax_BD) > 0, and, if dscreen,
+ * P_scr Q_AB Q_CD > eps. */
+static int survives(int ns, const double *Q, const double *Pm, int screen, double tau, int dscreen,
+                    double eps, int A, int Bs, int C, int D) {
+  if (!screen) return 1;
+  double qq = Q[A * ns + Bs] * Q[C * ns + D];
+  if (!(qq > tau)) return 0;
+  double ps = Pm[A * ns + C];
+  if (Pm[A * ns + D] > ps) ps = Pm[A * ns + D];
+  if (Pm[Bs * ns + C] > ps) ps = Pm[Bs * ns + C];
+  if (Pm[Bs * ns + D] > ps) ps = Pm[Bs * ns + D];
+  if (!(ps > 0.0)) return 0;
+  if (dscreen && !(ps * qq > eps)) return 0;
+  return 1;
+}
+
+/* K_ij = sum_kl (ik|jl) P_kl over surviving quartets (dense nbf x nbf, FP64).
+ * brute = 1: loop over all ordered shell quartets (I K | J L) and add
+ *            (ik|jl) P_kl to K_ij directly (the definition, Eq. H-HFX).
+ * brute = 0: loop over canonical quartets (I>=J, K>=L, IJ>=KL) and apply the
+ *            8 index permutations of Sec. 2 with degeneracy weights.
+ * bra_stride/bra_offset: only canonical bra pairs with index % stride == offset
+ *            (a bounded sample for timing; stride 1 = everything).
+ * Returns the number of surviving (canonical or ordered) shell quartets. */
+long long oracle_build_K(int n_shells, const double *xyz, const int *l, const int *prim_off,
+                         const double *alpha, const double *coef, const long long *func_off,
+                         const double *P, int kernel, double omega, int screen, double tau,
+                         int dscreen, double eps, int brute, int bra_stride, int bra_offset,
+                         int nthreads, double *K) {
+  basis_t B;
+  fill_basis(&B, n_shells, xyz, l, prim_off, alpha, coef, func_off);
+  int ns = n_shells, nbf = B.nbf;
+  double *Q = (double *)calloc((size_t)ns * ns, sizeof(double));
+  double *Pm = (double *)calloc((size_t)ns * ns, sizeof(double));
+  if (screen) oracle_schwarz(ns, xyz, l, prim_off, alpha, coef, func_off, kernel, omega, Q);
+  shell_pmax(&B, P, Pm);
+  memset(K, 0, sizeof(double) * (size_t)nbf * nbf);
+  long long count = 0;
+  if (nthreads <= 0) nthreads = 1;
+  if (bra_stride <= 0) bra_stride = 1;
+  long long npair = (long long)ns * (ns + 1) / 2;
+
+#pragma omp parallel num_threads(nthreads) reduction(+ : count)
+  {
+    double *Kt = (double *)calloc((size_t)nbf * nbf, sizeof(double));
+    double g[MAXC * MAXC * MAXC * MAXC];
+    if (brute) {
+#pragma omp for schedule(dynamic, 1) collapse(2)
+      for (int I = 0; I < ns; ++I)
+        for (int Ks = 0; Ks < ns; ++Ks)
+          for (int J = 0; J < ns; ++J)
+            for (int Ls = 0; Ls < ns; ++Ls) {
+              if (!survives(ns, Q, Pm, screen, tau, dscreen, eps, I, Ks, J, Ls)) continue;
+              ++count;
+              shell_quartet(&B, I, Ks, J, Ls, kernel, omega, g);
+              int nI = ncart(l[I]), nK = ncart(l[Ks]), nJ = ncart(l[J]), nL = ncart(l[Ls]);
+              for (int a = 0; a < nI; ++a)
+                for (int k = 0; k < nK; ++k)
+                  for (int b = 0; b < nJ; ++b)
+                    for (int d = 0; d < nL; ++d) {
+                      long long i = func_off[I] + a, kk = func_off[Ks] + k;
+                      long long j = func_off[J] + b, ll = func_off[Ls] + d;
+                      Kt[i * nbf + j] += g[((a * nK + k) * nJ + b) * nL + d] * P[kk * nbf + ll];
+                    }
+            }
+    } else {
+#pragma omp for schedule(dynamic, 1)
+      for (long long ij = 0; ij < npair; ++ij) {
+        if (ij % bra_stride != bra_offset) continue;
+        int I = (int)floor((sqrt(8.0 * (double)ij + 1.0) - 1.0) / 2.0);
+        while ((long long)I * (I + 1) / 2 > ij) --I;
+        while ((long long)(I + 1) * (I + 2) / 2 <= ij) ++I;
+        int J = (int)(ij - (long long)I * (I + 1) / 2);
+        for (int Kq = 0; Kq <= I; ++Kq)
+          for (int Lq = 0; Lq <= Kq; ++Lq) {
+            long long kl = (long long)Kq * (Kq + 1) / 2 + Lq;
+            if (kl > ij) continue;
+            if (!survives(ns, Q, Pm, screen, tau, dscreen, eps, I, J, Kq, Lq)) continue;
+            ++count;
+            shell_quartet(&B, I, J, Kq, Lq, kernel, omega, g);
+            double fac = 1.0;
+            if (I == J) fac *= 0.5;
+            if (Kq == Lq) fac *= 0.5;
+            if (ij == kl) fac *= 0.5;
+            int nI = ncart(l[I]), nJ = ncart(l[J]), nK = ncart(l[Kq]), nL = ncart(l[Lq]);
+            for (int a = 0; a < nI; ++a)
+              for (int b = 0; b < nJ; ++b)
+                for (int c = 0; c < nK; ++c)
+                  for (int d = 0; d < nL; ++d) {
+                    double v = fac * g[((a * nJ + b) * nK + c) * nL + d];
+                    long long ia = func_off[I] + a, ib = func_off[J] + b;
+                    long long ic = func_off[Kq] + c, id = func_off[Lq] + d;
+                    /* (ab|cd) (ba|cd) (ab|dc) (ba|dc) (cd|ab) (dc|ab) (cd|ba) (dc|ba):
+                     * an integral (xy|zw) adds (xy|zw) P_yw to K_xz. */
+                    Kt[ia * nbf + ic] += v * P[ib * nbf + id];
+                    Kt[ib * nbf + ic] += v * P[ia * nbf + id];
+                    Kt[ia * nbf + id] += v * P[ib * nbf + ic];
+                    Kt[ib * nbf + id] += v * P[ia * nbf + ic];
+                    Kt[ic * nbf + ia] += v * P[id * nbf + ib];
+                    Kt[id * nbf + ia] += v * P[ic * nbf + ib];
+                    Kt[ic * nbf + ib] += v * P[id * nbf + ia];
+                    Kt[id * nbf + ib] += v * P[ic * nbf + ia];
+                  }
+          }
+      }
+    }
+#pragma omp critical
+    {
+      for (long long x = 0; x < (long long)nbf * nbf; ++x) K[x] += Kt[x];
+    }
+    free(Kt);
+  }
+  free(Q);
+  free(Pm);
+  return count;
+}
+
+int oracle_max_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
