@@ -1,0 +1,351 @@
+#!/usr/bin/env python
+"""Benchmark of one HFX build (the hot path): zero K, shell-pair Pmax, screened
+ERI evaluation with the fused exchange contraction into block-sparse K,
+symmetrisation and E_x, on resident quartet lists.
+
+Default workload: 400-atom C/H molecular cluster in a 30 bohr box
+(2s+2p+1d shells per atom, 4 primitives, 5600 Cartesian functions), HSE
+erfc(w r)/r with w = 0.11 bohr^-1, Schwarz threshold 1e-8 with density
+screening, P zeroed beyond 14 bohr, mixed precision (FP32 recursions, FP64
+Boys/prefactors/K/E_x).  Synthetic seeded inputs (no paper datasets).
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 80.5: 128 FP32 FMA/clk/SM at the 2070 MHz max clock
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12     # 1.26: 2 FP64 FMA/clk/SM (1/64 of FP32)
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except Exception:
+        return {}
+
+
+def fp64_prologue_flops(L, kernel):
+    """FP64 flops (FMA = 2) of the per-primitive-quartet prologue as written in
+    eri_kernels.cuh / eri_common.cuh: argument T, prefactor, Boys function(s)."""
+    boys = 17 + (16 + 3 * L if L > 0 else 0)
+    base = 31
+    if kernel == 0:
+        return base + boys + (L + 1)
+    return base + 2 * boys + 1 + 8 + 12 + 4 * (L + 1)
+
+
+def class_flops(ci, n_q, n_pq, kernel, fp32):
+    """(fp64 flops, fp32 flops) of one class launch with n_q quartets and n_pq
+    primitive quartets."""
+    L = ci.la + ci.lb + ci.lc + ci.ld
+    f64 = n_pq * fp64_prologue_flops(L, kernel)
+    rec = n_pq * (ci.vrr_flops + 9) + n_q * (ci.hrr_flops + 8 * ci.n_out)
+    if fp32:
+        return f64, rec
+    return f64 + rec, 0
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, idx=0):
+        self.idx, self.proc, self.lines = idx, None, []
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload(atoms):
+    s, P = synth.config2(atoms)
+    mask = synth.atom_pair_mask(s, 14.0)
+    return s, P, mask
+
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_2009_03555_gb300 import hfx
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dev = torch.device("cuda")
+    stream = torch.cuda.current_stream()
+    s, P, mask = workload(args.atoms)
+    prec = hfx.HFX_PREC_MIXED if args.precision == "mixed" else hfx.HFX_PREC_FP64
+    opts = hfx.make_opts(kernel=hfx.HFX_KERNEL_ERFC, omega=0.11, screen=True, tau=1e-8, density_screen=True,
+                         eps=1e-8, prim_cutoff=args.prim_cutoff, precision=prec,
+                         fp64_promote_bound=args.promote, n_block=args.n_block)
+    basis = hfx.Basis(s)
+    q = hfx.Quartets(basis, opts, mask)
+    Pd = torch.from_numpy(P).to(dev)
+    Pv = torch.empty(q.n_values, dtype=torch.float64, device=dev)
+    Kv = torch.empty(q.n_values, dtype=torch.float64, device=dev)
+    q.pack(Pd, Pv)
+    del Pd
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
+
+    def step():
+        q.build_K(Pv, Kv)
+        return q.exchange_energy(Pv, Kv)
+
+    for _ in range(args.warmup):
+        E = step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clk.start()
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        E = step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    st = q.stats()
+    ms = sum(times) / len(times)
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.barrier()
+        ms = float(t.item())
+
+    # end to end through the public API with host buffers: pinned P in, K and E_x out
+    e2e = None
+    if not args.no_e2e:
+        Ph = torch.empty(q.n_values, dtype=torch.float64, pin_memory=True)
+        Ph.copy_(Pv.cpu())
+        Kh = torch.empty(q.n_values, dtype=torch.float64, pin_memory=True)
+        te = []
+        for i in range(max(1, args.e2e_steps) + 1):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            Pv.copy_(Ph, non_blocking=True)
+            q.build_K(Pv, Kv)
+            q.exchange_energy(Pv, Kv)
+            Kh.copy_(Kv, non_blocking=True)
+            torch.cuda.synchronize()
+            if i > 0:
+                te.append(time.perf_counter() - t0)
+        e2e = {"value": world * 1.0 / (sum(te) / len(te)), "unit": "builds/s",
+               "h2d_bytes_per_step": int(q.n_values * 8), "d2h_bytes_per_step": int(q.n_values * 8 + 8)}
+
+    # roofline of the dominant kernel (largest device time in the last build)
+    best = None
+    for p in range(2):
+        for c in range(hfx.N_CLASSES):
+            t = st.ms_class_pass[p][c]
+            if st.n_quartets_pass[p][c] > 0 and (best is None or t > best[0]):
+                best = (t, p, c)
+    roof = None
+    if best:
+        t, p, c = best
+        ci = hfx.hfx_get_class_info(c)
+        fp32 = (prec == hfx.HFX_PREC_MIXED and p == 0)
+        f64, f32 = class_flops(ci, st.n_quartets_pass[p][c], st.n_prim_quartets_pass[p][c], 1, fp32)
+        a64 = f64 / (t * 1e-3) / 1e12
+        a32 = f32 / (t * 1e-3) / 1e12
+        u64, u32 = a64 / FP64_PEAK_TFLOPS, a32 / FP32_PEAK_TFLOPS
+        pipe = "fp64" if u64 >= u32 else "fp32"
+        roof = {"bound": "alu", "pipe": pipe,
+                "kernel": f"k_build_K<Cls{ci.la}{ci.lb}{ci.lc}{ci.ld},{'float' if fp32 else 'double'}>",
+                "achieved": round(a64 if pipe == "fp64" else a32, 4),
+                "peak": round(FP64_PEAK_TFLOPS if pipe == "fp64" else FP32_PEAK_TFLOPS, 3),
+                "unit": "TFLOP/s", "frac": round(max(u64, u32), 4),
+                "other_pipe_frac": round(min(u64, u32), 4),
+                "peak_source": "derived: 152 SMs x (128 FP32 | 2 FP64) FMA/clk x 2070 MHz",
+                "traffic": None, "launch_ms": round(t, 3), "share_of_build": round(t / st.ms_last_build, 4)}
+    n_q = int(sum(st.n_quartets_computed))
+    n_pq = int(sum(st.n_prim_quartets_pass[0]) + sum(st.n_prim_quartets_pass[1]))
+    res = {
+        "metric": "hfx_builds_per_s", "value": world * 1000.0 / ms, "unit": "builds/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if prec == hfx.HFX_PREC_MIXED else "f64",
+        "data": "synthetic",
+        "config": {"workload": f"{args.atoms}-atom C/H cluster, HSE erfc w=0.11, Schwarz 1e-8 + density screening, "
+                               f"P cut 14 bohr, {args.precision}",
+                   "atoms": args.atoms, "n_bf": int(s.n_bf), "precision": args.precision,
+                   "fp64_promote_bound": args.promote, "n_block": args.n_block, "prim_cutoff": args.prim_cutoff,
+                   "l2": "flushed (256 MB write) between timed steps", "parallelism": f"replicas x{world}"},
+        "quartets_per_build": n_q, "prim_quartets_per_build": n_pq,
+        "eri_quartets_per_s": world * n_q / (ms * 1e-3),
+        "E_x": E, "setup_ms": st.ms_setup,
+        "gpu_launches": args.steps * (3 + sum(1 for p in range(2) for c in range(hfx.N_CLASSES)
+                                            if st.n_quartets_pass[p][c] > 0 or st.ms_class_pass[p][c] > 0)),
+        "clocks": clocks, "e2e": e2e, "roofline": roof,
+    }
+    return res, s, q
+
+
+def run_cpu_oracle(args, sample_atoms=10, bra_stride=2, full_quartets=None):
+    """The oracle (as it stands) on a bounded sample: the `sample_atoms` atoms of
+    the workload nearest its centre, every `bra_stride`-th canonical bra pair.
+    Returns quartets/s and cores used."""
+    import oracle
+    s, P, mask = workload(args.atoms)
+    c = s.atom_xyz.mean(axis=0)
+    order = np.argsort(np.sum((s.atom_xyz - c) ** 2, axis=1))[:sample_atoms]
+    keep = np.sort(order)
+    shells = [S for a in keep for S in range(s.n_shells) if s.shell_atom[S] == a]
+    newpos = {int(a): i for i, a in enumerate(keep)}
+    alpha, coef, off = [], [], [0]
+    for S in shells:
+        p0, p1 = s.prim_off[S], s.prim_off[S + 1]
+        alpha.extend(s.alpha[p0:p1]); coef.extend(s.coef[p0:p1]); off.append(off[-1] + p1 - p0)
+    sub = synth.System(name="sample", atom_Z=s.atom_Z[keep], atom_xyz=s.atom_xyz[keep],
+                       shell_atom=np.array([newpos[int(s.shell_atom[S])] for S in shells], dtype=np.int32),
+                       shell_l=s.shell_l[shells], prim_off=np.array(off, dtype=np.int32),
+                       alpha=np.array(alpha), coef=np.array(coef))
+    fo = s.func_off
+    fidx = np.concatenate([np.arange(fo[S], fo[S + 1]) for S in shells])
+    Psub = np.ascontiguousarray(P[np.ix_(fidx, fidx)])
+    nt = oracle.max_threads()
+    b = oracle.Basis(sub)
+    t0 = time.perf_counter()
+    _, n = oracle.build_K(b, Psub, kernel=oracle.KERNEL_ERFC, omega=0.11, screen=True, tau=1e-8,
+                          density_screen=True, eps=1e-8, bra_stride=bra_stride, nthreads=nt)
+    dt = time.perf_counter() - t0
+    return n / dt, nt, dt, n
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the CPU oracle on the host cores, each step a bounded
+    sample; value in builds/s extrapolated from quartets/s."""
+    if rank != 0:
+        return None
+    qpb = args.ref_quartets_per_build
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        pass
+    vals = []
+    for _ in range(args.steps):
+        qps, nt, dt, n = run_cpu_oracle(args)
+        vals.append((qps, dt, n))
+    qps = sum(v[0] for v in vals) / len(vals)
+    value = qps / qpb
+    sample = (f"oracle on the 10 atoms nearest the centre of the {args.atoms}-atom cluster, every 2nd canonical "
+              f"bra pair ({vals[-1][2]} quartets, {vals[-1][1]:.1f} s per step); builds/s = quartets/s / "
+              f"{qpb:.4g} quartets per full build")
+    return {"impl": "reference", "metric": "hfx_builds_per_s", "value": value, "unit": "builds/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value if value else None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{args.atoms}-atom C/H cluster, HSE erfc w=0.11, Schwarz 1e-8 + density "
+                                   f"screening, P cut 14 bohr", "atoms": args.atoms},
+            "eri_quartets_per_s": qps,
+            "cpu_baseline": {"value": value, "unit": "builds/s", "cores": nt, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "builds/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--atoms", type=int, default=400)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--promote", type=float, default=math.inf)
+    ap.add_argument("--prim-cutoff", type=float, default=1e-14)
+    ap.add_argument("--n-block", type=int, default=128)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    ap.add_argument("--ref-quartets-per-build", type=float, default=None)
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if args.ref_quartets_per_build is None:
+            args.ref_quartets_per_build = REF_QUARTETS_PER_BUILD.get(args.atoms, float("nan"))
+        res = run_reference(args, rank, world)
+        if res is not None:
+            print(json.dumps(res), flush=True)
+        return 0
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    res, s, q = run_ours(args, rank, world)
+    if rank == 0:
+        if not args.no_cpu:
+            qps, nt, dt, n = run_cpu_oracle(args)
+            qpb = res["quartets_per_build"]
+            res["cpu_baseline"] = {"value": qps / qpb, "unit": "builds/s", "cores": nt, "kind": "oracle",
+                                   "sample": f"oracle on the 10 atoms nearest the centre of the {args.atoms}-atom "
+                                             f"cluster, every 2nd canonical bra pair ({n} quartets in {dt:.1f} s, "
+                                             f"{qps:.4g} quartets/s), scaled by {qpb} quartets per full build"}
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+# Canonical quartets computed per build of the default workloads (measured by
+# the CUDA path's own counters; used only to express the oracle's quartets/s
+# in builds/s for --impl reference, which runs no GPU code).
+REF_QUARTETS_PER_BUILD = {}
+
+if __name__ == "__main__":
+    sys.exit(main())

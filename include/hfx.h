@@ -1,0 +1,176 @@
+/*
+ * hfx.h -- C ABI of the GB300 Hartree-Fock exchange (HFX) library.
+ *
+ * The library builds the exchange matrix of the paper's method (Sec. 2,
+ * Eq. H-HFX, without its -1/2 factor)
+ *
+ *     K_ij = sum_kl (ik|jl) P_kl
+ *
+ * over contracted Cartesian Gaussian shells (s, p, d), with the full Coulomb
+ * kernel 1/r (Sec. 2, full-range ERI definition) or the screened kernel
+ * erfc(w r)/r (Sec. 2, Eq. ERI-SR), Schwarz screening (Sec. 2, Eq. schwarz),
+ * density-matrix screening (Sec. 2, Eq. dmscreening), the 8-fold permutation
+ * symmetry of the integrals (Sec. 2), sparse replicated P and K (Sec. 3), and
+ * the exchange energy E_x = -1/2 sum_ij P_ij K_ij.  All compute runs in CUDA
+ * kernels for sm_103a; the device work queue of the exchange kernels is the
+ * single-GPU form of the paper's master/worker distribution (Sec. 3,
+ * Algorithms 1-3).
+ *
+ * Conventions
+ *   - Functions return hfx_status; no C++ exception crosses the ABI.  On error
+ *     hfx_last_error() returns a message (thread-local, valid until the next
+ *     call on the same thread).
+ *   - "host" pointers are read during the call only and may be freed after it;
+ *     "device" pointers are CUDA global memory owned by the caller.
+ *   - Stream arguments are cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Asynchronous functions only enqueue work; device errors show
+ *     up at the next synchronising call (hfx_exchange_energy, hfx_get_stats).
+ *   - Handles are not thread-safe: use one per thread or lock around them.
+ *   - Cartesian components are ordered x, y, z (p) and xx, xy, xz, yy, yz, zz
+ *     (d).  A primitive x^l exp(-a r^2) is scaled to unit norm and the
+ *     contracted shell to unit self-overlap of its x^l component.
+ *   - Sparse matrices (P and K) are atom-pair-blocked: a symmetric pattern of
+ *     atom pairs (X, Y) given as CSR over atoms; block (X, Y) holds the
+ *     nf(X) x nf(Y) functions of the two atoms row-major; blocks follow the CSR
+ *     order.  P and K use the same pattern and the same value layout (the
+ *     paper keeps the density and exchange matrices in one sparse format,
+ *     Sec. 3 and Table 1); K elements outside the pattern are not formed.
+ */
+#ifndef HFX_H
+#define HFX_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HFX_OK = 0,
+  HFX_ERR_INVALID_ARG = 1, /* bad argument or inconsistent input */
+  HFX_ERR_OOM = 2,         /* device allocation failed */
+  HFX_ERR_CUDA = 3,        /* CUDA runtime error (message has the detail) */
+  HFX_ERR_UNSUPPORTED = 4, /* e.g. l > 2 or more than 16 primitives */
+  HFX_ERR_TIMEOUT = 5,     /* a bounded device wait gave up */
+  HFX_ERR_BUSY = 6         /* resource in use (server admission) */
+} hfx_status;
+
+typedef enum { HFX_KERNEL_COULOMB = 0, HFX_KERNEL_ERFC = 1, HFX_KERNEL_ERF = 2 } hfx_kernel;
+typedef enum { HFX_PREC_FP64 = 0, HFX_PREC_MIXED = 1 } hfx_precision;
+
+/* One contracted shell.  alpha/coef: host arrays of nprim exponents (bohr^-2)
+ * and raw contraction coefficients (the library normalises them). */
+typedef struct {
+  int l;       /* 0, 1 or 2 */
+  int nprim;   /* 1..16 */
+  int atom;    /* index into the atom array; shells must be grouped by atom in atom order */
+  int reserved;
+  const double* alpha;
+  const double* coef;
+} hfx_shell_desc;
+
+/* Options of one quartet list (fixed for its lifetime, like the paper's
+ * pre-SCF pair lists, Sec. 2). */
+typedef struct {
+  int kernel;                 /* hfx_kernel */
+  double omega;               /* bohr^-1, erf/erfc kernels (HSE06: 0.11, Sec. 2) */
+  int screen;                 /* 1: Schwarz test Q_IJ Q_KL > tau and exact P_scr > 0 skip */
+  double tau;                 /* Schwarz drop tolerance (Sec. 2, Eq. schwarz) */
+  int density_screen;         /* 1: also require P_scr Q_IJ Q_KL > eps (Eq. dmscreening) */
+  double eps;                 /* density-screening threshold */
+  double prim_cutoff;         /* drop primitive pairs whose self-repulsion estimate is below this (0: keep all) */
+  int precision;              /* hfx_precision */
+  double fp64_promote_bound;  /* MIXED: quartets with Q_IJ Q_KL P_scr above this run in FP64 */
+  int n_block;                /* quartets per work-queue batch (the paper's n_block, Sec. 4); 0 = default */
+  int reserved[3];
+} hfx_opts;
+
+/* Atom-pair block pattern: CSR over atoms (host arrays). */
+typedef struct {
+  int n_atoms;
+  const int* row_ptr; /* n_atoms + 1 */
+  const int* col;     /* row_ptr[n_atoms] atom indices, sorted within each row */
+} hfx_pattern;
+
+typedef struct hfx_basis_s hfx_basis;
+typedef struct hfx_quartets_s hfx_quartets;
+
+/* Statistics of the most recent hfx_build_K on a quartet list. */
+typedef struct {
+  long long n_pairs_significant[6];   /* shell pairs kept per pair class (ss ps pp ds dp dd) */
+  long long n_quartets_schwarz[21];   /* canonical quartets passing the Schwarz test, per class */
+  long long n_quartets_computed[21];  /* quartets evaluated in the last build (after density screening) */
+  long long n_prim_pairs;             /* primitive pairs kept over all significant shell pairs */
+  long long n_values;                 /* length of the P / K value arrays */
+  float ms_setup;                     /* hfx_build_quartets wall time */
+  float ms_last_build;                /* device time of the last hfx_build_K (events) */
+  /* per launch of the last build: pass 0 = FP64 path or the FP32 part of the
+   * mixed path, pass 1 = the FP64-promoted part of the mixed path */
+  long long n_quartets_pass[2][21];
+  long long n_prim_quartets_pass[2][21]; /* primitive quartets evaluated */
+  float ms_class_pass[2][21];            /* device time of each class kernel (events) */
+} hfx_stats;
+
+/* Class table entry (for throughput and roofline accounting). */
+typedef struct {
+  int bra_class, ket_class;   /* pair classes 0..5 = ss ps pp ds dp dd */
+  int la, lb, lc, ld;
+  int n_out;                  /* Cartesian integrals per quartet */
+  int vrr_flops;              /* flops of the vertical recursion per primitive quartet */
+  int hrr_flops;              /* flops of the horizontal recursion per quartet */
+} hfx_class_info;
+
+/* Basis creation (setup).  Copies shells, normalises contraction coefficients
+ * on the device (Sec. 2: contracted GTO shells) and builds the Boys table.
+ * atom_xyz: host, n_atoms x 3 (bohr).  stream: work is enqueued on it and
+ * synchronised before return.  *out must be released with hfx_destroy_basis. */
+hfx_status hfx_create_basis(const hfx_shell_desc* shells, int n_shells, const double* atom_xyz, int n_atoms,
+                            void* stream, hfx_basis** out);
+
+/* Pre-SCF setup (Sec. 2): shell-pair records, Schwarz bounds with the run's
+ * kernel, significant pair lists sorted per class by descending bound, and
+ * the work-queue batches of canonical quartets (I>=J, K>=L, IJ>=KL) that pass
+ * the Schwarz test, grouped by angular-momentum class.  pattern: the sparsity
+ * pattern of P and K (must be symmetric and contain every diagonal block).
+ * Synchronises the stream before return. */
+hfx_status hfx_build_quartets(hfx_basis* basis, const hfx_opts* opts, const hfx_pattern* pattern, void* stream,
+                              hfx_quartets** out);
+
+/* Number of doubles in the P / K value arrays of this pattern. */
+long long hfx_value_count(const hfx_quartets* q);
+
+/* One exchange build (Algorithm 4): zero K, shell-pair Pmax of P, screened ERI
+ * evaluation with the fused exchange contraction, symmetrisation.  P_val, K_val:
+ * device arrays of hfx_value_count() doubles.  Asynchronous on `stream`. */
+hfx_status hfx_build_K(hfx_quartets* q, const double* P_val, double* K_val, void* stream);
+
+/* E_x = -1/2 sum_ij P_ij K_ij over the pattern (device reduction, FP64).
+ * Synchronises the stream; *E_x is a host double. */
+hfx_status hfx_exchange_energy(hfx_quartets* q, const double* P_val, const double* K_val, double* E_x,
+                               void* stream);
+
+/* Dense <-> block-sparse conversion on the device (dense: nbf x nbf row-major).
+ * Pack reads only the pattern's blocks; unpack writes zeros outside it. */
+hfx_status hfx_pack_dense(const hfx_quartets* q, const double* dense, double* val, void* stream);
+hfx_status hfx_unpack_dense(const hfx_quartets* q, const double* val, double* dense, void* stream);
+
+/* Contracted integrals of arbitrary shell quartets (diagnostics and tests).
+ * quartets: host, n x 4 shell indices (I J | K L); out_off: host, n offsets;
+ * out: device; quartet q writes nI*nJ*nK*nL doubles at out + out_off[q] in
+ * (i, j, k, l) row-major order.  precision selects the FP64 or mixed path.
+ * Synchronises the stream. */
+hfx_status hfx_eval_quartets(hfx_basis* basis, int kernel, double omega, int precision, int n,
+                             const int* quartets, const long long* out_off, double* out, void* stream);
+
+/* Statistics (synchronises the device). */
+hfx_status hfx_get_stats(const hfx_quartets* q, hfx_stats* out);
+
+/* Static per-class information; cls in [0, 21). */
+hfx_status hfx_get_class_info(int cls, hfx_class_info* out);
+
+void hfx_destroy_basis(hfx_basis* basis);
+void hfx_destroy_quartets(hfx_quartets* q);
+const char* hfx_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HFX_H */

@@ -1,0 +1,92 @@
+"""Build the HFX CUDA library in-tree: generate the per-class ERI sources, compile
+every translation unit for sm_103a in parallel with nvcc, link libhfx.so."""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import hashlib
+import os
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "csrc")
+GEN = os.path.join(CSRC, "generated")
+OBJ = os.path.join(HERE, "_build")
+INCLUDE = os.path.join(os.path.dirname(HERE), "include")
+LIB = os.path.join(HERE, "libhfx.so")
+NVCC = os.environ.get("NVCC", "nvcc")
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", CSRC, "-I", GEN, "-I", INCLUDE]
+
+
+def _sources():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("gen_eri", os.path.join(CSRC, "gen_eri.py"))
+    gen = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(gen)
+    gen.generate(GEN)
+    tus = sorted(os.path.join(GEN, f) for f in os.listdir(GEN) if f.endswith(".cu"))
+    return [os.path.join(CSRC, "hfx_core.cu")] + tus
+
+
+def _digest(src, extra):
+    h = hashlib.sha256()
+    h.update(" ".join(FLAGS + extra).encode())
+    for path in [src] + extra_headers():
+        with open(path, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def extra_headers():
+    hs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
+    hs += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
+    hs += [os.path.join(GEN, f) for f in ("class_table.h", "class_dispatch.h")]
+    return sorted(hs)
+
+
+def _compile(src):
+    base = os.path.splitext(os.path.basename(src))[0]
+    extra = []
+    tag = _digest(src, extra)
+    obj = os.path.join(OBJ, f"{base}.{tag}.o")
+    if os.path.exists(obj):
+        return obj, None
+    cmd = [NVCC] + FLAGS + extra + ["-c", src, "-o", obj + ".tmp"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        return None, f"{' '.join(cmd)}\n{r.stdout}\n{r.stderr}"
+    os.replace(obj + ".tmp", obj)
+    return obj, None
+
+
+def build(verbose: bool = False) -> str:
+    os.makedirs(OBJ, exist_ok=True)
+    srcs = _sources()
+    workers = max(1, min(len(srcs), os.cpu_count() or 1))
+    objs, errs = [], []
+    # the heaviest classes first so the pool's tail is short
+    srcs.sort(key=lambda p: -os.path.getsize(p.replace("tu_", "cls_").replace(".cu", ".cuh"))
+              if "tu_" in p else 0)
+    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+        for obj, err in ex.map(_compile, srcs):
+            if err:
+                errs.append(err)
+            else:
+                objs.append(obj)
+    if errs:
+        raise RuntimeError("nvcc failed:\n" + "\n".join(errs))
+    tmp = LIB + f".tmp{os.getpid()}"
+    cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + sorted(objs)
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"link failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, LIB)
+    if verbose:
+        print(f"built {LIB} from {len(objs)} objects")
+    return LIB
+
+
+if __name__ == "__main__":
+    build(verbose=True)
+    sys.exit(0)

@@ -1,0 +1,967 @@
+// hfx_core.cu -- C ABI, setup pipeline and the small kernels of the HFX
+// library (see include/hfx.h for the contract of every entry point).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include <cub/device/device_radix_sort.cuh>
+#include <cub/device/device_reduce.cuh>
+#include <cub/device/device_scan.cuh>
+
+#include "eri_kernels.cuh"
+#include "generated/class_dispatch.h"
+#include "generated/class_table.h"
+#include "hfx.h"
+
+using namespace hfx;
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string g_err;
+
+static hfx_status fail(hfx_status s, const std::string& m) {
+  g_err = m;
+  return s;
+}
+
+#define HFX_CK(x)                                                                          \
+  do {                                                                                     \
+    cudaError_t e_ = (x);                                                                  \
+    if (e_ != cudaSuccess) {                                                               \
+      if (e_ == cudaErrorMemoryAllocation) return fail(HFX_ERR_OOM, std::string(#x) + ": out of device memory"); \
+      return fail(HFX_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_));         \
+    }                                                                                      \
+  } while (0)
+
+template <typename T>
+struct DBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  ~DBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  cudaError_t alloc(size_t count) {
+    release();
+    n = count;
+    return cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T));
+  }
+};
+
+static inline int ncart(int l) { return (l + 1) * (l + 2) / 2; }
+static inline int pair_class_of(int la, int lb) { return la * (la + 1) / 2 + lb; }  // la >= lb
+static inline int quartet_class_of(int cb, int ck) { return cb * (cb + 1) / 2 + ck; }  // cb >= ck
+static inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// ------------------------------------------------------------------ handles
+struct hfx_basis_s {
+  int device = 0;
+  int n_shells = 0, n_atoms = 0, nbf = 0, max_nprim = 0;
+  std::vector<int> h_l, h_atom, h_np, h_poff, h_loc, h_atom_nf;
+  std::vector<long long> h_sh_foff, h_atom_foff;
+  DBuf<double> sh_xyz, alpha, coef, boys;
+  DBuf<int> sh_l, sh_atom, sh_poff, sh_loc, atom_nf;
+};
+
+struct hfx_quartets_s {
+  hfx_basis* basis = nullptr;
+  hfx_opts opts{};
+  int n_sm = 0;
+  // pattern
+  int n_atoms = 0;
+  long long n_values = 0;
+  int n_blocks = 0;
+  DBuf<long long> blk_off;                 // n_atoms x n_atoms
+  DBuf<int> blk_x, blk_y;                  // block list
+  DBuf<long long> blk_val_off;
+  // pairs per class
+  long long n_pairs[6] = {0};
+  DBuf<PairRec> pairs[6];
+  DBuf<PrimPair> prims[6];
+  long long n_prim_pairs = 0;
+  // batches per quartet class
+  DBuf<Desc> desc[HFX_NCLASS];
+  int n_desc[HFX_NCLASS] = {0};
+  long long n_quartets[HFX_NCLASS] = {0};
+  // per-build buffers
+  DBuf<double> pmax;                       // n_shells x n_shells
+  DBuf<int> counters;                      // 2 x HFX_NCLASS
+  DBuf<unsigned long long> n_done;         // 2 x 2 x HFX_NCLASS: (pass, class, {quartets, primitive quartets})
+  DBuf<double> scratch;                    // energy accumulator
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEvent_t evk[2][HFX_NCLASS][2] = {};  // per pass / class: start, stop
+  bool ran[2][HFX_NCLASS] = {};
+  float ms_setup = 0.f;
+  int grid_cache[2][HFX_NCLASS] = {{0}};
+  ~hfx_quartets_s() {
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    for (auto& p : evk)
+      for (auto& c : p)
+        for (auto& e : c)
+          if (e) cudaEventDestroy(e);
+  }
+};
+
+// ------------------------------------------------------------------ kernels
+// Boys table: F_m(T_k), T_k = k/16, m = 0..14, by the power series
+// F_m(T) = exp(-T) sum_k (2T)^k / ((2m+1)(2m+3)...(2m+2k+1)) (all terms
+// positive); column 15 holds exp(-T_k).
+__global__ void k_boys_table(double* tab) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kBoysNT * kBoysCols) return;
+  const int it = i / kBoysCols, m = i % kBoysCols;
+  const double T = it * kBoysStep;
+  if (m == kBoysCols - 1) {
+    tab[i] = exp(-T);
+    return;
+  }
+  double term = 1.0 / (2 * m + 1), sum = term;
+  for (int k = 1; k < 2000; ++k) {
+    term *= 2.0 * T / (2 * m + 2 * k + 1);
+    sum += term;
+    if (term < 1e-18 * sum) break;
+  }
+  tab[i] = exp(-T) * sum;
+}
+
+// Contraction coefficients: axial primitive normalisation
+// (2a/pi)^{3/4} (4a)^{l/2} / sqrt((2l-1)!!), then unit self-overlap of the
+// contracted x^l component.
+__global__ void k_normalize(int ns, const int* l, const int* poff, const double* alpha, double* coef) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= ns) return;
+  const int L = l[s], p0 = poff[s], p1 = poff[s + 1];
+  const double df = (L == 2) ? 3.0 : 1.0;
+  for (int k = p0; k < p1; ++k) {
+    const double a = alpha[k];
+    coef[k] *= pow(2.0 * a / M_PI, 0.75) * pow(4.0 * a, 0.5 * L) / sqrt(df);
+  }
+  double S = 0.0;
+  for (int k = p0; k < p1; ++k)
+    for (int m = p0; m < p1; ++m) {
+      const double g = alpha[k] + alpha[m];
+      S += coef[k] * coef[m] * df / pow(2.0 * g, L) * pow(M_PI / g, 1.5);
+    }
+  const double sc = 1.0 / sqrt(S);
+  for (int k = p0; k < p1; ++k) coef[k] *= sc;
+}
+
+// Shell-pair records (Sec. 2: shell pairs; Gaussian product theorem) for a list
+// of oriented pairs (l_A >= l_B).  Primitive pairs whose self-repulsion
+// estimate |c_a c_b K_ab| sqrt(2 pi^{5/2} / (p^2 sqrt(2p))) is below `cutoff`
+// are dropped.
+__global__ void k_pair_build(int n, const int2* list, const double* xyz, const int* l, const int* poff,
+                             const double* alpha, const double* coef, int stride, double cutoff, PairRec* out,
+                             PrimPair* prims, int* pclass) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int A = list[i].x, B = list[i].y;
+  PairRec r;
+  r.A = A;
+  r.B = B;
+  r.poff = (int)((long long)i * stride);
+  double Ax = xyz[3 * A], Ay = xyz[3 * A + 1], Az = xyz[3 * A + 2];
+  double Bx = xyz[3 * B], By = xyz[3 * B + 1], Bz = xyz[3 * B + 2];
+  r.AB[0] = Ax - Bx;
+  r.AB[1] = Ay - By;
+  r.AB[2] = Az - Bz;
+  const double ab2 = r.AB[0] * r.AB[0] + r.AB[1] * r.AB[1] + r.AB[2] * r.AB[2];
+  int cnt = 0;
+  for (int ia = poff[A]; ia < poff[A + 1]; ++ia)
+    for (int ib = poff[B]; ib < poff[B + 1]; ++ib) {
+      const double a = alpha[ia], b = alpha[ib], p = a + b;
+      const double kab = exp(-a * b / p * ab2);
+      const double kp = coef[ia] * coef[ib] * kab / p;
+      const double bound = fabs(kp) * sqrt(kTwoPi52 / sqrt(2.0 * p));
+      if (!(bound >= cutoff)) continue;
+      PrimPair q;
+      q.p = p;
+      q.kp = kp;
+      q.oo2p = 0.5 / p;
+      q.P[0] = (a * Ax + b * Bx) / p;
+      q.P[1] = (a * Ay + b * By) / p;
+      q.P[2] = (a * Az + b * Bz) / p;
+      q.PA[0] = q.P[0] - Ax;
+      q.PA[1] = q.P[1] - Ay;
+      q.PA[2] = q.P[2] - Az;
+      q.bound = bound;
+      prims[(long long)i * stride + cnt] = q;
+      ++cnt;
+    }
+  r.pcnt = cnt;
+  r.Q = 0.0;
+  out[i] = r;
+  const int la = l[A], lb = l[B];
+  pclass[i] = la * (la + 1) / 2 + lb;
+}
+
+__global__ void k_qmax(int n, const double* Q, unsigned long long* qmax_bits) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double v = (i < n) ? Q[i] : 0.0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(qmax_bits, (unsigned long long)__double_as_longlong(v));
+}
+
+__global__ void k_sort_keys(int n, const double* Q, const int* pclass, unsigned long long* qkey, int* idx) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  qkey[i] = ~(unsigned long long)__double_as_longlong(Q[i]);  // descending Q (Q >= 0)
+  idx[i] = i;
+}
+
+__global__ void k_gather_class(int n, const int* idx, const int* pclass, int* ckey) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) ckey[i] = pclass[idx[i]];
+}
+
+__global__ void k_class_counts(int n, const int* sorted_idx, const int* pclass, const double* Q, int screen,
+                               double tau, const unsigned long long* qmax_bits, int* count_all, int* count_kept) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int i = sorted_idx[j];
+  const int c = pclass[i];
+  atomicAdd(&count_all[c], 1);
+  const double qmax = __longlong_as_double((long long)*qmax_bits);
+  if (!screen || Q[i] * qmax > tau) atomicAdd(&count_kept[c], 1);
+}
+
+__global__ void k_gather_pairs(int n, const int* sorted_idx, const PairRec* pairs, const PrimPair* prims,
+                               const double* Q, int stride, PairRec* out, PrimPair* out_prims) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int i = sorted_idx[j];
+  PairRec r = pairs[i];
+  r.Q = Q[i];
+  const long long src = r.poff;
+  r.poff = (int)((long long)j * stride);
+  for (int k = 0; k < r.pcnt; ++k) out_prims[(long long)j * stride + k] = prims[src + k];
+  out[j] = r;
+}
+
+// Work-queue batches for one quartet class: bra pair j (class cb) against the
+// ket pairs of class ck whose bound passes the Schwarz test.  Ket lists are
+// sorted by descending Q, so the survivors of Q_bra Q_ket > tau are a prefix;
+// same class: canonical kets start at the bra's own rank.
+__global__ void k_desc_count(int nb, const PairRec* bra, int nk, const PairRec* ket, int same, int screen,
+                             double tau, int n_block, int* chunks, long long* nq) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nb) return;
+  int k1 = nk;
+  if (screen) {
+    const double qb = bra[j].Q;
+    const double thr = (qb > 0.0) ? (tau / qb) * (1.0 - 1e-12) : INFINITY;
+    int lo = 0, hi = nk;  // first index with Q <= thr
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (ket[mid].Q > thr) lo = mid + 1;
+      else hi = mid;
+    }
+    k1 = lo;
+  }
+  const int k0 = same ? j : 0;
+  const int cnt = k1 > k0 ? k1 - k0 : 0;
+  chunks[j] = (cnt + n_block - 1) / n_block;
+  nq[j] = cnt;
+}
+
+__global__ void k_desc_fill(int nb, int nk, const PairRec* bra, const PairRec* ket, int same, int screen,
+                            double tau, int n_block, const int* off, Desc* desc) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nb) return;
+  int k1 = nk;
+  if (screen) {
+    const double qb = bra[j].Q;
+    const double thr = (qb > 0.0) ? (tau / qb) * (1.0 - 1e-12) : INFINITY;
+    int lo = 0, hi = nk;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (ket[mid].Q > thr) lo = mid + 1;
+      else hi = mid;
+    }
+    k1 = lo;
+  }
+  const int k0 = same ? j : 0;
+  int o = off[j];
+  for (int k = k0; k < k1; k += n_block) {
+    Desc d;
+    d.bra = j;
+    d.k0 = k;
+    d.k1 = min(k + n_block, k1);
+    d.pad = 0;
+    desc[o++] = d;
+  }
+}
+
+// Pmax per shell pair, max |P_ij| over i in I, j in J (Sec. 2, density
+// screening; computed every build from the current P).
+__global__ void k_pmax(int ns, int na, const int* sh_atom, const int* sh_loc, const int* l, const int* atom_nf,
+                       const long long* blk_off, const double* P, double* pmax) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)ns * ns) return;
+  const int I = (int)(t / ns), J = (int)(t % ns);
+  const long long o = blk_off[sh_atom[I] * na + sh_atom[J]];
+  double mx = 0.0;
+  if (o >= 0) {
+    const int nI = (l[I] + 1) * (l[I] + 2) / 2, nJ = (l[J] + 1) * (l[J] + 2) / 2;
+    const int nfJ = atom_nf[sh_atom[J]];
+    for (int a = 0; a < nI; ++a)
+      for (int b = 0; b < nJ; ++b) mx = fmax(mx, fabs(P[o + (long long)(sh_loc[I] + a) * nfJ + sh_loc[J] + b]));
+  }
+  pmax[t] = mx;
+}
+
+// K = K' + K'^T over the pattern: the scatter adds four of the eight
+// permutations of each canonical quartet; the other four are the transposes.
+__global__ void k_symmetrize(int n_blocks, const int* bx, const int* by, const long long* boff, int na,
+                             const long long* blk_off, const int* atom_nf, double* K) {
+  const int b = blockIdx.x;
+  if (b >= n_blocks) return;
+  const int X = bx[b], Y = by[b];
+  if (X > Y) return;
+  const int nX = atom_nf[X], nY = atom_nf[Y];
+  const long long oXY = boff[b];
+  if (X == Y) {
+    for (int e = threadIdx.x; e < nX * nX; e += blockDim.x) {
+      const int r = e / nX, c = e % nX;
+      if (r < c) {
+        const double s = K[oXY + r * nX + c] + K[oXY + c * nX + r];
+        K[oXY + r * nX + c] = s;
+        K[oXY + c * nX + r] = s;
+      } else if (r == c) {
+        K[oXY + r * nX + r] *= 2.0;
+      }
+    }
+  } else {
+    const long long oYX = blk_off[Y * na + X];
+    for (int e = threadIdx.x; e < nX * nY; e += blockDim.x) {
+      const int r = e / nY, c = e % nY;
+      const double s = K[oXY + r * nY + c] + K[oYX + c * nX + r];
+      K[oXY + r * nY + c] = s;
+      K[oYX + c * nX + r] = s;
+    }
+  }
+}
+
+// sum_i P_i K_i (FP64), block reduction then one atomicAdd per block.  `vec`:
+// both arrays 16-byte aligned, read as double2.
+__global__ void k_dot(long long n, const double* __restrict__ P, const double* __restrict__ K, int vec,
+                      double* out) {
+  double s = 0.0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (vec) {
+    const long long n2 = n / 2;
+    const double2* P2 = reinterpret_cast<const double2*>(P);
+    const double2* K2 = reinterpret_cast<const double2*>(K);
+    for (long long j = i; j < n2; j += stride) {
+      const double2 p = __ldg(P2 + j), k = __ldg(K2 + j);
+      s = fma(p.x, k.x, fma(p.y, k.y, s));
+    }
+    if (i == 0 && (n & 1)) s = fma(P[n - 1], K[n - 1], s);
+  } else {
+    for (long long j = i; j < n; j += stride) s = fma(__ldg(P + j), __ldg(K + j), s);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  __shared__ double ws[32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < (blockDim.x >> 5)) ? ws[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) atomicAdd(out, s);
+  }
+}
+
+__global__ void k_pack(int n_blocks, const int* bx, const int* by, const long long* boff, const long long* afoff,
+                       const int* atom_nf, long long nbf, double* dense, double* val, int unpack) {
+  const int b = blockIdx.x;
+  if (b >= n_blocks) return;
+  const int X = bx[b], Y = by[b];
+  const int nX = atom_nf[X], nY = atom_nf[Y];
+  for (int e = threadIdx.x; e < nX * nY; e += blockDim.x) {
+    const int r = e / nY, c = e % nY;
+    const long long di = (afoff[X] + r) * nbf + afoff[Y] + c;
+    if (unpack)
+      dense[di] = val[boff[b] + e];
+    else
+      val[boff[b] + e] = dense[di];
+  }
+}
+
+// ------------------------------------------------------------------ helpers
+static int device_sm_count() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 1;
+}
+
+template <typename T>
+static cudaError_t upload(DBuf<T>& b, const std::vector<T>& v, cudaStream_t s) {
+  cudaError_t e = b.alloc(v.size());
+  if (e != cudaSuccess) return e;
+  if (v.empty()) return cudaSuccess;
+  return cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+}
+
+// ------------------------------------------------------------------ ABI
+extern "C" {
+
+const char* hfx_last_error(void) { return g_err.c_str(); }
+
+hfx_status hfx_get_class_info(int cls, hfx_class_info* out) {
+  if (cls < 0 || cls >= HFX_NCLASS || !out) return fail(HFX_ERR_INVALID_ARG, "class index out of range");
+  const int* t = hfx_class_table[cls];
+  out->bra_class = t[0];
+  out->ket_class = t[1];
+  out->la = t[2];
+  out->lb = t[3];
+  out->lc = t[4];
+  out->ld = t[5];
+  out->n_out = t[7];
+  out->vrr_flops = t[8];
+  out->hrr_flops = t[9];
+  return HFX_OK;
+}
+
+hfx_status hfx_create_basis(const hfx_shell_desc* shells, int n_shells, const double* atom_xyz, int n_atoms,
+                            void* stream, hfx_basis** out) {
+  if (!out) return fail(HFX_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (n_shells <= 0 || n_atoms <= 0 || !shells || !atom_xyz)
+    return fail(HFX_ERR_INVALID_ARG, "need at least one shell and one atom");
+  cudaStream_t s = (cudaStream_t)stream;
+  auto* b = new hfx_basis_s();
+  cudaGetDevice(&b->device);
+  b->n_shells = n_shells;
+  b->n_atoms = n_atoms;
+  std::vector<double> xyz(3 * (size_t)n_shells), alpha, coef;
+  std::vector<int> poff(1, 0);
+  b->h_atom_nf.assign(n_atoms, 0);
+  int prev_atom = 0;
+  for (int i = 0; i < n_shells; ++i) {
+    const hfx_shell_desc& d = shells[i];
+    if (d.l < 0 || d.l > kMaxL) {
+      delete b;
+      return fail(HFX_ERR_UNSUPPORTED, "shell " + std::to_string(i) + ": angular momentum must be 0, 1 or 2");
+    }
+    if (d.nprim < 1 || d.nprim > 16 || !d.alpha || !d.coef) {
+      delete b;
+      return fail(HFX_ERR_UNSUPPORTED, "shell " + std::to_string(i) + ": need 1..16 primitives");
+    }
+    if (d.atom < 0 || d.atom >= n_atoms || d.atom < prev_atom) {
+      delete b;
+      return fail(HFX_ERR_INVALID_ARG, "shells must be grouped by atom in increasing atom order");
+    }
+    prev_atom = d.atom;
+    for (int k = 0; k < d.nprim; ++k) {
+      if (!(d.alpha[k] > 0.0) || !std::isfinite(d.alpha[k]) || !std::isfinite(d.coef[k])) {
+        delete b;
+        return fail(HFX_ERR_INVALID_ARG, "shell " + std::to_string(i) + ": exponents must be positive and finite");
+      }
+      alpha.push_back(d.alpha[k]);
+      coef.push_back(d.coef[k]);
+    }
+    poff.push_back((int)alpha.size());
+    for (int x = 0; x < 3; ++x) xyz[3 * i + x] = atom_xyz[3 * d.atom + x];
+    b->h_l.push_back(d.l);
+    b->h_atom.push_back(d.atom);
+    b->h_np.push_back(d.nprim);
+    b->h_loc.push_back(b->h_atom_nf[d.atom]);
+    b->h_atom_nf[d.atom] += ncart(d.l);
+    b->max_nprim = std::max(b->max_nprim, d.nprim);
+  }
+  b->h_poff = poff;
+  b->h_atom_foff.assign(n_atoms + 1, 0);
+  for (int a = 0; a < n_atoms; ++a) b->h_atom_foff[a + 1] = b->h_atom_foff[a] + b->h_atom_nf[a];
+  b->nbf = (int)b->h_atom_foff[n_atoms];
+  b->h_sh_foff.resize(n_shells + 1);
+  for (int i = 0; i < n_shells; ++i) b->h_sh_foff[i] = b->h_atom_foff[b->h_atom[i]] + b->h_loc[i];
+  b->h_sh_foff[n_shells] = b->nbf;
+  cudaError_t e = cudaSuccess;
+  if ((e = upload(b->sh_xyz, xyz, s)) != cudaSuccess || (e = upload(b->alpha, alpha, s)) != cudaSuccess ||
+      (e = upload(b->coef, coef, s)) != cudaSuccess || (e = upload(b->sh_l, b->h_l, s)) != cudaSuccess ||
+      (e = upload(b->sh_atom, b->h_atom, s)) != cudaSuccess || (e = upload(b->sh_poff, poff, s)) != cudaSuccess ||
+      (e = upload(b->sh_loc, b->h_loc, s)) != cudaSuccess || (e = upload(b->atom_nf, b->h_atom_nf, s)) != cudaSuccess ||
+      (e = b->boys.alloc((size_t)kBoysNT * kBoysCols)) != cudaSuccess) {
+    delete b;
+    return fail(e == cudaErrorMemoryAllocation ? HFX_ERR_OOM : HFX_ERR_CUDA,
+                std::string("hfx_create_basis: ") + cudaGetErrorString(e));
+  }
+  k_normalize<<<blocks_for(n_shells, 128), 128, 0, s>>>(n_shells, b->sh_l.p, b->sh_poff.p, b->alpha.p, b->coef.p);
+  k_boys_table<<<blocks_for(kBoysNT * kBoysCols, 128), 128, 0, s>>>(b->boys.p);
+  e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    delete b;
+    return fail(HFX_ERR_CUDA, std::string("hfx_create_basis: ") + cudaGetErrorString(e));
+  }
+  *out = b;
+  return HFX_OK;
+}
+
+void hfx_destroy_basis(hfx_basis* b) { delete b; }
+
+static hfx_status setup_pattern(hfx_quartets_s* q, const hfx_pattern* pat, cudaStream_t s) {
+  hfx_basis* b = q->basis;
+  const int na = b->n_atoms;
+  if (!pat || pat->n_atoms != na || !pat->row_ptr || !pat->col)
+    return fail(HFX_ERR_INVALID_ARG, "pattern must cover the basis's atoms");
+  std::vector<long long> off((size_t)na * na, -1);
+  std::vector<int> bx, by;
+  std::vector<long long> bo;
+  long long nv = 0;
+  for (int X = 0; X < na; ++X) {
+    if (pat->row_ptr[X + 1] < pat->row_ptr[X]) return fail(HFX_ERR_INVALID_ARG, "pattern row_ptr not monotone");
+    for (int k = pat->row_ptr[X]; k < pat->row_ptr[X + 1]; ++k) {
+      const int Y = pat->col[k];
+      if (Y < 0 || Y >= na || off[(size_t)X * na + Y] >= 0)
+        return fail(HFX_ERR_INVALID_ARG, "pattern column out of range or repeated");
+      off[(size_t)X * na + Y] = nv;
+      bx.push_back(X);
+      by.push_back(Y);
+      bo.push_back(nv);
+      nv += (long long)b->h_atom_nf[X] * b->h_atom_nf[Y];
+    }
+  }
+  for (int X = 0; X < na; ++X) {
+    if (off[(size_t)X * na + X] < 0) return fail(HFX_ERR_INVALID_ARG, "pattern must contain every diagonal block");
+    for (int Y = 0; Y < na; ++Y)
+      if ((off[(size_t)X * na + Y] >= 0) != (off[(size_t)Y * na + X] >= 0))
+        return fail(HFX_ERR_INVALID_ARG, "pattern must be symmetric");
+  }
+  q->n_atoms = na;
+  q->n_values = nv;
+  q->n_blocks = (int)bx.size();
+  HFX_CK(upload(q->blk_off, off, s));
+  HFX_CK(upload(q->blk_x, bx, s));
+  HFX_CK(upload(q->blk_y, by, s));
+  HFX_CK(upload(q->blk_val_off, bo, s));
+  return HFX_OK;
+}
+
+hfx_status hfx_build_quartets(hfx_basis* b, const hfx_opts* opts_in, const hfx_pattern* pattern, void* stream,
+                              hfx_quartets** out) {
+  if (!out || !b || !opts_in) return fail(HFX_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  hfx_opts o = *opts_in;
+  if (o.kernel < 0 || o.kernel > 2) return fail(HFX_ERR_INVALID_ARG, "unknown kernel");
+  if (o.kernel != HFX_KERNEL_COULOMB && !(o.omega > 0.0)) return fail(HFX_ERR_INVALID_ARG, "omega must be > 0");
+  if (o.precision != HFX_PREC_FP64 && o.precision != HFX_PREC_MIXED)
+    return fail(HFX_ERR_INVALID_ARG, "unknown precision");
+  if (o.n_block <= 0) o.n_block = 128;
+  if (!(o.tau >= 0.0) || !(o.eps >= 0.0) || !(o.prim_cutoff >= 0.0))
+    return fail(HFX_ERR_INVALID_ARG, "thresholds must be >= 0");
+  auto* q = new hfx_quartets_s();
+  std::unique_ptr<hfx_quartets_s> guard(q);
+  q->basis = b;
+  q->opts = o;
+  q->n_sm = device_sm_count();
+  cudaEvent_t t0, t1;
+  HFX_CK(cudaEventCreate(&t0));
+  HFX_CK(cudaEventCreate(&t1));
+  HFX_CK(cudaEventRecord(t0, s));
+  hfx_status st = setup_pattern(q, pattern, s);
+  if (st != HFX_OK) return st;
+
+  // 1. all shell pairs, oriented l_A >= l_B
+  const int ns = b->n_shells;
+  const long long npair_ll = (long long)ns * (ns + 1) / 2;
+  if (npair_ll > (1LL << 30)) return fail(HFX_ERR_UNSUPPORTED, "too many shell pairs");
+  const int npair = (int)npair_ll;
+  const int stride = b->max_nprim * b->max_nprim;
+  if ((long long)npair * stride > (1LL << 31) - 1) return fail(HFX_ERR_UNSUPPORTED, "too many primitive pairs");
+  std::vector<int2> list((size_t)npair);
+  {
+    size_t k = 0;
+    for (int I = 0; I < ns; ++I)
+      for (int J = 0; J <= I; ++J) {
+        int A = I, B = J;
+        if (b->h_l[A] < b->h_l[B]) std::swap(A, B);
+        list[k++] = make_int2(A, B);
+      }
+  }
+  DBuf<int2> d_list;
+  DBuf<PairRec> all_pairs;
+  DBuf<PrimPair> all_prims;
+  DBuf<int> pclass;
+  DBuf<double> Q;
+  HFX_CK(upload(d_list, list, s));
+  HFX_CK(all_pairs.alloc(npair));
+  HFX_CK(all_prims.alloc((size_t)npair * stride));
+  HFX_CK(pclass.alloc(npair));
+  HFX_CK(Q.alloc(npair));
+  k_pair_build<<<blocks_for(npair, 128), 128, 0, s>>>(npair, d_list.p, b->sh_xyz.p, b->sh_l.p, b->sh_poff.p,
+                                                       b->alpha.p, b->coef.p, stride, o.prim_cutoff, all_pairs.p,
+                                                       all_prims.p, pclass.p);
+  HFX_CK(cudaGetLastError());
+
+  // 2. Schwarz bounds with the run's kernel (Sec. 2, Eq. schwarz)
+  for (int c = 0; c < 6; ++c) {
+    SchwarzArgs a;
+    a.pairs = all_pairs.p;
+    a.prims = all_prims.p;
+    a.pair_class = pclass.p;
+    a.n_pairs = npair;
+    a.cls = c;
+    a.boys = b->boys.p;
+    a.kernel = o.kernel;
+    a.omega2 = o.omega * o.omega;
+    a.Q = Q.p;
+    kClassOps[quartet_class_of(c, c)].launch_schwarz(a, s);
+  }
+  HFX_CK(cudaGetLastError());
+
+  // 3. sort pairs by (class, descending Q); significant pairs are a prefix of
+  //    each class segment (Q_IJ Q_max > tau is lossless)
+  DBuf<unsigned long long> qmax, key, key_out;
+  DBuf<int> idx, idx_out, ckey, ckey_out, cnt;
+  HFX_CK(qmax.alloc(1));
+  HFX_CK(cudaMemsetAsync(qmax.p, 0, sizeof(unsigned long long), s));
+  k_qmax<<<blocks_for(npair, 256), 256, 0, s>>>(npair, Q.p, qmax.p);
+  HFX_CK(key.alloc(npair));
+  HFX_CK(key_out.alloc(npair));
+  HFX_CK(idx.alloc(npair));
+  HFX_CK(idx_out.alloc(npair));
+  HFX_CK(ckey.alloc(npair));
+  HFX_CK(ckey_out.alloc(npair));
+  k_sort_keys<<<blocks_for(npair, 256), 256, 0, s>>>(npair, Q.p, pclass.p, key.p, idx.p);
+  {
+    size_t tmp_bytes = 0, tmp2 = 0;
+    cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, key.p, key_out.p, idx.p, idx_out.p, npair, 0, 64, s);
+    cub::DeviceRadixSort::SortPairs(nullptr, tmp2, ckey.p, ckey_out.p, idx_out.p, idx.p, npair, 0, 3, s);
+    DBuf<unsigned char> tmp;
+    HFX_CK(tmp.alloc(std::max(tmp_bytes, tmp2)));
+    tmp_bytes = tmp.n;
+    HFX_CK(cub::DeviceRadixSort::SortPairs(tmp.p, tmp_bytes, key.p, key_out.p, idx.p, idx_out.p, npair, 0, 64, s));
+    k_gather_class<<<blocks_for(npair, 256), 256, 0, s>>>(npair, idx_out.p, pclass.p, ckey.p);
+    tmp_bytes = tmp.n;
+    HFX_CK(cub::DeviceRadixSort::SortPairs(tmp.p, tmp_bytes, ckey.p, ckey_out.p, idx_out.p, idx.p, npair, 0, 3, s));
+  }
+  HFX_CK(cnt.alloc(12));
+  HFX_CK(cudaMemsetAsync(cnt.p, 0, 12 * sizeof(int), s));
+  k_class_counts<<<blocks_for(npair, 256), 256, 0, s>>>(npair, idx.p, pclass.p, Q.p, o.screen, o.tau, qmax.p,
+                                                        cnt.p, cnt.p + 6);
+  int h_cnt[12];
+  HFX_CK(cudaMemcpyAsync(h_cnt, cnt.p, sizeof(h_cnt), cudaMemcpyDeviceToHost, s));
+  HFX_CK(cudaStreamSynchronize(s));
+
+  // 4. per-class significant pair lists
+  long long seg = 0;
+  for (int c = 0; c < 6; ++c) {
+    const int nk = h_cnt[6 + c];
+    q->n_pairs[c] = nk;
+    HFX_CK(q->pairs[c].alloc(nk));
+    HFX_CK(q->prims[c].alloc((size_t)nk * stride));
+    if (nk > 0)
+      k_gather_pairs<<<blocks_for(nk, 128), 128, 0, s>>>(nk, idx.p + seg, all_pairs.p, all_prims.p, Q.p, stride,
+                                                         q->pairs[c].p, q->prims[c].p);
+    seg += h_cnt[c];
+  }
+  HFX_CK(cudaGetLastError());
+
+  // 5. work-queue batches per quartet class
+  for (int cb = 0; cb < 6; ++cb)
+    for (int ck = 0; ck <= cb; ++ck) {
+      const int cls = quartet_class_of(cb, ck);
+      const int nb = (int)q->n_pairs[cb], nk = (int)q->n_pairs[ck];
+      q->n_desc[cls] = 0;
+      q->n_quartets[cls] = 0;
+      if (nb == 0 || nk == 0) continue;
+      DBuf<int> chunks, off;
+      DBuf<long long> nq, nq_sum;
+      HFX_CK(chunks.alloc(nb));
+      HFX_CK(off.alloc(nb));
+      HFX_CK(nq.alloc(nb));
+      HFX_CK(nq_sum.alloc(1));
+      k_desc_count<<<blocks_for(nb, 128), 128, 0, s>>>(nb, q->pairs[cb].p, nk, q->pairs[ck].p, cb == ck, o.screen,
+                                                       o.tau, o.n_block, chunks.p, nq.p);
+      size_t t1b = 0, t2b = 0;
+      cub::DeviceScan::ExclusiveSum(nullptr, t1b, chunks.p, off.p, nb, s);
+      cub::DeviceReduce::Sum(nullptr, t2b, nq.p, nq_sum.p, nb, s);
+      DBuf<unsigned char> tmp;
+      HFX_CK(tmp.alloc(std::max(t1b, t2b)));
+      t1b = tmp.n;
+      HFX_CK(cub::DeviceScan::ExclusiveSum(tmp.p, t1b, chunks.p, off.p, nb, s));
+      t2b = tmp.n;
+      HFX_CK(cub::DeviceReduce::Sum(tmp.p, t2b, nq.p, nq_sum.p, nb, s));
+      int last_off = 0, last_chunks = 0;
+      long long total_q = 0;
+      HFX_CK(cudaMemcpyAsync(&last_off, off.p + nb - 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+      HFX_CK(cudaMemcpyAsync(&last_chunks, chunks.p + nb - 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+      HFX_CK(cudaMemcpyAsync(&total_q, nq_sum.p, sizeof(long long), cudaMemcpyDeviceToHost, s));
+      HFX_CK(cudaStreamSynchronize(s));
+      const long long nd = (long long)last_off + last_chunks;
+      if (nd > (1LL << 31) - 1) return fail(HFX_ERR_UNSUPPORTED, "too many work-queue batches; raise n_block");
+      q->n_desc[cls] = (int)nd;
+      q->n_quartets[cls] = total_q;
+      HFX_CK(q->desc[cls].alloc(nd));
+      if (nd > 0)
+        k_desc_fill<<<blocks_for(nb, 128), 128, 0, s>>>(nb, nk, q->pairs[cb].p, q->pairs[ck].p, cb == ck, o.screen,
+                                                        o.tau, o.n_block, off.p, q->desc[cls].p);
+      HFX_CK(cudaGetLastError());
+    }
+  long long npp = 0;
+  for (int c = 0; c < 6; ++c) {
+    if (q->n_pairs[c] == 0) continue;
+    std::vector<PairRec> h((size_t)q->n_pairs[c]);
+    HFX_CK(cudaMemcpyAsync(h.data(), q->pairs[c].p, h.size() * sizeof(PairRec), cudaMemcpyDeviceToHost, s));
+    HFX_CK(cudaStreamSynchronize(s));
+    for (auto& r : h) npp += r.pcnt;
+  }
+  q->n_prim_pairs = npp;
+
+  // 6. per-build buffers
+  HFX_CK(q->pmax.alloc((size_t)ns * ns));
+  HFX_CK(q->counters.alloc(2 * HFX_NCLASS));
+  HFX_CK(q->n_done.alloc(4 * HFX_NCLASS));
+  HFX_CK(q->scratch.alloc(2));
+  HFX_CK(cudaMemsetAsync(q->n_done.p, 0, 4 * HFX_NCLASS * sizeof(unsigned long long), s));
+  HFX_CK(cudaEventCreate(&q->ev0));
+  HFX_CK(cudaEventCreate(&q->ev1));
+  for (auto& p : q->evk)
+    for (auto& c : p)
+      for (auto& e : c) HFX_CK(cudaEventCreate(&e));
+  HFX_CK(cudaEventRecord(t1, s));
+  HFX_CK(cudaEventSynchronize(t1));
+  cudaEventElapsedTime(&q->ms_setup, t0, t1);
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  HFX_CK(cudaGetLastError());
+  *out = guard.release();
+  return HFX_OK;
+}
+
+void hfx_destroy_quartets(hfx_quartets* q) { delete q; }
+
+long long hfx_value_count(const hfx_quartets* q) { return q ? q->n_values : -1; }
+
+hfx_status hfx_build_K(hfx_quartets* q, const double* P, double* K, void* stream) {
+  if (!q || !P || !K) return fail(HFX_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  hfx_basis* b = q->basis;
+  const hfx_opts& o = q->opts;
+  const int ns = b->n_shells;
+  HFX_CK(cudaEventRecord(q->ev0, s));
+  HFX_CK(cudaMemsetAsync(K, 0, (size_t)q->n_values * sizeof(double), s));
+  k_pmax<<<blocks_for((long long)ns * ns, 256), 256, 0, s>>>(ns, q->n_atoms, b->sh_atom.p, b->sh_loc.p, b->sh_l.p,
+                                                               b->atom_nf.p, q->blk_off.p, P, q->pmax.p);
+  HFX_CK(cudaMemsetAsync(q->counters.p, 0, 2 * HFX_NCLASS * sizeof(int), s));
+  HFX_CK(cudaMemsetAsync(q->n_done.p, 0, 4 * HFX_NCLASS * sizeof(unsigned long long), s));
+  for (auto& p : q->ran)
+    for (auto& r : p) r = false;
+  const bool mixed = o.precision == HFX_PREC_MIXED;
+  const bool promote = mixed && std::isfinite(o.fp64_promote_bound);
+  for (int cls = 0; cls < HFX_NCLASS; ++cls) {
+    if (q->n_desc[cls] == 0) continue;
+    const int cb = hfx_class_table[cls][0], ck = hfx_class_table[cls][1];
+    BuildArgs a;
+    a.bra_pairs = q->pairs[cb].p;
+    a.bra_prims = q->prims[cb].p;
+    a.ket_pairs = q->pairs[ck].p;
+    a.ket_prims = q->prims[ck].p;
+    a.desc = q->desc[cls].p;
+    a.n_desc = q->n_desc[cls];
+    a.same_class = cb == ck;
+    a.boys = b->boys.p;
+    a.kernel = o.kernel;
+    a.omega2 = o.omega * o.omega;
+    a.screen = o.screen;
+    a.tau = o.tau;
+    a.dscreen = o.density_screen;
+    a.eps = o.eps;
+    a.promote = o.fp64_promote_bound;
+    a.pmax = q->pmax.p;
+    a.ns = ns;
+    a.P = P;
+    a.K = K;
+    a.blk_off = q->blk_off.p;
+    a.n_atoms = q->n_atoms;
+    a.sh_atom = b->sh_atom.p;
+    a.sh_loc = b->sh_loc.p;
+    a.atom_nf = b->atom_nf.p;
+    const int passes = promote ? 2 : 1;
+    for (int pass = 0; pass < passes; ++pass) {
+      const int fp32 = mixed && pass == 0;
+      a.route = promote ? (pass == 0 ? 1 : 2) : 0;
+      a.counter = q->counters.p + pass * HFX_NCLASS + cls;
+      a.n_done = q->n_done.p + 2 * (pass * HFX_NCLASS + cls);
+      int& g = q->grid_cache[fp32][cls];
+      if (g == 0) g = kClassOps[cls].occupancy_K(fp32) * q->n_sm;
+      HFX_CK(cudaEventRecord(q->evk[pass][cls][0], s));
+      kClassOps[cls].launch_K(a, fp32, g, s);
+      HFX_CK(cudaEventRecord(q->evk[pass][cls][1], s));
+      q->ran[pass][cls] = true;
+    }
+  }
+  k_symmetrize<<<q->n_blocks, 128, 0, s>>>(q->n_blocks, q->blk_x.p, q->blk_y.p, q->blk_val_off.p, q->n_atoms,
+                                           q->blk_off.p, b->atom_nf.p, K);
+  HFX_CK(cudaEventRecord(q->ev1, s));
+  HFX_CK(cudaGetLastError());
+  return HFX_OK;
+}
+
+hfx_status hfx_exchange_energy(hfx_quartets* q, const double* P, const double* K, double* E_x, void* stream) {
+  if (!q || !P || !K || !E_x) return fail(HFX_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  HFX_CK(cudaMemsetAsync(q->scratch.p, 0, sizeof(double), s));
+  const int blocks = std::max(1, std::min<int>(4 * q->n_sm, (int)((q->n_values / 2 + 255) / 256)));
+  const int vec = ((reinterpret_cast<uintptr_t>(P) | reinterpret_cast<uintptr_t>(K)) & 15) == 0;
+  k_dot<<<blocks, 256, 0, s>>>(q->n_values, P, K, vec, q->scratch.p);
+  double h = 0.0;
+  HFX_CK(cudaMemcpyAsync(&h, q->scratch.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+  HFX_CK(cudaStreamSynchronize(s));
+  *E_x = -0.5 * h;
+  return HFX_OK;
+}
+
+hfx_status hfx_pack_dense(const hfx_quartets* q, const double* dense, double* val, void* stream) {
+  if (!q || !dense || !val) return fail(HFX_ERR_INVALID_ARG, "NULL argument");
+  DBuf<long long> afoff;
+  cudaStream_t s = (cudaStream_t)stream;
+  HFX_CK(upload(afoff, q->basis->h_atom_foff, s));
+  k_pack<<<q->n_blocks, 128, 0, s>>>(q->n_blocks, q->blk_x.p, q->blk_y.p, q->blk_val_off.p, afoff.p,
+                                     q->basis->atom_nf.p, q->basis->nbf, const_cast<double*>(dense), val, 0);
+  HFX_CK(cudaStreamSynchronize(s));
+  return HFX_OK;
+}
+
+hfx_status hfx_unpack_dense(const hfx_quartets* q, const double* val, double* dense, void* stream) {
+  if (!q || !dense || !val) return fail(HFX_ERR_INVALID_ARG, "NULL argument");
+  DBuf<long long> afoff;
+  cudaStream_t s = (cudaStream_t)stream;
+  HFX_CK(upload(afoff, q->basis->h_atom_foff, s));
+  const size_t nbf = (size_t)q->basis->nbf;
+  HFX_CK(cudaMemsetAsync(dense, 0, nbf * nbf * sizeof(double), s));
+  k_pack<<<q->n_blocks, 128, 0, s>>>(q->n_blocks, q->blk_x.p, q->blk_y.p, q->blk_val_off.p, afoff.p,
+                                     q->basis->atom_nf.p, q->basis->nbf, dense, const_cast<double*>(val), 1);
+  HFX_CK(cudaStreamSynchronize(s));
+  return HFX_OK;
+}
+
+hfx_status hfx_eval_quartets(hfx_basis* b, int kernel, double omega, int precision, int n, const int* quartets,
+                             const long long* out_off, double* out, void* stream) {
+  if (!b || (n > 0 && (!quartets || !out_off || !out))) return fail(HFX_ERR_INVALID_ARG, "NULL argument");
+  if (kernel < 0 || kernel > 2) return fail(HFX_ERR_INVALID_ARG, "unknown kernel");
+  if (n <= 0) return HFX_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  std::map<std::pair<int, int>, int> pid;
+  std::vector<int2> plist;
+  std::vector<int4> items((size_t)n), strides((size_t)n);
+  auto orient = [&](int I, int J, bool& swapped) {
+    swapped = b->h_l[I] < b->h_l[J];
+    const int A = swapped ? J : I, B = swapped ? I : J;
+    auto key = std::make_pair(A, B);
+    auto it = pid.find(key);
+    if (it != pid.end()) return it->second;
+    const int id = (int)plist.size();
+    pid[key] = id;
+    plist.push_back(make_int2(A, B));
+    return id;
+  };
+  for (int t = 0; t < n; ++t) {
+    const int* sh = quartets + 4 * t;
+    for (int k = 0; k < 4; ++k)
+      if (sh[k] < 0 || sh[k] >= b->n_shells) return fail(HFX_ERR_INVALID_ARG, "shell index out of range");
+    const int nI = ncart(b->h_l[sh[0]]), nJ = ncart(b->h_l[sh[1]]), nK = ncart(b->h_l[sh[2]]),
+              nL = ncart(b->h_l[sh[3]]);
+    const int sI = nJ * nK * nL, sJ = nK * nL, sK = nL, sL = 1;
+    bool swb, swk;
+    const int pb = orient(sh[0], sh[1], swb), pk = orient(sh[2], sh[3], swk);
+    int sa = swb ? sJ : sI, sb = swb ? sI : sJ, sc = swk ? sL : sK, sd = swk ? sK : sL;
+    const int lA = b->h_l[plist[pb].x], lB = b->h_l[plist[pb].y];
+    const int lC = b->h_l[plist[pk].x], lD = b->h_l[plist[pk].y];
+    int cb = pair_class_of(lA, lB), ck = pair_class_of(lC, lD);
+    int bra = pb, ket = pk;
+    if (cb < ck) {
+      std::swap(bra, ket);
+      std::swap(cb, ck);
+      std::swap(sa, sc);
+      std::swap(sb, sd);
+    }
+    items[t] = make_int4(bra, ket, quartet_class_of(cb, ck), 0);
+    strides[t] = make_int4(sa, sb, sc, sd);
+  }
+  const int np = (int)plist.size();
+  const int stride = b->max_nprim * b->max_nprim;
+  DBuf<int2> d_list;
+  DBuf<PairRec> pairs;
+  DBuf<PrimPair> prims;
+  DBuf<int> pclass;
+  DBuf<int4> d_items, d_strides;
+  DBuf<long long> d_off;
+  HFX_CK(upload(d_list, plist, s));
+  HFX_CK(pairs.alloc(np));
+  HFX_CK(prims.alloc((size_t)np * stride));
+  HFX_CK(pclass.alloc(np));
+  HFX_CK(upload(d_items, items, s));
+  HFX_CK(upload(d_strides, strides, s));
+  std::vector<long long> offv(out_off, out_off + n);
+  HFX_CK(upload(d_off, offv, s));
+  k_pair_build<<<blocks_for(np, 128), 128, 0, s>>>(np, d_list.p, b->sh_xyz.p, b->sh_l.p, b->sh_poff.p, b->alpha.p,
+                                                   b->coef.p, stride, 0.0, pairs.p, prims.p, pclass.p);
+  for (int cls = 0; cls < HFX_NCLASS; ++cls) {
+    EvalArgs a;
+    a.pairs = pairs.p;
+    a.prims = prims.p;
+    a.quartets = d_items.p;
+    a.out_off = d_off.p;
+    a.strides = d_strides.p;
+    a.n = n;
+    a.cls = cls;
+    a.boys = b->boys.p;
+    a.kernel = kernel;
+    a.omega2 = omega * omega;
+    a.out = out;
+    kClassOps[cls].launch_eval(a, precision == HFX_PREC_MIXED, s);
+  }
+  HFX_CK(cudaGetLastError());
+  HFX_CK(cudaStreamSynchronize(s));
+  return HFX_OK;
+}
+
+hfx_status hfx_get_stats(const hfx_quartets* q, hfx_stats* out) {
+  if (!q || !out) return fail(HFX_ERR_INVALID_ARG, "NULL argument");
+  std::memset(out, 0, sizeof(*out));
+  HFX_CK(cudaDeviceSynchronize());
+  unsigned long long done[4 * HFX_NCLASS];
+  HFX_CK(cudaMemcpy(done, q->n_done.p, sizeof(done), cudaMemcpyDeviceToHost));
+  for (int c = 0; c < 6; ++c) out->n_pairs_significant[c] = q->n_pairs[c];
+  for (int c = 0; c < HFX_NCLASS; ++c) {
+    out->n_quartets_schwarz[c] = q->n_quartets[c];
+    for (int pass = 0; pass < 2; ++pass) {
+      const unsigned long long* d = done + 2 * (pass * HFX_NCLASS + c);
+      out->n_quartets_computed[c] += (long long)d[0];
+      out->n_quartets_pass[pass][c] = (long long)d[0];
+      out->n_prim_quartets_pass[pass][c] = (long long)d[1];
+      float ms = 0.f;
+      if (q->ran[pass][c] && cudaEventElapsedTime(&ms, q->evk[pass][c][0], q->evk[pass][c][1]) == cudaSuccess)
+        out->ms_class_pass[pass][c] = ms;
+    }
+  }
+  out->n_prim_pairs = q->n_prim_pairs;
+  out->n_values = q->n_values;
+  out->ms_setup = q->ms_setup;
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, q->ev0, q->ev1) == cudaSuccess) out->ms_last_build = ms;
+  cudaGetLastError();
+  return HFX_OK;
+}
+
+}  // extern "C"

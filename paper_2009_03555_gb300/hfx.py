@@ -1,0 +1,302 @@
+"""Thin ctypes binding of the HFX C ABI (include/hfx.h).
+
+Argument marshalling only: every step of the exchange build runs in the CUDA
+library ``libhfx.so`` built in-tree by ``paper_2009_03555_gb300/build.py``.
+PyTorch supplies device memory (tensors) and streams.  If the library is
+missing, loading fails loudly; there is no CPU fallback.
+
+The functions carry the C names (``hfx_create_basis``, ``hfx_build_quartets``,
+``hfx_build_K``, ``hfx_exchange_energy``, ...).  ``Basis`` and ``Quartets``
+own the handles and release them.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhfx.so")
+HEADER_PATH = os.path.join(os.path.dirname(_HERE), "include", "hfx.h")
+
+HFX_KERNEL_COULOMB, HFX_KERNEL_ERFC, HFX_KERNEL_ERF = 0, 1, 2
+HFX_PREC_FP64, HFX_PREC_MIXED = 0, 1
+N_CLASSES = 21
+PAIR_CLASS_NAMES = ["ss", "ps", "pp", "ds", "dp", "dd"]
+
+_STATUS = {0: "HFX_OK", 1: "HFX_ERR_INVALID_ARG", 2: "HFX_ERR_OOM", 3: "HFX_ERR_CUDA",
+           4: "HFX_ERR_UNSUPPORTED", 5: "HFX_ERR_TIMEOUT", 6: "HFX_ERR_BUSY"}
+
+
+class HFXError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class ShellDesc(ctypes.Structure):
+    _fields_ = [("l", ctypes.c_int), ("nprim", ctypes.c_int), ("atom", ctypes.c_int),
+                ("reserved", ctypes.c_int), ("alpha", ctypes.c_void_p), ("coef", ctypes.c_void_p)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int), ("omega", ctypes.c_double), ("screen", ctypes.c_int),
+                ("tau", ctypes.c_double), ("density_screen", ctypes.c_int), ("eps", ctypes.c_double),
+                ("prim_cutoff", ctypes.c_double), ("precision", ctypes.c_int),
+                ("fp64_promote_bound", ctypes.c_double), ("n_block", ctypes.c_int),
+                ("reserved", ctypes.c_int * 3)]
+
+
+class Pattern(ctypes.Structure):
+    _fields_ = [("n_atoms", ctypes.c_int), ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n_pairs_significant", ctypes.c_longlong * 6),
+                ("n_quartets_schwarz", ctypes.c_longlong * N_CLASSES),
+                ("n_quartets_computed", ctypes.c_longlong * N_CLASSES),
+                ("n_prim_pairs", ctypes.c_longlong), ("n_values", ctypes.c_longlong),
+                ("ms_setup", ctypes.c_float), ("ms_last_build", ctypes.c_float),
+                ("n_quartets_pass", (ctypes.c_longlong * N_CLASSES) * 2),
+                ("n_prim_quartets_pass", (ctypes.c_longlong * N_CLASSES) * 2),
+                ("ms_class_pass", (ctypes.c_float * N_CLASSES) * 2)]
+
+
+class ClassInfo(ctypes.Structure):
+    _fields_ = [("bra_class", ctypes.c_int), ("ket_class", ctypes.c_int), ("la", ctypes.c_int),
+                ("lb", ctypes.c_int), ("lc", ctypes.c_int), ("ld", ctypes.c_int), ("n_out", ctypes.c_int),
+                ("vrr_flops", ctypes.c_int), ("hrr_flops", ctypes.c_int)]
+
+
+EXPORTED = ["hfx_create_basis", "hfx_build_quartets", "hfx_value_count", "hfx_build_K", "hfx_exchange_energy",
+            "hfx_pack_dense", "hfx_unpack_dense", "hfx_eval_quartets", "hfx_get_stats", "hfx_get_class_info",
+            "hfx_destroy_basis", "hfx_destroy_quartets", "hfx_last_error"]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libhfx.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: run paper_2009_03555_gb300/build.py (or __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    V, I, D, LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+    PV = ctypes.POINTER(ctypes.c_void_p)
+    lib.hfx_create_basis.argtypes = [ctypes.POINTER(ShellDesc), I, V, I, V, PV]
+    lib.hfx_build_quartets.argtypes = [V, ctypes.POINTER(Opts), ctypes.POINTER(Pattern), V, PV]
+    lib.hfx_value_count.argtypes = [V]
+    lib.hfx_value_count.restype = LL
+    lib.hfx_build_K.argtypes = [V, V, V, V]
+    lib.hfx_exchange_energy.argtypes = [V, V, V, ctypes.POINTER(D), V]
+    lib.hfx_pack_dense.argtypes = [V, V, V, V]
+    lib.hfx_unpack_dense.argtypes = [V, V, V, V]
+    lib.hfx_eval_quartets.argtypes = [V, I, D, I, I, V, V, V, V]
+    lib.hfx_get_stats.argtypes = [V, ctypes.POINTER(Stats)]
+    lib.hfx_get_class_info.argtypes = [I, ctypes.POINTER(ClassInfo)]
+    lib.hfx_destroy_basis.argtypes = [V]
+    lib.hfx_destroy_basis.restype = None
+    lib.hfx_destroy_quartets.argtypes = [V]
+    lib.hfx_destroy_quartets.restype = None
+    lib.hfx_last_error.restype = ctypes.c_char_p
+    for name in EXPORTED:
+        if name not in ("hfx_value_count", "hfx_destroy_basis", "hfx_destroy_quartets", "hfx_last_error"):
+            getattr(lib, name).restype = I
+    _lib = lib
+    return lib
+
+
+def _check(status):
+    if status != 0:
+        raise HFXError(status, load().hfx_last_error().decode(errors="replace"))
+
+
+def _ptr(x):
+    """Device or host address of a torch tensor / numpy array (marshalling)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return ctypes.c_void_p(x.data_ptr())
+    return x.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except Exception:  # pragma: no cover
+            pass
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+# ----------------------------------------------------------------- C names
+def hfx_create_basis(shell_l, shell_atom, prim_off, alpha, coef, atom_xyz, stream=None):
+    """Shells from flat arrays (host numpy).  Returns the raw handle."""
+    lib = load()
+    n = len(shell_l)
+    alpha = np.ascontiguousarray(alpha, dtype=np.float64)
+    coef = np.ascontiguousarray(coef, dtype=np.float64)
+    xyz = np.ascontiguousarray(atom_xyz, dtype=np.float64)
+    descs = (ShellDesc * n)()
+    base_a, base_c = alpha.ctypes.data, coef.ctypes.data
+    for i in range(n):
+        p0, p1 = int(prim_off[i]), int(prim_off[i + 1])
+        descs[i].l = int(shell_l[i])
+        descs[i].nprim = p1 - p0
+        descs[i].atom = int(shell_atom[i])
+        descs[i].alpha = base_a + 8 * p0
+        descs[i].coef = base_c + 8 * p0
+    h = ctypes.c_void_p()
+    _check(lib.hfx_create_basis(descs, n, _ptr(xyz), int(xyz.shape[0]), _stream(stream), ctypes.byref(h)))
+    return h
+
+
+def make_opts(kernel=HFX_KERNEL_ERFC, omega=0.11, screen=True, tau=1e-8, density_screen=True, eps=None,
+              prim_cutoff=1e-14, precision=HFX_PREC_FP64, fp64_promote_bound=math.inf, n_block=128) -> Opts:
+    o = Opts()
+    o.kernel, o.omega, o.screen, o.tau = int(kernel), float(omega), int(bool(screen)), float(tau)
+    o.density_screen = int(bool(density_screen))
+    o.eps = float(tau if eps is None else eps)
+    o.prim_cutoff, o.precision = float(prim_cutoff), int(precision)
+    o.fp64_promote_bound, o.n_block = float(fp64_promote_bound), int(n_block)
+    return o
+
+
+def pattern_from_mask(mask):
+    """CSR arrays of a symmetric boolean atom-pair mask."""
+    mask = np.asarray(mask, dtype=bool)
+    rows = [np.nonzero(mask[i])[0] for i in range(mask.shape[0])]
+    row_ptr = np.zeros(mask.shape[0] + 1, dtype=np.int32)
+    row_ptr[1:] = np.cumsum([len(r) for r in rows])
+    col = np.ascontiguousarray(np.concatenate(rows).astype(np.int32)) if rows else np.zeros(0, np.int32)
+    return row_ptr, col
+
+
+def hfx_build_quartets(basis, opts: Opts, row_ptr, col, stream=None):
+    lib = load()
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    pat = Pattern(len(row_ptr) - 1, row_ptr.ctypes.data, col.ctypes.data)
+    h = ctypes.c_void_p()
+    _check(lib.hfx_build_quartets(basis, ctypes.byref(opts), ctypes.byref(pat), _stream(stream), ctypes.byref(h)))
+    return h
+
+
+def hfx_value_count(q) -> int:
+    return int(load().hfx_value_count(q))
+
+
+def hfx_build_K(q, P_val, K_val, stream=None):
+    _check(load().hfx_build_K(q, _ptr(P_val), _ptr(K_val), _stream(stream)))
+
+
+def hfx_exchange_energy(q, P_val, K_val, stream=None) -> float:
+    e = ctypes.c_double()
+    _check(load().hfx_exchange_energy(q, _ptr(P_val), _ptr(K_val), ctypes.byref(e), _stream(stream)))
+    return float(e.value)
+
+
+def hfx_pack_dense(q, dense, val, stream=None):
+    _check(load().hfx_pack_dense(q, _ptr(dense), _ptr(val), _stream(stream)))
+
+
+def hfx_unpack_dense(q, val, dense, stream=None):
+    _check(load().hfx_unpack_dense(q, _ptr(val), _ptr(dense), _stream(stream)))
+
+
+def hfx_eval_quartets(basis, kernel, omega, precision, quartets, out_off, out, stream=None):
+    q = np.ascontiguousarray(np.asarray(quartets, dtype=np.int32).reshape(-1, 4))
+    off = np.ascontiguousarray(out_off, dtype=np.int64)
+    _check(load().hfx_eval_quartets(basis, int(kernel), float(omega), int(precision), int(q.shape[0]),
+                                    _ptr(q), _ptr(off), _ptr(out), _stream(stream)))
+
+
+def hfx_get_stats(q) -> Stats:
+    st = Stats()
+    _check(load().hfx_get_stats(q, ctypes.byref(st)))
+    return st
+
+
+def hfx_get_class_info(cls) -> ClassInfo:
+    ci = ClassInfo()
+    _check(load().hfx_get_class_info(int(cls), ctypes.byref(ci)))
+    return ci
+
+
+def hfx_destroy_basis(h):
+    load().hfx_destroy_basis(h)
+
+
+def hfx_destroy_quartets(h):
+    load().hfx_destroy_quartets(h)
+
+
+# ----------------------------------------------------------------- owners
+class Basis:
+    """Owns an hfx_basis built from a system with flat shell arrays
+    (``shell_l``, ``shell_atom``, ``prim_off``, ``alpha``, ``coef``, ``atom_xyz``)."""
+
+    def __init__(self, system, stream=None):
+        self.system = system
+        self.nbf = int(system.n_bf)
+        self.handle = hfx_create_basis(system.shell_l, system.shell_atom, system.prim_off, system.alpha,
+                                       system.coef, system.atom_xyz, stream)
+
+    def eval_quartets(self, quartets, kernel=HFX_KERNEL_ERFC, omega=0.11, precision=HFX_PREC_FP64, stream=None):
+        import torch
+        q = np.asarray(quartets, dtype=np.int32).reshape(-1, 4)
+        nf = np.array([(int(l) + 1) * (int(l) + 2) // 2 for l in self.system.shell_l])
+        sizes = np.prod(nf[q], axis=1).astype(np.int64)
+        off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+        out = torch.zeros(int(off[-1]), dtype=torch.float64, device="cuda")
+        hfx_eval_quartets(self.handle, kernel, omega, precision, q, off[:-1], out, stream)
+        host = out.cpu().numpy()
+        return [host[off[i]:off[i + 1]].reshape(tuple(int(x) for x in nf[q[i]])) for i in range(q.shape[0])]
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and _lib is not None:
+            _lib.hfx_destroy_basis(h)
+            self.handle = None
+
+
+class Quartets:
+    """Owns an hfx_quartets (screened quartet lists + work queue) for one
+    basis, options and atom-pair pattern."""
+
+    def __init__(self, basis: Basis, opts: Opts, mask, stream=None):
+        self.basis = basis
+        self.opts = opts
+        row_ptr, col = pattern_from_mask(mask)
+        self.handle = hfx_build_quartets(basis.handle, opts, row_ptr, col, stream)
+        self.n_values = hfx_value_count(self.handle)
+
+    def build_K(self, P_val, K_val, stream=None):
+        hfx_build_K(self.handle, P_val, K_val, stream)
+
+    def exchange_energy(self, P_val, K_val, stream=None) -> float:
+        return hfx_exchange_energy(self.handle, P_val, K_val, stream)
+
+    def pack(self, dense, val, stream=None):
+        hfx_pack_dense(self.handle, dense, val, stream)
+
+    def unpack(self, val, dense, stream=None):
+        hfx_unpack_dense(self.handle, val, dense, stream)
+
+    def stats(self) -> Stats:
+        return hfx_get_stats(self.handle)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and _lib is not None:
+            _lib.hfx_destroy_quartets(h)
+            self.handle = None

@@ -1,0 +1,156 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances (stated by the method's accuracy target):
+  * FP64 path: |dK|max <= 1e-10 and |dE_x| <= 1e-9 * |E_x|;
+    individual integrals within 1e-12 of the largest integral of the quartet.
+  * mixed path (FP32 recursions, FP64 Boys/prefactors/accumulation):
+    |dE_x| <= 1e-6 Ha; integrals within 2e-5 relative to the quartet's largest.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_helpers import mask_dense, pattern_mask, run_gpu_K
+
+pytestmark = pytest.mark.gpu
+
+KMAP = {"coulomb": oracle.KERNEL_COULOMB, "erfc": oracle.KERNEL_ERFC, "erf": oracle.KERNEL_ERF}
+
+
+@pytest.fixture(scope="module")
+def ch3():
+    return synth.ch_cluster(3, 97, nprim=4)
+
+
+def _all_class_quartets(s, rng, per_class=3):
+    """Shell quartets covering every (la lb | lc ld) pattern in random orders."""
+    by = {l: [S for S in range(s.n_shells) if s.shell_l[S] == l] for l in (0, 1, 2)}
+    out = []
+    for la in range(3):
+        for lb in range(3):
+            for lc in range(3):
+                for ld in range(3):
+                    for _ in range(per_class):
+                        out.append(tuple(int(rng.choice(by[l])) for l in (la, lb, lc, ld)))
+    return out
+
+
+@pytest.mark.parametrize("kname", ["coulomb", "erfc", "erf"])
+def test_quartet_integrals_fp64(ch3, kname):
+    from paper_2009_03555_gb300 import hfx
+    rng = np.random.default_rng(21)
+    qs = _all_class_quartets(ch3, rng, per_class=2)
+    b = hfx.Basis(ch3)
+    got = b.eval_quartets(qs, kernel=KMAP[kname], omega=0.11, precision=hfx.HFX_PREC_FP64)
+    ref = oracle.quartets(oracle.Basis(ch3), qs, KMAP[kname], 0.11)
+    for q, g, r in zip(qs, got, ref):
+        scale = max(np.abs(r).max(), 1e-300)
+        assert np.abs(g - r).max() <= 1e-12 * max(scale, 1.0), (q, np.abs(g - r).max(), scale)
+
+
+def test_quartet_integrals_mixed(ch3):
+    from paper_2009_03555_gb300 import hfx
+    rng = np.random.default_rng(22)
+    qs = _all_class_quartets(ch3, rng, per_class=1)
+    b = hfx.Basis(ch3)
+    got = b.eval_quartets(qs, kernel=hfx.HFX_KERNEL_ERFC, omega=0.11, precision=hfx.HFX_PREC_MIXED)
+    ref = oracle.quartets(oracle.Basis(ch3), qs, oracle.KERNEL_ERFC, 0.11)
+    for q, g, r in zip(qs, got, ref):
+        scale = np.abs(r).max()
+        assert np.abs(g - r).max() <= 2e-5 * scale + 1e-12, (q, np.abs(g - r).max(), scale)
+
+
+def test_water_dimer_coulomb_fp64():
+    """Two water-like molecules, full Coulomb, no screening, dense P."""
+    s, P = synth.config0()
+    Kref, n = oracle.build_K(oracle.Basis(s), P)
+    K, E, q = run_gpu_K(s, P, kernel=0, screen=False, density_screen=False, prim_cutoff=0.0)
+    st = q.stats()
+    assert sum(st.n_quartets_computed) == n == 32131
+    assert np.abs(K - Kref).max() <= 1e-10
+    Eref = oracle.exchange_energy(P, Kref)
+    assert abs(E - Eref) <= 1e-9 * abs(Eref)
+    np.testing.assert_allclose(K, K.T, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("n_block", [1, 7, 128])
+def test_water_dimer_batch_sizes(n_block):
+    """The work-queue batch size must not change the result (ragged tails)."""
+    s, P = synth.config0()
+    Kref, _ = oracle.build_K(oracle.Basis(s), P)
+    K, _, _ = run_gpu_K(s, P, kernel=0, screen=False, density_screen=False, prim_cutoff=0.0, n_block=n_block)
+    assert np.abs(K - Kref).max() <= 1e-10
+
+
+@pytest.mark.parametrize("n_atoms,seed", [(3, 11), (5, 12)])
+def test_hse_cluster_screened_fp64(n_atoms, seed):
+    """C/H cluster with d shells, erfc kernel (w = 0.11), Schwarz 1e-8 and
+    density screening, P cut beyond 6 bohr (sparse pattern)."""
+    s = synth.ch_cluster(n_atoms, seed)
+    mask = pattern_mask(s, 6.0)
+    P = synth.density_matrix(s, seed) * mask_dense(s, mask)
+    kw = dict(kernel=oracle.KERNEL_ERFC, omega=0.11, screen=True, tau=1e-8, density_screen=True, eps=1e-8)
+    Kref, n = oracle.build_K(oracle.Basis(s), P, **kw)
+    K, E, q = run_gpu_K(s, P, mask=mask, prim_cutoff=1e-14, **kw)
+    md = mask_dense(s, mask)
+    assert np.abs((K - Kref) * md).max() <= 1e-10
+    assert np.all(K[md == 0] == 0)
+    assert sum(q.stats().n_quartets_computed) == n
+    Eref = oracle.exchange_energy(P, Kref)
+    assert abs(E - Eref) <= 1e-9 * abs(Eref)
+
+
+def test_hse_cluster_mixed_energy():
+    s = synth.ch_cluster(5, 12)
+    mask = pattern_mask(s, 6.0)
+    P = synth.density_matrix(s, 12) * mask_dense(s, mask)
+    kw = dict(kernel=oracle.KERNEL_ERFC, omega=0.11, screen=True, tau=1e-8, density_screen=True, eps=1e-8)
+    Kref, _ = oracle.build_K(oracle.Basis(s), P, **kw)
+    Eref = oracle.exchange_energy(P, Kref)
+    from paper_2009_03555_gb300 import hfx
+    K, E, _ = run_gpu_K(s, P, mask=mask, precision=hfx.HFX_PREC_MIXED, **kw)
+    assert abs(E - Eref) <= 1e-6
+    K2, E2, _ = run_gpu_K(s, P, mask=mask, precision=hfx.HFX_PREC_MIXED, fp64_promote_bound=1e-3, **kw)
+    assert abs(E2 - Eref) <= abs(E - Eref) + 1e-9
+
+
+def test_zero_density_gives_zero_K():
+    s, P = synth.config0()
+    K, E, q = run_gpu_K(s, np.zeros_like(P), kernel=0, screen=True, density_screen=True)
+    assert np.all(K == 0) and E == 0.0
+    assert sum(q.stats().n_quartets_computed) == 0
+
+
+def test_single_s_shell():
+    s = synth.System(name="one", atom_Z=np.array([1], dtype=np.int32), atom_xyz=np.zeros((1, 3)),
+                     shell_atom=np.array([0], dtype=np.int32), shell_l=np.array([0], dtype=np.int32),
+                     prim_off=np.array([0, 1], dtype=np.int32), alpha=np.array([0.7]), coef=np.array([1.0]))
+    P = np.array([[1.0]])
+    Kref, _ = oracle.build_K(oracle.Basis(s), P)
+    K, E, _ = run_gpu_K(s, P, kernel=0, screen=False, density_screen=False, prim_cutoff=0.0)
+    # (ss|ss) of one unit Gaussian charge: 2 sqrt(mu/pi), mu = (2a)(2a)/(4a) = a
+    assert K[0, 0] == pytest.approx(2.0 * np.sqrt(0.7 / np.pi), rel=1e-14)
+    assert K[0, 0] == pytest.approx(Kref[0, 0], rel=1e-14)
+
+
+def test_errors_are_reported():
+    from paper_2009_03555_gb300 import hfx
+    s = synth.ch_cluster(2, 5)
+    bad = synth.System(name="f", atom_Z=s.atom_Z, atom_xyz=s.atom_xyz, shell_atom=s.shell_atom,
+                       shell_l=np.where(s.shell_l == 2, 3, s.shell_l).astype(np.int32), prim_off=s.prim_off,
+                       alpha=s.alpha, coef=s.coef)
+    with pytest.raises(hfx.HFXError) as ei:
+        hfx.Basis(bad)
+    assert ei.value.status == 4
+    nan = synth.System(name="n", atom_Z=s.atom_Z, atom_xyz=s.atom_xyz, shell_atom=s.shell_atom,
+                       shell_l=s.shell_l, prim_off=s.prim_off, alpha=np.where(np.arange(len(s.alpha)) == 3,
+                                                                              np.nan, s.alpha), coef=s.coef)
+    with pytest.raises(hfx.HFXError) as ei:
+        hfx.Basis(nan)
+    assert ei.value.status == 1
+    b = hfx.Basis(s)
+    asym = np.array([[True, True], [False, True]])
+    with pytest.raises(hfx.HFXError) as ei:
+        hfx.Quartets(b, hfx.make_opts(), asym)
+    assert ei.value.status == 1
