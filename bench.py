@@ -217,6 +217,14 @@ def run_ours(args, rank, world):
                 "other_pipe_frac": round(min(u64, u32), 4),
                 "peak_source": "derived: 152 SMs x (128 FP32 | 2 FP64) FMA/clk x 2070 MHz",
                 "traffic": None, "launch_ms": round(t, 3), "share_of_build": round(t / st.ms_last_build, 4)}
+    per_class = []
+    for p in range(2):
+        for c in range(hfx.N_CLASSES):
+            if st.n_quartets_pass[p][c] > 0:
+                ci = hfx.hfx_get_class_info(c)
+                per_class.append({"class": f"({ci.la}{ci.lb}|{ci.lc}{ci.ld})", "pass": p,
+                                  "ms": round(st.ms_class_pass[p][c], 3), "quartets": int(st.n_quartets_pass[p][c]),
+                                  "prim_quartets": int(st.n_prim_quartets_pass[p][c])})
     n_q = int(sum(st.n_quartets_computed))
     n_pq = int(sum(st.n_prim_quartets_pass[0]) + sum(st.n_prim_quartets_pass[1]))
     res = {
@@ -234,7 +242,7 @@ def run_ours(args, rank, world):
         "E_x": E, "setup_ms": st.ms_setup,
         "gpu_launches": args.steps * (3 + sum(1 for p in range(2) for c in range(hfx.N_CLASSES)
                                             if st.n_quartets_pass[p][c] > 0 or st.ms_class_pass[p][c] > 0)),
-        "clocks": clocks, "e2e": e2e, "roofline": roof,
+        "clocks": clocks, "e2e": e2e, "roofline": roof, "per_class": per_class,
     }
     return res, s, q
 
@@ -307,7 +315,7 @@ def main():
     ap.add_argument("--atoms", type=int, default=400)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--promote", type=float, default=math.inf)
-    ap.add_argument("--prim-cutoff", type=float, default=1e-14)
+    ap.add_argument("--prim-cutoff", type=float, default=1e-13)
     ap.add_argument("--n-block", type=int, default=128)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)

@@ -76,7 +76,7 @@ typedef struct {
   double tau;                 /* Schwarz drop tolerance (Sec. 2, Eq. schwarz) */
   int density_screen;         /* 1: also require P_scr Q_IJ Q_KL > eps (Eq. dmscreening) */
   double eps;                 /* density-screening threshold */
-  double prim_cutoff;         /* drop primitive pairs whose self-repulsion estimate is below this (0: keep all) */
+  double prim_cutoff;         /* skip primitive quartets whose bound estimate product is below this (0: keep all) */
   int precision;              /* hfx_precision */
   double fp64_promote_bound;  /* MIXED: quartets with Q_IJ Q_KL P_scr above this run in FP64 */
   int n_block;                /* quartets per work-queue batch (the paper's n_block, Sec. 4); 0 = default */
@@ -159,6 +159,14 @@ hfx_status hfx_unpack_dense(const hfx_quartets* q, const double* val, double* de
  * Synchronises the stream. */
 hfx_status hfx_eval_quartets(hfx_basis* basis, int kernel, double omega, int precision, int n,
                              const int* quartets, const long long* out_off, double* out, void* stream);
+
+/* Boys function F_m(T) = int_0^1 t^{2m} exp(-T t^2) dt, m = 0..mmax (mmax <= 8),
+ * as the ERI kernels evaluate it (diagnostics and tests): precision FP64 uses
+ * the FP64 Taylor/downward-recursion evaluator, MIXED the double-single one.
+ * T: device array of n arguments (>= 0); F: device array of n x (mmax+1),
+ * row-major.  Synchronises the stream. */
+hfx_status hfx_boys_eval(hfx_basis* basis, int precision, int mmax, int n, const double* T, double* F,
+                         void* stream);
 
 /* Statistics (synchronises the device). */
 hfx_status hfx_get_stats(const hfx_quartets* q, hfx_stats* out);

@@ -1,21 +1,22 @@
 // eri_kernels.cuh -- per-class kernel templates of the HFX library:
 //   * k_build_K   persistent exchange-build kernel: warps pull quartet batches
-//                 from a device work queue (atomic counter), screen each
-//                 quartet, evaluate its contracted ERIs and scatter the four
-//                 exchange contributions into atom-pair-blocked K;
+//                 from a device work queue (atomic counter), screen the
+//                 quartets, compact the survivors so every lane works, evaluate
+//                 the contracted ERIs and scatter the four exchange
+//                 contributions into atom-pair-blocked K;
 //   * k_schwarz   Schwarz bounds Q_AB = sqrt(max |(ab|ab)|) of shell pairs;
 //   * k_eval      raw shell-quartet integrals (diagnostics and tests).
 // Included once per angular-momentum class by the generated tu_*.cu files.
 #pragma once
 #include <cuda_runtime.h>
 
+#include "boys_ds.cuh"
 #include "eri_common.cuh"
 
 namespace hfx {
 
 constexpr int kThreadsK = 128;
-
-enum Kernel { kCoulomb = 0, kErfc = 1, kErf = 2 };
+constexpr int kWarpsK = kThreadsK / 32;
 
 struct BuildArgs {
   const PairRec* bra_pairs;
@@ -26,13 +27,15 @@ struct BuildArgs {
   int n_desc;
   int* counter;           // work-queue head (zeroed before the launch)
   int same_class;         // bra class == ket class: canonical k >= bra rank
-  const double* boys;     // Boys table
+  const double* boys;     // Boys Taylor tables (FP64)
+  const float* boysf;     // the same tables as double-single (mixed path)
   int kernel;             // Kernel
   double omega2;          // omega^2 of the attenuated kernels
   int screen;             // Schwarz + P_scr > 0 tests on
   double tau;             // Schwarz threshold
   int dscreen;            // density screening on
   double eps;             // density-screening threshold
+  float eps_prim;         // primitive quartets with bound_ab bound_cd below this are skipped
   int route;              // 0: all quartets, 1: only bound <= promote, 2: only bound > promote
   double promote;         // FP64 promotion bound on Q_AB Q_CD P_scr
   const double* pmax;     // n_shells x n_shells shell-pair max |P|
@@ -68,91 +71,79 @@ struct EvalArgs {
   int n;
   int cls;
   const double* boys;
+  const float* boysf;
   int kernel;
   double omega2;
   double* out;
 };
 
-// Auxiliary integrals G_m = [00|00]^(m), m = 0..L, FP64.
-//   Coulomb: G_m = pref F_m(T)
-//   erf(w r)/r:  G_m = pref f^{m+1/2} F_m(f T),  f = w^2 / (w^2 + rho)
-//   erfc(w r)/r: Coulomb - erf   (Sec. 2, Eq. ERI-SR)
-template <int L>
-__device__ __forceinline__ void aux_integrals(const double* __restrict__ boys, int kernel, double omega2,
-                                              double T, double rho, double pref, double* G) {
-  double F[L + 1];
-  if (kernel != kErf) {
-    boys_fp64<L>(boys, T, F);
-    if (kernel == kCoulomb) {
-#pragma unroll
-      for (int m = 0; m <= L; ++m) G[m] = pref * F[m];
-      return;
-    }
-  }
-  const double f = omega2 * rcp_nr(omega2 + rho);
-  double Fw[L + 1];
-  boys_fp64<L>(boys, f * T, Fw);
-  double s = pref * (f * rsqrt_nr(f));
-  if (kernel == kErfc) {
-#pragma unroll
-    for (int m = 0; m <= L; ++m) {
-      G[m] = fma(-s, Fw[m], pref * F[m]);
-      s *= f;
-    }
-  } else {
-#pragma unroll
-    for (int m = 0; m <= L; ++m) {
-      G[m] = s * Fw[m];
-      s *= f;
-    }
-  }
-}
-
 // Contracted integrals (ab|cd) of one shell quartet into out[NOUT]
 // (index ((a NB + b) NC + c) ND + d).  The per-primitive-quartet prologue
-// (argument T, prefactor, Boys function) is FP64; the recursions, the
-// contraction and the horizontal recursion run in R.
+// (argument, prefactor, Boys function, erfc difference) is FP64; the
+// recursions, the contraction and the horizontal recursion run in R.
+// Primitive pairs are sorted by descending bound, so the loops stop at the
+// first primitive quartet whose bound product falls below eps_prim.
+// Returns the number of primitive quartets evaluated.
 template <class C, typename R>
-__device__ __forceinline__ void contracted_quartet(const PairRec& bra, const PrimPair* __restrict__ bprims,
-                                                   const PairRec& ket, const PrimPair* __restrict__ kprims,
-                                                   const double* __restrict__ boys, int kernel,
-                                                   double omega2, R* __restrict__ out) {
-  R acc[C::NACC];
+__device__ __forceinline__ int contracted_quartet(const PairRec& bra, const PrimPair* __restrict__ bprims,
+                                                  const PairRec& ket, const PrimPair* __restrict__ kprims,
+                                                  const double* __restrict__ boys,
+                                                  const float* __restrict__ boysf, int kernel, double omega2,
+                                                  float eps_prim, R* __restrict__ out) {
+  constexpr bool kMixed = sizeof(R) == 4;
+  constexpr int NR = kMixed ? 1 : 2;
+  R acc[C::NACC], comp[C::NACC];
 #pragma unroll
-  for (int i = 0; i < C::NACC; ++i) acc[i] = R(0);
+  for (int i = 0; i < C::NACC; ++i) {
+    acc[i] = R(0);
+    comp[i] = R(0);
+  }
+  int n = 0;
+  const float kmax = ket.pcnt > 0 ? kprims[ket.poff].bound : 0.f;
   for (int ib = 0; ib < bra.pcnt; ++ib) {
     const PrimPair pb = bprims[bra.poff + ib];
+    if (pb.bound * kmax < eps_prim) break;
     for (int ik = 0; ik < ket.pcnt; ++ik) {
       const PrimPair pk = kprims[ket.poff + ik];
-      const double s = pb.p + pk.p;
-      const double inv_s = rcp_nr(s);
-      const double rho = pb.p * pk.p * inv_s;
-      const double PQx = pb.P[0] - pk.P[0], PQy = pb.P[1] - pk.P[1], PQz = pb.P[2] - pk.P[2];
-      const double T = rho * fma(PQx, PQx, fma(PQy, PQy, PQz * PQz));
-      const double pref = kTwoPi52 * pb.kp * pk.kp * rsqrt_nr(s);
-      double Gd[C::L + 1];
-      aux_integrals<C::L>(boys, kernel, omega2, T, rho, pref, Gd);
-      R G[C::L + 1];
-#pragma unroll
-      for (int m = 0; m <= C::L; ++m) G[m] = R(Gd[m]);
+      if (pb.bound * pk.bound < eps_prim) break;
+      ++n;
+      R G[C::L + 1], PQ[3], rinv;
+      if constexpr (kMixed) {
+        prologue_ds<C::L>(boysf, kernel, omega2, pb, pk, G, rinv, PQ);
+      } else {
+        double inv_s;
+        prologue<C::L, NR>(boys, kernel, omega2, pb, pk, G, inv_s, PQ);
+        rinv = inv_s;
+      }
       VrrGeo<R> g;
-      const R rinv = R(inv_s);
-      const R rop = R(pk.p) * rinv, roq = R(pb.p) * rinv;
-      g.PA[0] = R(pb.PA[0]); g.PA[1] = R(pb.PA[1]); g.PA[2] = R(pb.PA[2]);
-      g.QC[0] = R(pk.PA[0]); g.QC[1] = R(pk.PA[1]); g.QC[2] = R(pk.PA[2]);
-      const R qx = R(PQx), qy = R(PQy), qz = R(PQz);
+      if constexpr (kMixed) {
+        g.PA[0] = pb.PAf[0]; g.PA[1] = pb.PAf[1]; g.PA[2] = pb.PAf[2];
+        g.QC[0] = pk.PAf[0]; g.QC[1] = pk.PAf[1]; g.QC[2] = pk.PAf[2];
+        g.oo2p = pb.oo2pf;
+        g.oo2q = pk.oo2pf;
+      } else {
+        g.PA[0] = pb.PA[0]; g.PA[1] = pb.PA[1]; g.PA[2] = pb.PA[2];
+        g.QC[0] = pk.PA[0]; g.QC[1] = pk.PA[1]; g.QC[2] = pk.PA[2];
+        g.oo2p = pb.oo2p;
+        g.oo2q = pk.oo2p;
+      }
+      const R rop = (kMixed ? R(pk.pf) : R(pk.p)) * rinv, roq = (kMixed ? R(pb.pf) : R(pb.p)) * rinv;
+      const R qx = PQ[0], qy = PQ[1], qz = PQ[2];
       g.WP[0] = -rop * qx; g.WP[1] = -rop * qy; g.WP[2] = -rop * qz;
       g.WQ[0] = roq * qx; g.WQ[1] = roq * qy; g.WQ[2] = roq * qz;
-      g.oo2p = R(pb.oo2p);
-      g.oo2q = R(pk.oo2p);
       g.oo2pq = R(0.5) * rinv;
       g.rop = rop;
       g.roq = roq;
-      C::template vrr<R>(G, g, acc);
+      C::template vrr<R>(G, g, acc, comp);
     }
+  }
+  if constexpr (kMixed) {
+#pragma unroll
+    for (int i = 0; i < C::NACC; ++i) acc[i] -= comp[i];
   }
   C::template hrr<R>(acc, R(bra.AB[0]), R(bra.AB[1]), R(bra.AB[2]), R(ket.AB[0]), R(ket.AB[1]),
                      R(ket.AB[2]), out);
+  return n;
 }
 
 // The four exchange contributions of canonical quartet (AB|CD) with integrals
@@ -241,18 +232,60 @@ __device__ __forceinline__ void scatter_K(const BuildArgs& a, int sA, int sB, in
   }
 }
 
+// Screening of quartet (bra | ket k) (Sec. 2: Eq. schwarz and Eq. dmscreening;
+// exact skip when every P block it touches is zero) and precision routing.
+__device__ __forceinline__ bool keep_quartet(const BuildArgs& a, const PairRec& bra, const PairRec& ket) {
+  const double qq = bra.Q * ket.Q;
+  double pscr = 0.0;
+  if (a.screen || a.route) {
+    const double* pm = a.pmax;
+    const int ns = a.ns;
+    pscr = fmax(fmax(__ldg(pm + bra.A * ns + ket.A), __ldg(pm + bra.A * ns + ket.B)),
+                fmax(__ldg(pm + bra.B * ns + ket.A), __ldg(pm + bra.B * ns + ket.B)));
+  }
+  if (a.screen) {
+    if (!(qq > a.tau) || !(pscr > 0.0)) return false;
+    if (a.dscreen && !(pscr * qq > a.eps)) return false;
+  }
+  if (a.route) {
+    const bool big = qq * pscr > a.promote;
+    return (a.route == 1) ? !big : big;
+  }
+  return true;
+}
+
 // Persistent exchange-build kernel for one quartet class.  The device work
 // queue replaces the paper's master/sub-master/worker message passing
 // (Sec. 3, Algorithms 1-3): lane 0 of a warp takes the next batch descriptor
-// with one atomicAdd on the queue head (the master's "send the indexes of the
-// batched ERIs"); the warp then hands the batch's quartets to its 32 lanes in
-// groups of 32 (the sub-master level); a head past the end is the terminal
-// token.  Each lane runs the body of Algorithm 4 for its quartet: screen,
-// compute the shell quartet, accumulate into K.
+// with one atomicAdd on the queue head (the master handing out the indexes of
+// the batched ERIs); a head past the end is the terminal token.  The warp
+// screens the batch's quartets 32 at a time and appends the survivors to a
+// per-warp queue in shared memory (ballot + prefix count); whenever 32 are
+// queued, each lane takes one and runs the body of Algorithm 4 for it
+// (compute the shell quartet, accumulate into K).  Lanes therefore never idle
+// on screened-out quartets.
 template <class C, typename R>
 __global__ void __launch_bounds__(kThreadsK) k_build_K(const BuildArgs a) {
+  __shared__ int2 s_queue[kWarpsK][64];
   const int lane = threadIdx.x & 31;
+  int2* Qw = s_queue[threadIdx.x >> 5];
+  int qn = 0;
   unsigned long long done = 0, pdone = 0;
+
+  auto process = [&](int2 it) {
+    const PairRec bra = a.bra_pairs[it.x];
+    const PairRec ket = a.ket_pairs[it.y];
+    double fac = 1.0;
+    if (bra.A == bra.B) fac *= 0.5;
+    if (ket.A == ket.B) fac *= 0.5;
+    if (a.same_class && it.x == it.y) fac *= 0.5;
+    R out[C::NOUT];
+    pdone += (unsigned long long)contracted_quartet<C, R>(bra, a.bra_prims, ket, a.ket_prims, a.boys, a.boysf,
+                                                          a.kernel, a.omega2, a.eps_prim, out);
+    scatter_K<C, R>(a, bra.A, bra.B, ket.A, ket.B, out, fac);
+    ++done;
+  };
+
   for (;;) {
     int d = 0;
     if (lane == 0) d = atomicAdd(a.counter, 1);
@@ -262,37 +295,23 @@ __global__ void __launch_bounds__(kThreadsK) k_build_K(const BuildArgs a) {
     const PairRec bra = a.bra_pairs[ds.bra];
     for (int kb = ds.k0; kb < ds.k1; kb += 32) {
       const int k = kb + lane;
-      if (k >= ds.k1) continue;
-      const PairRec ket = a.ket_pairs[k];
-      const double qq = bra.Q * ket.Q;
-      bool go = true;
-      double pscr = 0.0;
-      if (a.screen || a.route) {
-        const double* pm = a.pmax;
-        const int ns = a.ns;
-        pscr = fmax(fmax(pm[bra.A * ns + ket.A], pm[bra.A * ns + ket.B]),
-                    fmax(pm[bra.B * ns + ket.A], pm[bra.B * ns + ket.B]));
+      bool ok = false;
+      if (k < ds.k1) ok = keep_quartet(a, bra, a.ket_pairs[k]);
+      const unsigned m = __ballot_sync(0xffffffffu, ok);
+      if (ok) Qw[qn + __popc(m & ((1u << lane) - 1u))] = make_int2(ds.bra, k);
+      qn += __popc(m);
+      __syncwarp();
+      if (qn >= 32) {
+        const int2 it = Qw[lane];
+        __syncwarp();
+        if (lane < qn - 32) Qw[lane] = Qw[32 + lane];
+        __syncwarp();
+        qn -= 32;
+        process(it);
       }
-      if (a.screen) {
-        go = (qq > a.tau) && (pscr > 0.0);
-        if (go && a.dscreen) go = pscr * qq > a.eps;
-      }
-      if (go && a.route) {
-        const bool big = qq * pscr > a.promote;
-        go = (a.route == 1) ? !big : big;
-      }
-      if (!go) continue;
-      double fac = 1.0;
-      if (bra.A == bra.B) fac *= 0.5;
-      if (ket.A == ket.B) fac *= 0.5;
-      if (a.same_class && k == ds.bra) fac *= 0.5;
-      R out[C::NOUT];
-      contracted_quartet<C, R>(bra, a.bra_prims, ket, a.ket_prims, a.boys, a.kernel, a.omega2, out);
-      scatter_K<C, R>(a, bra.A, bra.B, ket.A, ket.B, out, fac);
-      ++done;
-      pdone += (unsigned long long)(bra.pcnt * ket.pcnt);
     }
   }
+  if (lane < qn) process(Qw[lane]);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     done += __shfl_down_sync(0xffffffffu, done, o);
@@ -304,8 +323,282 @@ __global__ void __launch_bounds__(kThreadsK) k_build_K(const BuildArgs a) {
   }
 }
 
+
+// ------------------------------------------------------------ cooperative
+// Classes with many contracted accumulators (d-shell quartets) run one warp
+// per shell quartet.  The 32 lanes compute the FP64 prologue of 32 primitive
+// quartets at once into a per-warp buffer; the warp then walks the vertical
+// recursion of each primitive quartet level by level (node tables emitted by
+// the generator, intermediates in shared memory), every lane owning a slice of
+// the contracted accumulators, which therefore stay in registers.  The
+// horizontal recursion and the four exchange contractions are spread over the
+// lanes the same way.
+constexpr int kThreadsCoop = 64;
+constexpr int kGeo = 17;  // PA[3] QC[3] WP[3] WQ[3] oo2p oo2q oo2pq rop roq
+
+template <class C, typename R>
+struct CoopLayout {
+  using T = typename C::Coop;
+  static constexpr int WS = 2 * T::VRR_SLOTS > T::HRR_SLOTS ? 2 * T::VRR_SLOTS : T::HRR_SLOTS;
+  static constexpr int PB = C::L + 1 + kGeo;              // prologue record per primitive quartet
+  static constexpr int PBUF = 32 * PB > 160 ? 32 * PB : 160;  // also holds the four P blocks
+  static constexpr int PER_WARP = WS + PBUF + 64;          // + geometry of the two current quartets
+  static constexpr int NPL = (C::NACC + 31) / 32;          // accumulators per lane
+  static constexpr size_t bytes() { return (size_t)(kThreadsCoop / 32) * PER_WARP * sizeof(R); }
+};
+
+template <class C, typename R>
+__device__ __forceinline__ void coop_quartet(const BuildArgs& a, int bi, int ki, R* ws, R* pbuf, R* sg,
+                                             unsigned long long& pdone) {
+  using T = typename C::Coop;
+  using Lay = CoopLayout<C, R>;
+  constexpr bool kMixed = sizeof(R) == 4;
+  constexpr int NR = kMixed ? 1 : 2;
+  constexpr int NG = C::L + 1;
+  const int lane = threadIdx.x & 31;
+  const PairRec bra = a.bra_pairs[bi], ket = a.ket_pairs[ki];
+  R acc[Lay::NPL], comp[Lay::NPL];
+#pragma unroll
+  for (int k = 0; k < Lay::NPL; ++k) {
+    acc[k] = R(0);
+    comp[k] = R(0);
+  }
+  const uint4* __restrict__ vrr = T::vrr();
+  const int* __restrict__ vlev = T::vlev();
+  const int* __restrict__ vsplit = T::vsplit();
+  const unsigned short* __restrict__ tgt = T::tgt();
+  const int nk = ket.pcnt, total = bra.pcnt * ket.pcnt;
+  for (int t0 = 0; t0 < total; t0 += 32) {
+    const int t = t0 + lane;
+    bool valid = false;
+    if (t < total) {
+      const int ib = t / nk, ik = t - ib * nk;
+      const PrimPair& pb = a.bra_prims[bra.poff + ib];
+      const PrimPair& pk = a.ket_prims[ket.poff + ik];
+      valid = pb.bound * pk.bound >= a.eps_prim;
+      if (valid) {
+        R* rec = pbuf + lane * Lay::PB;
+        R G[NG], PQ[3], rinv;
+        if constexpr (kMixed) {
+          prologue_ds<C::L>(a.boysf, a.kernel, a.omega2, pb, pk, G, rinv, PQ);
+        } else {
+          double inv_s;
+          prologue<C::L, NR>(a.boys, a.kernel, a.omega2, pb, pk, G, inv_s, PQ);
+          rinv = inv_s;
+        }
+#pragma unroll
+        for (int m = 0; m < NG; ++m) rec[m] = G[m];
+        R* geo = rec + NG;
+        const R rop = (kMixed ? R(pk.pf) : R(pk.p)) * rinv, roq = (kMixed ? R(pb.pf) : R(pb.p)) * rinv;
+#pragma unroll
+        for (int x = 0; x < 3; ++x) {
+          geo[x] = kMixed ? R(pb.PAf[x]) : R(pb.PA[x]);
+          geo[3 + x] = kMixed ? R(pk.PAf[x]) : R(pk.PA[x]);
+          geo[6 + x] = -rop * PQ[x];
+          geo[9 + x] = roq * PQ[x];
+        }
+        geo[12] = kMixed ? R(pb.oo2pf) : R(pb.oo2p);
+        geo[13] = kMixed ? R(pk.oo2pf) : R(pk.oo2p);
+        geo[14] = R(0.5) * rinv;
+        geo[15] = rop;
+        geo[16] = roq;
+      }
+    }
+    unsigned mask = __ballot_sync(0xffffffffu, valid);
+    __syncwarp();
+    pdone += __popc(mask);
+    // two primitive quartets per pass (two independent chains per node)
+    R* ws1 = ws + T::VRR_SLOTS;
+    while (mask) {
+      const int j0 = __ffs(mask) - 1;
+      mask &= mask - 1;
+      int j1 = -1;
+      if (mask) {
+        j1 = __ffs(mask) - 1;
+        mask &= mask - 1;
+      }
+      const R* rec0 = pbuf + j0 * Lay::PB;
+      const R* rec1 = pbuf + (j1 >= 0 ? j1 : j0) * Lay::PB;
+      const R live1 = j1 >= 0 ? R(1) : R(0);
+      if (lane < NG) {
+        ws[1 + lane] = rec0[lane];
+        ws1[1 + lane] = live1 * rec1[lane];
+      }
+      if (lane < kGeo) {
+        sg[lane] = rec0[NG + lane];
+        sg[32 + lane] = rec1[NG + lane];
+      }
+      if (lane == 0) {
+        ws[0] = R(0);
+        ws1[0] = R(0);
+      }
+      __syncwarp();
+      const R oo2pq0 = sg[14], oo2pq1 = sg[32 + 14];
+      const R h0b = sg[12], r0b = sg[15], h1b = sg[32 + 12], r1b = sg[32 + 15];
+      const R h0k = sg[13], r0k = sg[16], h1k = sg[32 + 13], r1k = sg[32 + 16];
+      for (int l = 1; l <= C::L; ++l) {
+        const int nb = __ldg(vlev + l), ns = __ldg(vsplit + l), n1 = __ldg(vlev + l + 1);
+        for (int n = nb + lane; n < ns; n += 32) {  // bra nodes: PA, WP, 1/(2p), rho/p
+          const uint4 x = __ldg(vrr + n);
+          const int axis = (x.x >> 18) & 3;
+          const R k1 = R((x.x >> 20) & 15);
+          const int s0 = x.y & 0xffff, s1 = x.y >> 16, s2 = x.z & 0xffff, s3 = x.z >> 16;
+          const R v0 = sg[axis] * ws[s0] + sg[6 + axis] * ws[s1] + k1 * h0b * (ws[s2] - r0b * ws[s3]);
+          const R v1 = sg[32 + axis] * ws1[s0] + sg[38 + axis] * ws1[s1] + k1 * h1b * (ws1[s2] - r1b * ws1[s3]);
+          ws[x.x & 0xffff] = v0;
+          ws1[x.x & 0xffff] = v1;
+        }
+        for (int n = ns + lane; n < n1; n += 32) {  // ket nodes: QC, WQ, 1/(2q), rho/q, 1/(2(p+q))
+          const uint4 x = __ldg(vrr + n);
+          const int axis = (x.x >> 18) & 3;
+          const R k1 = R((x.x >> 20) & 15), k2 = R((x.x >> 24) & 15);
+          const int s0 = x.y & 0xffff, s1 = x.y >> 16, s2 = x.z & 0xffff, s3 = x.z >> 16, s4 = x.w;
+          const R v0 = sg[3 + axis] * ws[s0] + sg[9 + axis] * ws[s1] + k1 * h0k * (ws[s2] - r0k * ws[s3]) +
+                       k2 * oo2pq0 * ws[s4];
+          const R v1 = sg[35 + axis] * ws1[s0] + sg[41 + axis] * ws1[s1] +
+                       k1 * h1k * (ws1[s2] - r1k * ws1[s3]) + k2 * oo2pq1 * ws1[s4];
+          ws[x.x & 0xffff] = v0;
+          ws1[x.x & 0xffff] = v1;
+        }
+        __syncwarp();
+      }
+#pragma unroll
+      for (int k = 0; k < Lay::NPL; ++k) {
+        const int tt = lane + 32 * k;
+        if (tt < C::NACC) {
+          const int sl = __ldg(tgt + tt);
+          kacc<R>(acc[k], comp[k], ws[sl]);
+          kacc<R>(acc[k], comp[k], ws1[sl]);
+        }
+      }
+      __syncwarp();
+    }
+  }
+  // contracted [e0|f0] into HRR slots 0..NACC-1
+#pragma unroll
+  for (int k = 0; k < Lay::NPL; ++k) {
+    const int tt = lane + 32 * k;
+    if (tt < C::NACC) ws[tt] = kMixed ? acc[k] - comp[k] : acc[k];
+  }
+  __syncwarp();
+  const uint4* __restrict__ hrr = T::hrr();
+  const int* __restrict__ hlev = T::hlev();
+  const R ab0 = R(bra.AB[0]), ab1 = R(bra.AB[1]), ab2 = R(bra.AB[2]);
+  const R cd0 = R(ket.AB[0]), cd1 = R(ket.AB[1]), cd2 = R(ket.AB[2]);
+  for (int l = 1; l <= T::N_HLEV; ++l) {
+    const int n1 = __ldg(hlev + l + 1);
+    for (int n = __ldg(hlev + l) + lane; n < n1; n += 32) {
+      const uint4 x = __ldg(hrr + n);
+      const int kind = (x.x >> 16) & 3, axis = (x.x >> 18) & 3;
+      const R c = (kind == 2) ? (axis == 0 ? ab0 : (axis == 1 ? ab1 : ab2))
+                              : (axis == 0 ? cd0 : (axis == 1 ? cd1 : cd2));
+      ws[x.x & 0xffff] = ws[x.y & 0xffff] + c * ws[x.y >> 16];
+    }
+    __syncwarp();
+  }
+  // four exchange contributions (see scatter_K), outputs spread over lanes
+  constexpr int NA = C::NA, NB = C::NB, NC = C::NC, ND = C::ND;
+  const unsigned short* __restrict__ outs = T::out();
+  double fac = 1.0;
+  if (bra.A == bra.B) fac *= 0.5;
+  if (ket.A == ket.B) fac *= 0.5;
+  if (a.same_class && bi == ki) fac *= 0.5;
+  const int na = a.n_atoms;
+  const int sA = bra.A, sB = bra.B, sC = ket.A, sD = ket.B;
+  const int atA = a.sh_atom[sA], atB = a.sh_atom[sB], atC = a.sh_atom[sC], atD = a.sh_atom[sD];
+  const int lA = a.sh_loc[sA], lB = a.sh_loc[sB], lC = a.sh_loc[sC], lD = a.sh_loc[sD];
+  const int nfC = a.atom_nf[atC], nfD = a.atom_nf[atD];
+  const long long oAC = a.blk_off[atA * na + atC], oAD = a.blk_off[atA * na + atD];
+  const long long oBC = a.blk_off[atB * na + atC], oBD = a.blk_off[atB * na + atD];
+  const bool h1 = oAC >= 0 && oBD >= 0, h2 = oBC >= 0 && oAD >= 0;
+  // P blocks into the (now free) prologue buffer: BD | AC | AD | BC
+  R* pBD = pbuf;
+  R* pAC = pBD + NB * ND;
+  R* pAD = pAC + NA * NC;
+  R* pBC = pAD + NA * ND;
+  for (int e = lane; e < NB * ND; e += 32)
+    pBD[e] = h1 ? R(__ldg(a.P + oBD + (long long)(lB + e / ND) * nfD + lD + e % ND)) : R(0);
+  for (int e = lane; e < NA * NC; e += 32)
+    pAC[e] = h1 ? R(__ldg(a.P + oAC + (long long)(lA + e / NC) * nfC + lC + e % NC)) : R(0);
+  for (int e = lane; e < NA * ND; e += 32)
+    pAD[e] = h2 ? R(__ldg(a.P + oAD + (long long)(lA + e / ND) * nfD + lD + e % ND)) : R(0);
+  for (int e = lane; e < NB * NC; e += 32)
+    pBC[e] = h2 ? R(__ldg(a.P + oBC + (long long)(lB + e / NC) * nfC + lC + e % NC)) : R(0);
+  __syncwarp();
+  constexpr int N1 = NA * NC, N2 = N1 + NB * ND, N3 = N2 + NB * NC, N4 = N3 + NA * ND;
+  for (int o = lane; o < N4; o += 32) {
+    R s = R(0);
+    if (o < N1) {  // K_AC[x][c] += sum_{b,d} g P_BD
+      if (!h1) continue;
+      const int x = o / NC, c = o % NC;
+      for (int b = 0; b < NB; ++b)
+        for (int d = 0; d < ND; ++d) s += ws[__ldg(outs + ((x * NB + b) * NC + c) * ND + d)] * pBD[b * ND + d];
+      atomicAdd(a.K + oAC + (long long)(lA + x) * nfC + lC + c, fac * (double)s);
+    } else if (o < N2) {  // K_BD[b][d] += sum_{x,c} g P_AC
+      if (!h1) continue;
+      const int b = (o - N1) / ND, d = (o - N1) % ND;
+      for (int x = 0; x < NA; ++x)
+        for (int c = 0; c < NC; ++c) s += ws[__ldg(outs + ((x * NB + b) * NC + c) * ND + d)] * pAC[x * NC + c];
+      atomicAdd(a.K + oBD + (long long)(lB + b) * nfD + lD + d, fac * (double)s);
+    } else if (o < N3) {  // K_BC[b][c] += sum_{x,d} g P_AD
+      if (!h2) continue;
+      const int b = (o - N2) / NC, c = (o - N2) % NC;
+      for (int x = 0; x < NA; ++x)
+        for (int d = 0; d < ND; ++d) s += ws[__ldg(outs + ((x * NB + b) * NC + c) * ND + d)] * pAD[x * ND + d];
+      atomicAdd(a.K + oBC + (long long)(lB + b) * nfC + lC + c, fac * (double)s);
+    } else {  // K_AD[x][d] += sum_{b,c} g P_BC
+      if (!h2) continue;
+      const int x = (o - N3) / ND, d = (o - N3) % ND;
+      for (int b = 0; b < NB; ++b)
+        for (int c = 0; c < NC; ++c) s += ws[__ldg(outs + ((x * NB + b) * NC + c) * ND + d)] * pBC[b * NC + c];
+      atomicAdd(a.K + oAD + (long long)(lA + x) * nfD + lD + d, fac * (double)s);
+    }
+  }
+  __syncwarp();
+}
+
+// Persistent cooperative kernel: same device work queue and screening as
+// k_build_K; the survivors of each 32-quartet screening round are processed
+// one after the other by the whole warp.
+template <class C, typename R>
+__global__ void __launch_bounds__(kThreadsCoop) k_build_K_coop(const BuildArgs a) {
+  using Lay = CoopLayout<C, R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  R* base = reinterpret_cast<R*>(smem_raw) + warp * Lay::PER_WARP;
+  R* ws = base;
+  R* pbuf = base + Lay::WS;
+  R* sg = pbuf + Lay::PBUF;
+  unsigned long long done = 0, pdone = 0;
+  for (;;) {
+    int d = 0;
+    if (lane == 0) d = atomicAdd(a.counter, 1);
+    d = __shfl_sync(0xffffffffu, d, 0);
+    if (d >= a.n_desc) break;
+    const Desc ds = a.desc[d];
+    const PairRec bra = a.bra_pairs[ds.bra];
+    for (int kb = ds.k0; kb < ds.k1; kb += 32) {
+      const int k = kb + lane;
+      bool ok = false;
+      if (k < ds.k1) ok = keep_quartet(a, bra, a.ket_pairs[k]);
+      unsigned m = __ballot_sync(0xffffffffu, ok);
+      done += __popc(m);
+      while (m) {
+        const int j = __ffs(m) - 1;
+        m &= m - 1;
+        coop_quartet<C, R>(a, ds.bra, kb + j, ws, pbuf, sg, pdone);
+      }
+    }
+  }
+  if (lane == 0 && done) {
+    atomicAdd(a.n_done, done);
+    atomicAdd(a.n_done + 1, pdone);
+  }
+}
+
 // Schwarz bounds of every shell pair of pair class `cls` (Sec. 2, Eq. schwarz):
-// Q_AB = sqrt(max_{a in A, b in B} |(ab|ab)|), FP64, with the run's kernel.
+// Q_AB = sqrt(max_{a in A, b in B} |(ab|ab)|), FP64, with the run's kernel and
+// every primitive quartet.
 template <class C>
 __global__ void __launch_bounds__(64) k_schwarz(const SchwarzArgs a) {
   if constexpr (C::bra_class == C::ket_class) {
@@ -313,7 +606,7 @@ __global__ void __launch_bounds__(64) k_schwarz(const SchwarzArgs a) {
     if (i >= a.n_pairs || a.pair_class[i] != a.cls) return;
     const PairRec pr = a.pairs[i];
     double out[C::NOUT];
-    contracted_quartet<C, double>(pr, a.prims, pr, a.prims, a.boys, a.kernel, a.omega2, out);
+    contracted_quartet<C, double>(pr, a.prims, pr, a.prims, a.boys, nullptr, a.kernel, a.omega2, 0.f, out);
     double mx = 0.0;
 #pragma unroll
     for (int x = 0; x < C::NA; ++x)
@@ -323,8 +616,9 @@ __global__ void __launch_bounds__(64) k_schwarz(const SchwarzArgs a) {
   }
 }
 
-// Raw integrals of listed quartets of this class, written with per-item strides
-// so the caller receives them in the shell order it asked for.
+// Raw integrals of listed quartets of this class (every primitive quartet),
+// written with per-item strides so the caller receives them in the shell
+// order it asked for.
 template <class C, typename R>
 __global__ void __launch_bounds__(64) k_eval(const EvalArgs a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -333,7 +627,7 @@ __global__ void __launch_bounds__(64) k_eval(const EvalArgs a) {
   if (q.z != a.cls) return;
   const PairRec bra = a.pairs[q.x], ket = a.pairs[q.y];
   R out[C::NOUT];
-  contracted_quartet<C, R>(bra, a.prims, ket, a.prims, a.boys, a.kernel, a.omega2, out);
+  contracted_quartet<C, R>(bra, a.prims, ket, a.prims, a.boys, a.boysf, a.kernel, a.omega2, 0.f, out);
   const int4 st = a.strides[i];
   double* o = a.out + a.out_off[i];
 #pragma unroll
@@ -348,22 +642,45 @@ __global__ void __launch_bounds__(64) k_eval(const EvalArgs a) {
 }
 
 // Host-side launchers, one set per class (declared in class_dispatch.h).
+template <class C, typename R>
+void launch_build_K_t(const BuildArgs& a, int grid, cudaStream_t s) {
+  if constexpr (C::COOP) {
+    const size_t sm = CoopLayout<C, R>::bytes();
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_build_K_coop<C, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      attr = true;
+    }
+    k_build_K_coop<C, R><<<grid, kThreadsCoop, sm, s>>>(a);
+  } else {
+    k_build_K<C, R><<<grid, kThreadsK, 0, s>>>(a);
+  }
+}
+
 template <class C>
 void launch_build_K(const BuildArgs& a, int fp32, int grid, cudaStream_t s) {
   if (fp32)
-    k_build_K<C, float><<<grid, kThreadsK, 0, s>>>(a);
+    launch_build_K_t<C, float>(a, grid, s);
   else
-    k_build_K<C, double><<<grid, kThreadsK, 0, s>>>(a);
+    launch_build_K_t<C, double>(a, grid, s);
+}
+
+template <class C, typename R>
+int occupancy_build_K_t() {
+  int nb = 0;
+  if constexpr (C::COOP) {
+    const size_t sm = CoopLayout<C, R>::bytes();
+    cudaFuncSetAttribute(k_build_K_coop<C, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_build_K_coop<C, R>, kThreadsCoop, sm);
+  } else {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_build_K<C, R>, kThreadsK, 0);
+  }
+  return nb < 1 ? 1 : nb;
 }
 
 template <class C>
 int occupancy_build_K(int fp32) {
-  int nb = 0;
-  if (fp32)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_build_K<C, float>, kThreadsK, 0);
-  else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_build_K<C, double>, kThreadsK, 0);
-  return nb < 1 ? 1 : nb;
+  return fp32 ? occupancy_build_K_t<C, float>() : occupancy_build_K_t<C, double>();
 }
 
 template <class C>

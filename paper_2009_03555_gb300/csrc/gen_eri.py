@@ -3,11 +3,13 @@
 For every canonical class (la lb | lc ld) of s/p/d shells (la >= lb, lc >= ld,
 bra pair class >= ket pair class: 21 classes) it emits a traits struct with
 
-  vrr<R>(G, geo, acc)   Obara-Saika / Head-Gordon-Pople vertical recursion for
+  vrr<R>(G, geo, acc, comp)
+                        Obara-Saika / Head-Gordon-Pople vertical recursion for
                         one primitive quartet: builds [e0|f0]^(0) for
                         |e| in [la, la+lb], |f| in [lc, lc+ld] from the
                         auxiliary integrals G_m = [00|00]^(m), m = 0..L, and
-                        adds them into the contracted accumulators acc.
+                        adds them into the contracted accumulators acc
+                        (compensated summation with comp in FP32).
   hrr<R>(acc, AB, CD, out)
                         horizontal recursion on the contracted integrals,
                         (a,b+1_i| = (a+1_i,b| + AB_i (a,b|, first on the bra
@@ -140,7 +142,7 @@ class VRR:
         for ie, e in enumerate(self.E):
             for jf, f in enumerate(self.F):
                 nm = self.node(e, f, 0)
-                acc_lines.append(f"    acc[{ie * nf + jf}] += {nm};")
+                acc_lines.append(f"    kacc<R>(acc[{ie * nf + jf}], comp[{ie * nf + jf}], {nm});")
                 self.flops += 1
         return self.lines + acc_lines
 
@@ -219,7 +221,13 @@ def gen_class(ib, ik, la, lb, lc, ld):
     name = f"Cls{la}{lb}{lc}{ld}"
     NA, NB, NC, ND = (len(comps(x)) for x in (la, lb, lc, ld))
     src = []
+    coop = len(v.E) * len(v.F) >= COOP_MIN_ACC
+    if coop:
+        src.append(emit_coop(name, coop_tables(la, lb, lc, ld)))
     src.append(f"struct {name} {{")
+    src.append(f"  static constexpr bool COOP = {'true' if coop else 'false'};")
+    if coop:
+        src.append(f"  using Coop = {name}Coop;")
     src.append(f"  static constexpr int la = {la}, lb = {lb}, lc = {lc}, ld = {ld};")
     src.append(f"  static constexpr int bra_class = {ib}, ket_class = {ik};")
     src.append(f"  static constexpr int L = {la + lb + lc + ld};")
@@ -229,7 +237,8 @@ def gen_class(ib, ik, la, lb, lc, ld):
     src.append(f"  static constexpr int VRR_FLOPS = {v.flops}, HRR_FLOPS = {h.flops};")
     inl = "__forceinline__" if len(v.E) * len(v.F) <= INLINE_MAX_ACC else "__noinline__"
     src.append("  template <typename R>")
-    src.append(f"  __device__ {inl} static void vrr(const R* __restrict__ G, const VrrGeo<R>& g, R* __restrict__ acc) {{")
+    src.append(f"  __device__ {inl} static void vrr(const R* __restrict__ G, const VrrGeo<R>& g, R* __restrict__ acc,")
+    src.append("                                  R* __restrict__ comp) {")
     src.append("    const R PAx = g.PA[0], PAy = g.PA[1], PAz = g.PA[2];")
     src.append("    const R QCx = g.QC[0], QCy = g.QC[1], QCz = g.QC[2];")
     src.append("    const R WPx = g.WP[0], WPy = g.WP[1], WPz = g.WP[2];")
@@ -317,6 +326,186 @@ def _write_if_changed(path, text):
                 return
     with open(path, "w") as fh:
         fh.write(text)
+
+
+
+
+# ---------------------------------------------------------------- cooperative
+# Large classes run the recursions cooperatively: one warp per contracted
+# quartet, intermediates in shared memory, the DAG evaluated level by level
+# from node tables.  A node is four 32-bit words:
+#   x: dst | kind << 16 | axis << 18 | k1 << 20 | k2 << 24
+#   y: s0 | s1 << 16,  z: s2 | s3 << 16,  w: s4
+# kind 0 (bra VRR):  v = PA_i s0 + WP_i s1 + k1/(2p) (s2 - rho/p s3)
+# kind 1 (ket VRR):  v = QC_i s0 + WQ_i s1 + k1/(2q) (s2 - rho/q s3) + k2/(2(p+q)) s4
+# kind 2 (bra HRR):  v = s0 + AB_i s1;   kind 3 (ket HRR): v = s0 + CD_i s1
+# VRR slots: 0 = constant zero, 1..L+1 = G_0..G_L, then nodes by level
+# (level = |e| + |f|).  HRR slots: 0..NACC-1 = contracted [e0|f0], then nodes.
+COOP_MIN_ACC = 180
+
+
+def coop_tables(la, lb, lc, ld):
+    v = VRR(la, lb, lc, ld)
+    L = la + lb + lc + ld
+    recs = {}  # (e, f, m) -> (kind, axis, k1, k2, srcs)
+
+    def build(e, f, m):
+        key = (e, f, m)
+        if key in recs or (sum(e) == 0 and sum(f) == 0):
+            return
+        if sum(f) > 0:
+            i = next(k for k in range(3) if f[k] > 0)
+            f1 = _sub(f, i)
+            srcs = [(e, f1, m), (e, f1, m + 1), None, None, None]
+            k1 = f1[i]
+            if k1 > 0:
+                srcs[2], srcs[3] = (e, _sub(f1, i), m), (e, _sub(f1, i), m + 1)
+            k2 = e[i]
+            if k2 > 0:
+                srcs[4] = (_sub(e, i), f1, m + 1)
+            recs[key] = (1, i, k1, k2, srcs)
+        else:
+            i = next(k for k in range(3) if e[k] > 0)
+            e1 = _sub(e, i)
+            srcs = [(e1, f, m), (e1, f, m + 1), None, None, None]
+            k1 = e1[i]
+            if k1 > 0:
+                srcs[2], srcs[3] = (_sub(e1, i), f, m), (_sub(e1, i), f, m + 1)
+            recs[key] = (0, i, k1, 0, srcs)
+        for s in recs[key][4]:
+            if s is not None:
+                build(*s)
+
+    for e in v.E:
+        for f in v.F:
+            build(e, f, 0)
+    slot = {}
+    order = sorted(recs, key=lambda k: (sum(k[0]) + sum(k[1]), recs[k][0], k[2], k[0], k[1]))
+    base = L + 2
+    for n, k in enumerate(order):
+        slot[k] = base + n
+
+    def sidx(s):
+        if s is None:
+            return 0
+        e, f, m = s
+        if sum(e) == 0 and sum(f) == 0:
+            return 1 + m
+        return slot[s]
+
+    nodes, lev_off = [], [0] * (L + 2)
+    for k in order:
+        kind, axis, k1, k2, srcs = recs[k]
+        lev = sum(k[0]) + sum(k[1])
+        lev_off[lev + 1] = len(nodes) + 1
+        s = [sidx(x) for x in srcs]
+        nodes.append((slot[k] | kind << 16 | axis << 18 | k1 << 20 | k2 << 24, s[0] | s[1] << 16,
+                      s[2] | s[3] << 16, s[4]))
+    # level offsets: lev_off[l] = first node of level l (levels 1..L)
+    offs = [0] * (L + 2)
+    cnt = [0] * (L + 2)
+    for k in order:
+        cnt[sum(k[0]) + sum(k[1])] += 1
+    acc = 0
+    for l in range(L + 2):
+        offs[l] = acc
+        acc += cnt[l]
+    # first ket node of every level (bra nodes come first within a level)
+    split = list(offs)
+    for n, k in enumerate(order):
+        lev = sum(k[0]) + sum(k[1])
+        if recs[k][0] == 0:
+            split[lev] = n + 1
+    for l in range(L + 2):
+        split[l] = max(split[l], offs[l])
+    nf = len(v.F)
+    targets = [sidx((e, f, 0)) for e in v.E for f in v.F]
+    vrr_slots = base + len(order)
+    vrr_flops_n = v.flops if False else None
+    # horizontal recursion, bra then ket, as a DAG of kind-2/3 nodes
+    E, F = v.E, v.F
+    eidx = {e: i for i, e in enumerate(E)}
+    fidx = {f: i for i, f in enumerate(F)}
+    A_, B_, C_, D_ = comps(la), comps(lb), comps(lc), comps(ld)
+    hnodes, hslot = [], {}
+    nacc = len(E) * nf
+    nxt = [nacc]
+    hlev = {}
+
+    def bslot(a, b, jf):
+        if sum(b) == 0:
+            return eidx[a] * nf + jf
+        key = ("b", a, b, jf)
+        if key in hslot:
+            return hslot[key]
+        i = next(k for k in range(3) if b[k] > 0)
+        b1 = _sub(b, i)
+        x, y = bslot(_add(a, i), b1, jf), bslot(a, b1, jf)
+        hslot[key] = nxt[0]
+        nxt[0] += 1
+        hnodes.append(((hslot[key] | 2 << 16 | i << 18), x | y << 16, 0, 0, sum(b)))
+        return hslot[key]
+
+    def kslot(ia, ib, c, d):
+        if sum(d) == 0:
+            return bslot(A_[ia], B_[ib], fidx[c])
+        key = ("k", ia, ib, c, d)
+        if key in hslot:
+            return hslot[key]
+        i = next(k for k in range(3) if d[k] > 0)
+        d1 = _sub(d, i)
+        x, y = kslot(ia, ib, _add(c, i), d1), kslot(ia, ib, c, d1)
+        hslot[key] = nxt[0]
+        nxt[0] += 1
+        hnodes.append(((hslot[key] | 3 << 16 | i << 18), x | y << 16, 0, 0, lb + sum(d)))
+        return hslot[key]
+
+    outs = []
+    for ia in range(len(A_)):
+        for ib in range(len(B_)):
+            for c in C_:
+                for d in D_:
+                    outs.append(kslot(ia, ib, c, d))
+    # HRR levels: bra nodes by |b| (1..lb), then ket nodes by lb + |d|
+    nl = lb + ld
+    hcnt = [0] * (nl + 2)
+    for hn in hnodes:
+        hcnt[hn[4]] += 1
+    hnodes_sorted = sorted(hnodes, key=lambda hn: hn[4])
+    hoffs, acc = [0] * (nl + 2), 0
+    for l in range(nl + 2):
+        hoffs[l] = acc
+        acc += hcnt[l]
+    return dict(nodes=nodes, lev_off=offs, lev_split=split, targets=targets, vrr_slots=vrr_slots,
+                hnodes=[hn[:4] for hn in hnodes_sorted], hlev_off=hoffs, n_hlev=nl,
+                hrr_slots=nxt[0], outs=outs, nacc=nacc)
+
+
+def emit_coop(name, t):
+    def arr(tp, nm, vals):
+        body = ", ".join(str(x) for x in vals) if vals else "0"
+        return f"__device__ const {tp} {nm}[] = {{{body}}};"
+
+    def arr4(nm, vals):
+        body = ", ".join(f"{{{a}u, {b}u, {c}u, {d}u}}" for (a, b, c, d) in vals) if vals else "{0u, 0u, 0u, 0u}"
+        return f"__device__ const uint4 {nm}[] = {{{body}}};"
+
+    lines = [arr4(f"k{name}_vrr", t["nodes"]), arr("int", f"k{name}_vlev", t["lev_off"]),
+             arr("int", f"k{name}_vsplit", t["lev_split"]),
+             arr("unsigned short", f"k{name}_tgt", t["targets"]), arr4(f"k{name}_hrr", t["hnodes"]),
+             arr("int", f"k{name}_hlev", t["hlev_off"]), arr("unsigned short", f"k{name}_out", t["outs"])]
+    lines.append(f"struct {name}Coop {{")
+    lines.append(f"  static constexpr int VRR_SLOTS = {t['vrr_slots']}, HRR_SLOTS = {t['hrr_slots']};")
+    lines.append(f"  static constexpr int N_VLEV = {len(t['lev_off']) - 1}, N_HLEV = {t['n_hlev']};")
+    lines.append(f"  __device__ static const uint4* vrr() {{ return k{name}_vrr; }}")
+    lines.append(f"  __device__ static const int* vlev() {{ return k{name}_vlev; }}")
+    lines.append(f"  __device__ static const int* vsplit() {{ return k{name}_vsplit; }}")
+    lines.append(f"  __device__ static const unsigned short* tgt() {{ return k{name}_tgt; }}")
+    lines.append(f"  __device__ static const uint4* hrr() {{ return k{name}_hrr; }}")
+    lines.append(f"  __device__ static const int* hlev() {{ return k{name}_hlev; }}")
+    lines.append(f"  __device__ static const unsigned short* out() {{ return k{name}_out; }}")
+    lines.append("};")
+    return "\n".join(lines)
 
 
 if __name__ == "__main__":

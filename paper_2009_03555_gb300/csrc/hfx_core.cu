@@ -60,6 +60,9 @@ struct DBuf {
 };
 
 static inline int ncart(int l) { return (l + 1) * (l + 2) / 2; }
+// Primitive pairs whose bound estimate is below this are dropped when pairs are
+// built (far below any quartet threshold; keeps FP32 bound products finite).
+static constexpr double kPairDropBound = 1e-24;
 static inline int pair_class_of(int la, int lb) { return la * (la + 1) / 2 + lb; }  // la >= lb
 static inline int quartet_class_of(int cb, int ck) { return cb * (cb + 1) / 2 + ck; }  // cb >= ck
 static inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -71,6 +74,7 @@ struct hfx_basis_s {
   std::vector<int> h_l, h_atom, h_np, h_poff, h_loc, h_atom_nf;
   std::vector<long long> h_sh_foff, h_atom_foff;
   DBuf<double> sh_xyz, alpha, coef, boys;
+  DBuf<float> boysf;
   DBuf<int> sh_l, sh_atom, sh_poff, sh_loc, atom_nf;
 };
 
@@ -115,25 +119,54 @@ struct hfx_quartets_s {
 };
 
 // ------------------------------------------------------------------ kernels
-// Boys table: F_m(T_k), T_k = k/16, m = 0..14, by the power series
-// F_m(T) = exp(-T) sum_k (2T)^k / ((2m+1)(2m+3)...(2m+2k+1)) (all terms
-// positive); column 15 holds exp(-T_k).
+// Boys Taylor tables: for top order L = 0..8 and T_k = k/16, the coefficients
+// F_{L+j}(T_k) / j!, j = 0..6, and exp(-T_k).  F_m by the power series
+// F_m(T) = exp(-T) sum_k (2T)^k / ((2m+1)(2m+3)...(2m+2k+1)) (all terms positive).
 __global__ void k_boys_table(double* tab) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= kBoysNT * kBoysCols) return;
-  const int it = i / kBoysCols, m = i % kBoysCols;
+  if (i >= kBoysNL * kBoysNT * kBoysCols) return;
+  const int col = i % kBoysCols, it = (i / kBoysCols) % kBoysNT, L = i / (kBoysCols * kBoysNT);
   const double T = it * kBoysStep;
-  if (m == kBoysCols - 1) {
+  if (col == kBoysCols - 1) {
     tab[i] = exp(-T);
     return;
   }
+  const int m = L + col;
   double term = 1.0 / (2 * m + 1), sum = term;
   for (int k = 1; k < 2000; ++k) {
     term *= 2.0 * T / (2 * m + 2 * k + 1);
     sum += term;
     if (term < 1e-18 * sum) break;
   }
-  tab[i] = exp(-T) * sum;
+  double fact = 1.0;
+  for (int j = 2; j <= col; ++j) fact *= j;
+  tab[i] = exp(-T) * sum / fact;
+}
+
+// Double-single copy of the Boys tables (hi = fl(v), lo = fl(v - hi)).
+__global__ void k_boys_split(const double* tab, float* tabf, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float h = (float)tab[i];
+  tabf[2 * i] = h;
+  tabf[2 * i + 1] = (float)(tab[i] - (double)h);
+}
+
+// F_0..F_L of the device evaluators at given arguments (diagnostics, tests).
+template <int L>
+__global__ void k_boys_eval(const double* tab, const float* tabf, int ds_path, int n, const double* T,
+                            double* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (ds_path) {
+    ds F[L + 1];
+    boys_ds<L>(tabf, ds_from_double(T[i]), F);
+    for (int m = 0; m <= L; ++m) out[(size_t)i * (L + 1) + m] = (double)F[m].hi + (double)F[m].lo;
+  } else {
+    double F[L + 1];
+    boys_fp64<L, 2>(tab, T[i], F);
+    for (int m = 0; m <= L; ++m) out[(size_t)i * (L + 1) + m] = F[m];
+  }
 }
 
 // Contraction coefficients: axial primitive normalisation
@@ -158,10 +191,12 @@ __global__ void k_normalize(int ns, const int* l, const int* poff, const double*
   for (int k = p0; k < p1; ++k) coef[k] *= sc;
 }
 
-// Shell-pair records (Sec. 2: shell pairs; Gaussian product theorem) for a list
-// of oriented pairs (l_A >= l_B).  Primitive pairs whose self-repulsion
-// estimate |c_a c_b K_ab| sqrt(2 pi^{5/2} / (p^2 sqrt(2p))) is below `cutoff`
-// are dropped.
+// Shell-pair records (Gaussian product theorem) for a list of oriented pairs
+// (l_A >= l_B).  Every primitive pair gets the estimate
+// bound = |c_a c_b K_ab| sqrt(2 pi^{5/2} / (p^2 sqrt(2p))) (the square root of
+// the s-type self-repulsion of the primitive product); pairs below `cutoff`
+// are dropped and the rest are sorted by descending bound, so the ERI kernels
+// can stop a primitive loop at the first negligible primitive quartet.
 __global__ void k_pair_build(int n, const int2* list, const double* xyz, const int* l, const int* poff,
                              const double* alpha, const double* coef, int stride, double cutoff, PairRec* out,
                              PrimPair* prims, int* pclass) {
@@ -178,6 +213,7 @@ __global__ void k_pair_build(int n, const int2* list, const double* xyz, const i
   r.AB[1] = Ay - By;
   r.AB[2] = Az - Bz;
   const double ab2 = r.AB[0] * r.AB[0] + r.AB[1] * r.AB[1] + r.AB[2] * r.AB[2];
+  PrimPair* dst = prims + (long long)i * stride;
   int cnt = 0;
   for (int ia = poff[A]; ia < poff[A + 1]; ++ia)
     for (int ib = poff[B]; ib < poff[B + 1]; ++ib) {
@@ -196,8 +232,25 @@ __global__ void k_pair_build(int n, const int2* list, const double* xyz, const i
       q.PA[0] = q.P[0] - Ax;
       q.PA[1] = q.P[1] - Ay;
       q.PA[2] = q.P[2] - Az;
-      q.bound = bound;
-      prims[(long long)i * stride + cnt] = q;
+      q.PAf[0] = (float)q.PA[0];
+      q.PAf[1] = (float)q.PA[1];
+      q.PAf[2] = (float)q.PA[2];
+      q.oo2pf = (float)q.oo2p;
+      q.pf = (float)p;
+      q.plo = (float)(p - (double)q.pf);
+      for (int x = 0; x < 3; ++x) {
+        q.Phi[x] = (float)q.P[x];
+        q.Plo[x] = (float)(q.P[x] - (double)q.Phi[x]);
+      }
+      q.kpf = (float)kp;
+      q.bound = (float)bound;
+      // insertion into the descending-bound order
+      int j = cnt;
+      while (j > 0 && dst[j - 1].bound < q.bound) {
+        dst[j] = dst[j - 1];
+        --j;
+      }
+      dst[j] = q;
       ++cnt;
     }
   r.pcnt = cnt;
@@ -498,13 +551,16 @@ hfx_status hfx_create_basis(const hfx_shell_desc* shells, int n_shells, const do
       (e = upload(b->coef, coef, s)) != cudaSuccess || (e = upload(b->sh_l, b->h_l, s)) != cudaSuccess ||
       (e = upload(b->sh_atom, b->h_atom, s)) != cudaSuccess || (e = upload(b->sh_poff, poff, s)) != cudaSuccess ||
       (e = upload(b->sh_loc, b->h_loc, s)) != cudaSuccess || (e = upload(b->atom_nf, b->h_atom_nf, s)) != cudaSuccess ||
-      (e = b->boys.alloc((size_t)kBoysNT * kBoysCols)) != cudaSuccess) {
+      (e = b->boys.alloc((size_t)kBoysNL * kBoysNT * kBoysCols)) != cudaSuccess ||
+      (e = b->boysf.alloc((size_t)2 * kBoysNL * kBoysNT * kBoysCols)) != cudaSuccess) {
     delete b;
     return fail(e == cudaErrorMemoryAllocation ? HFX_ERR_OOM : HFX_ERR_CUDA,
                 std::string("hfx_create_basis: ") + cudaGetErrorString(e));
   }
   k_normalize<<<blocks_for(n_shells, 128), 128, 0, s>>>(n_shells, b->sh_l.p, b->sh_poff.p, b->alpha.p, b->coef.p);
-  k_boys_table<<<blocks_for(kBoysNT * kBoysCols, 128), 128, 0, s>>>(b->boys.p);
+  k_boys_table<<<blocks_for(kBoysNL * kBoysNT * kBoysCols, 128), 128, 0, s>>>(b->boys.p);
+  k_boys_split<<<blocks_for(kBoysNL * kBoysNT * kBoysCols, 128), 128, 0, s>>>(b->boys.p, b->boysf.p,
+                                                                               kBoysNL * kBoysNT * kBoysCols);
   e = cudaStreamSynchronize(s);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -608,7 +664,7 @@ hfx_status hfx_build_quartets(hfx_basis* b, const hfx_opts* opts_in, const hfx_p
   HFX_CK(pclass.alloc(npair));
   HFX_CK(Q.alloc(npair));
   k_pair_build<<<blocks_for(npair, 128), 128, 0, s>>>(npair, d_list.p, b->sh_xyz.p, b->sh_l.p, b->sh_poff.p,
-                                                       b->alpha.p, b->coef.p, stride, o.prim_cutoff, all_pairs.p,
+                                                       b->alpha.p, b->coef.p, stride, kPairDropBound, all_pairs.p,
                                                        all_prims.p, pclass.p);
   HFX_CK(cudaGetLastError());
 
@@ -780,6 +836,7 @@ hfx_status hfx_build_K(hfx_quartets* q, const double* P, double* K, void* stream
     a.n_desc = q->n_desc[cls];
     a.same_class = cb == ck;
     a.boys = b->boys.p;
+    a.boysf = b->boysf.p;
     a.kernel = o.kernel;
     a.omega2 = o.omega * o.omega;
     a.screen = o.screen;
@@ -787,6 +844,7 @@ hfx_status hfx_build_K(hfx_quartets* q, const double* P, double* K, void* stream
     a.dscreen = o.density_screen;
     a.eps = o.eps;
     a.promote = o.fp64_promote_bound;
+    a.eps_prim = (float)o.prim_cutoff;
     a.pmax = q->pmax.p;
     a.ns = ns;
     a.P = P;
@@ -926,10 +984,34 @@ hfx_status hfx_eval_quartets(hfx_basis* b, int kernel, double omega, int precisi
     a.n = n;
     a.cls = cls;
     a.boys = b->boys.p;
+    a.boysf = b->boysf.p;
     a.kernel = kernel;
     a.omega2 = omega * omega;
     a.out = out;
     kClassOps[cls].launch_eval(a, precision == HFX_PREC_MIXED, s);
+  }
+  HFX_CK(cudaGetLastError());
+  HFX_CK(cudaStreamSynchronize(s));
+  return HFX_OK;
+}
+
+hfx_status hfx_boys_eval(hfx_basis* b, int precision, int mmax, int n, const double* T, double* F, void* stream) {
+  if (!b || (n > 0 && (!T || !F))) return fail(HFX_ERR_INVALID_ARG, "NULL argument");
+  if (mmax < 0 || mmax > kMaxLtot) return fail(HFX_ERR_INVALID_ARG, "mmax must be in 0..8");
+  if (n <= 0) return HFX_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int dsp = precision == HFX_PREC_MIXED;
+  const unsigned g = blocks_for(n, 128);
+  switch (mmax) {
+    case 0: k_boys_eval<0><<<g, 128, 0, s>>>(b->boys.p, b->boysf.p, dsp, n, T, F); break;
+    case 1: k_boys_eval<1><<<g, 128, 0, s>>>(b->boys.p, b->boysf.p, dsp, n, T, F); break;
+    case 2: k_boys_eval<2><<<g, 128, 0, s>>>(b->boys.p, b->boysf.p, dsp, n, T, F); break;
+    case 3: k_boys_eval<3><<<g, 128, 0, s>>>(b->boys.p, b->boysf.p, dsp, n, T, F); break;
+    case 4: k_boys_eval<4><<<g, 128, 0, s>>>(b->boys.p, b->boysf.p, dsp, n, T, F); break;
+    case 5: k_boys_eval<5><<<g, 128, 0, s>>>(b->boys.p, b->boysf.p, dsp, n, T, F); break;
+    case 6: k_boys_eval<6><<<g, 128, 0, s>>>(b->boys.p, b->boysf.p, dsp, n, T, F); break;
+    case 7: k_boys_eval<7><<<g, 128, 0, s>>>(b->boys.p, b->boysf.p, dsp, n, T, F); break;
+    default: k_boys_eval<8><<<g, 128, 0, s>>>(b->boys.p, b->boysf.p, dsp, n, T, F); break;
   }
   HFX_CK(cudaGetLastError());
   HFX_CK(cudaStreamSynchronize(s));

@@ -71,7 +71,8 @@ class ClassInfo(ctypes.Structure):
 
 
 EXPORTED = ["hfx_create_basis", "hfx_build_quartets", "hfx_value_count", "hfx_build_K", "hfx_exchange_energy",
-            "hfx_pack_dense", "hfx_unpack_dense", "hfx_eval_quartets", "hfx_get_stats", "hfx_get_class_info",
+            "hfx_pack_dense", "hfx_unpack_dense", "hfx_eval_quartets", "hfx_boys_eval", "hfx_get_stats",
+            "hfx_get_class_info",
             "hfx_destroy_basis", "hfx_destroy_quartets", "hfx_last_error"]
 
 _lib = None
@@ -96,6 +97,7 @@ def load(path: str = LIB_PATH):
     lib.hfx_pack_dense.argtypes = [V, V, V, V]
     lib.hfx_unpack_dense.argtypes = [V, V, V, V]
     lib.hfx_eval_quartets.argtypes = [V, I, D, I, I, V, V, V, V]
+    lib.hfx_boys_eval.argtypes = [V, I, I, I, V, V, V]
     lib.hfx_get_stats.argtypes = [V, ctypes.POINTER(Stats)]
     lib.hfx_get_class_info.argtypes = [I, ctypes.POINTER(ClassInfo)]
     lib.hfx_destroy_basis.argtypes = [V]
@@ -161,7 +163,7 @@ def hfx_create_basis(shell_l, shell_atom, prim_off, alpha, coef, atom_xyz, strea
 
 
 def make_opts(kernel=HFX_KERNEL_ERFC, omega=0.11, screen=True, tau=1e-8, density_screen=True, eps=None,
-              prim_cutoff=1e-14, precision=HFX_PREC_FP64, fp64_promote_bound=math.inf, n_block=128) -> Opts:
+              prim_cutoff=1e-15, precision=HFX_PREC_FP64, fp64_promote_bound=math.inf, n_block=128) -> Opts:
     o = Opts()
     o.kernel, o.omega, o.screen, o.tau = int(kernel), float(omega), int(bool(screen)), float(tau)
     o.density_screen = int(bool(density_screen))
@@ -220,6 +222,11 @@ def hfx_eval_quartets(basis, kernel, omega, precision, quartets, out_off, out, s
                                     _ptr(q), _ptr(off), _ptr(out), _stream(stream)))
 
 
+def hfx_boys_eval(basis, precision, mmax, T, F, stream=None):
+    _check(load().hfx_boys_eval(basis, int(precision), int(mmax), int(T.numel()), _ptr(T), _ptr(F),
+                                _stream(stream)))
+
+
 def hfx_get_stats(q) -> Stats:
     st = Stats()
     _check(load().hfx_get_stats(q, ctypes.byref(st)))
@@ -261,6 +268,14 @@ class Basis:
         hfx_eval_quartets(self.handle, kernel, omega, precision, q, off[:-1], out, stream)
         host = out.cpu().numpy()
         return [host[off[i]:off[i + 1]].reshape(tuple(int(x) for x in nf[q[i]])) for i in range(q.shape[0])]
+
+    def boys(self, T, mmax, precision=HFX_PREC_FP64, stream=None):
+        """F_0..F_mmax at the arguments T (numpy) from the device evaluators."""
+        import torch
+        Td = torch.as_tensor(np.ascontiguousarray(T, dtype=np.float64)).cuda()
+        Fd = torch.empty((Td.numel(), mmax + 1), dtype=torch.float64, device="cuda")
+        hfx_boys_eval(self.handle, precision, mmax, Td, Fd, stream)
+        return Fd.cpu().numpy()
 
     def __del__(self):
         h = getattr(self, "handle", None)
