@@ -32,7 +32,11 @@ def _sources():
 def _digest(src, extra):
     h = hashlib.sha256()
     h.update(" ".join(FLAGS + extra).encode())
-    for path in [src] + extra_headers():
+    own = [os.path.join(GEN, os.path.basename(src).replace("tu_", "cls_").replace(".cu", ".cuh"))]
+    own = [p for p in own if os.path.exists(p)]
+    if os.path.basename(src) == "hfx_core.cu":
+        own = sorted(os.path.join(GEN, f) for f in os.listdir(GEN) if f.endswith(".cuh"))
+    for path in [src] + own + extra_headers():
         with open(path, "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

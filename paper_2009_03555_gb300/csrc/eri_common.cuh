@@ -71,6 +71,25 @@ __device__ __forceinline__ void kacc<float>(float& s, float& c, float v) {
   s = t;
 }
 
+// Butterfly reduce-scatter over a warp: every lane contributes 32 values and on
+// return lane j holds the sum over the 32 lanes of v[j] (five exchange steps,
+// 31 shuffles per lane; v is clobbered).
+template <typename R>
+__device__ __forceinline__ R reduce_scatter32(R (&v)[32]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int sft = 16; sft >= 1; sft >>= 1) {
+    const bool up = (lane & sft) != 0;
+#pragma unroll
+    for (int i = 0; i < sft; ++i) {
+      const R send = up ? v[i] : v[i + sft];
+      const R keep = up ? v[i + sft] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, sft);
+    }
+  }
+  return v[0];
+}
+
 // ---------------------------------------------------------- Boys function
 // F_m(T) = int_0^1 t^{2m} exp(-T t^2) dt.  For every top order L = 0..8 the
 // table holds, on the grid T_k = k / 16 (k = 0..960, T <= 60), the Taylor

@@ -347,6 +347,91 @@ struct CoopLayout {
   static constexpr size_t bytes() { return (size_t)(kThreadsCoop / 32) * PER_WARP * sizeof(R); }
 };
 
+// Horizontal recursion (node tables, shared memory) on the contracted
+// [e0|f0] held in ws[0..NACC-1], then the four exchange contributions
+// (see scatter_K) spread over the lanes.  Whole warp.
+template <class C, typename R>
+__device__ __forceinline__ void quartet_epilogue(const BuildArgs& a, const PairRec& bra, const PairRec& ket,
+                                                 int bi, int ki, R* ws, R* pbuf) {
+  using T = typename C::Coop;
+  const int lane = threadIdx.x & 31;
+  const uint4* __restrict__ hrr = T::hrr();
+  const int* __restrict__ hlev = T::hlev();
+  const R ab0 = R(bra.AB[0]), ab1 = R(bra.AB[1]), ab2 = R(bra.AB[2]);
+  const R cd0 = R(ket.AB[0]), cd1 = R(ket.AB[1]), cd2 = R(ket.AB[2]);
+  for (int l = 1; l <= T::N_HLEV; ++l) {
+    const int n1 = __ldg(hlev + l + 1);
+    for (int n = __ldg(hlev + l) + lane; n < n1; n += 32) {
+      const uint4 x = __ldg(hrr + n);
+      const int kind = (x.x >> 16) & 3, axis = (x.x >> 18) & 3;
+      const R c = (kind == 2) ? (axis == 0 ? ab0 : (axis == 1 ? ab1 : ab2))
+                              : (axis == 0 ? cd0 : (axis == 1 ? cd1 : cd2));
+      ws[x.x & 0xffff] = ws[x.y & 0xffff] + c * ws[x.y >> 16];
+    }
+    __syncwarp();
+  }
+  // four exchange contributions (see scatter_K), outputs spread over lanes
+  constexpr int NA = C::NA, NB = C::NB, NC = C::NC, ND = C::ND;
+  const unsigned short* __restrict__ outs = T::out();
+  double fac = 1.0;
+  if (bra.A == bra.B) fac *= 0.5;
+  if (ket.A == ket.B) fac *= 0.5;
+  if (a.same_class && bi == ki) fac *= 0.5;
+  const int na = a.n_atoms;
+  const int sA = bra.A, sB = bra.B, sC = ket.A, sD = ket.B;
+  const int atA = a.sh_atom[sA], atB = a.sh_atom[sB], atC = a.sh_atom[sC], atD = a.sh_atom[sD];
+  const int lA = a.sh_loc[sA], lB = a.sh_loc[sB], lC = a.sh_loc[sC], lD = a.sh_loc[sD];
+  const int nfC = a.atom_nf[atC], nfD = a.atom_nf[atD];
+  const long long oAC = a.blk_off[atA * na + atC], oAD = a.blk_off[atA * na + atD];
+  const long long oBC = a.blk_off[atB * na + atC], oBD = a.blk_off[atB * na + atD];
+  const bool h1 = oAC >= 0 && oBD >= 0, h2 = oBC >= 0 && oAD >= 0;
+  // P blocks into the (now free) prologue buffer: BD | AC | AD | BC
+  R* pBD = pbuf;
+  R* pAC = pBD + NB * ND;
+  R* pAD = pAC + NA * NC;
+  R* pBC = pAD + NA * ND;
+  for (int e = lane; e < NB * ND; e += 32)
+    pBD[e] = h1 ? R(__ldg(a.P + oBD + (long long)(lB + e / ND) * nfD + lD + e % ND)) : R(0);
+  for (int e = lane; e < NA * NC; e += 32)
+    pAC[e] = h1 ? R(__ldg(a.P + oAC + (long long)(lA + e / NC) * nfC + lC + e % NC)) : R(0);
+  for (int e = lane; e < NA * ND; e += 32)
+    pAD[e] = h2 ? R(__ldg(a.P + oAD + (long long)(lA + e / ND) * nfD + lD + e % ND)) : R(0);
+  for (int e = lane; e < NB * NC; e += 32)
+    pBC[e] = h2 ? R(__ldg(a.P + oBC + (long long)(lB + e / NC) * nfC + lC + e % NC)) : R(0);
+  __syncwarp();
+  constexpr int N1 = NA * NC, N2 = N1 + NB * ND, N3 = N2 + NB * NC, N4 = N3 + NA * ND;
+  for (int o = lane; o < N4; o += 32) {
+    R s = R(0);
+    if (o < N1) {  // K_AC[x][c] += sum_{b,d} g P_BD
+      if (!h1) continue;
+      const int x = o / NC, c = o % NC;
+      for (int b = 0; b < NB; ++b)
+        for (int d = 0; d < ND; ++d) s += ws[__ldg(outs + ((x * NB + b) * NC + c) * ND + d)] * pBD[b * ND + d];
+      atomicAdd(a.K + oAC + (long long)(lA + x) * nfC + lC + c, fac * (double)s);
+    } else if (o < N2) {  // K_BD[b][d] += sum_{x,c} g P_AC
+      if (!h1) continue;
+      const int b = (o - N1) / ND, d = (o - N1) % ND;
+      for (int x = 0; x < NA; ++x)
+        for (int c = 0; c < NC; ++c) s += ws[__ldg(outs + ((x * NB + b) * NC + c) * ND + d)] * pAC[x * NC + c];
+      atomicAdd(a.K + oBD + (long long)(lB + b) * nfD + lD + d, fac * (double)s);
+    } else if (o < N3) {  // K_BC[b][c] += sum_{x,d} g P_AD
+      if (!h2) continue;
+      const int b = (o - N2) / NC, c = (o - N2) % NC;
+      for (int x = 0; x < NA; ++x)
+        for (int d = 0; d < ND; ++d) s += ws[__ldg(outs + ((x * NB + b) * NC + c) * ND + d)] * pAD[x * ND + d];
+      atomicAdd(a.K + oBC + (long long)(lB + b) * nfC + lC + c, fac * (double)s);
+    } else {  // K_AD[x][d] += sum_{b,c} g P_BC
+      if (!h2) continue;
+      const int x = (o - N3) / ND, d = (o - N3) % ND;
+      for (int b = 0; b < NB; ++b)
+        for (int c = 0; c < NC; ++c) s += ws[__ldg(outs + ((x * NB + b) * NC + c) * ND + d)] * pBC[b * NC + c];
+      atomicAdd(a.K + oAD + (long long)(lA + x) * nfD + lD + d, fac * (double)s);
+    }
+  }
+  __syncwarp();
+}
+
+
 template <class C, typename R>
 __device__ __forceinline__ void coop_quartet(const BuildArgs& a, int bi, int ki, R* ws, R* pbuf, R* sg,
                                              unsigned long long& pdone) {
@@ -481,80 +566,7 @@ __device__ __forceinline__ void coop_quartet(const BuildArgs& a, int bi, int ki,
     if (tt < C::NACC) ws[tt] = kMixed ? acc[k] - comp[k] : acc[k];
   }
   __syncwarp();
-  const uint4* __restrict__ hrr = T::hrr();
-  const int* __restrict__ hlev = T::hlev();
-  const R ab0 = R(bra.AB[0]), ab1 = R(bra.AB[1]), ab2 = R(bra.AB[2]);
-  const R cd0 = R(ket.AB[0]), cd1 = R(ket.AB[1]), cd2 = R(ket.AB[2]);
-  for (int l = 1; l <= T::N_HLEV; ++l) {
-    const int n1 = __ldg(hlev + l + 1);
-    for (int n = __ldg(hlev + l) + lane; n < n1; n += 32) {
-      const uint4 x = __ldg(hrr + n);
-      const int kind = (x.x >> 16) & 3, axis = (x.x >> 18) & 3;
-      const R c = (kind == 2) ? (axis == 0 ? ab0 : (axis == 1 ? ab1 : ab2))
-                              : (axis == 0 ? cd0 : (axis == 1 ? cd1 : cd2));
-      ws[x.x & 0xffff] = ws[x.y & 0xffff] + c * ws[x.y >> 16];
-    }
-    __syncwarp();
-  }
-  // four exchange contributions (see scatter_K), outputs spread over lanes
-  constexpr int NA = C::NA, NB = C::NB, NC = C::NC, ND = C::ND;
-  const unsigned short* __restrict__ outs = T::out();
-  double fac = 1.0;
-  if (bra.A == bra.B) fac *= 0.5;
-  if (ket.A == ket.B) fac *= 0.5;
-  if (a.same_class && bi == ki) fac *= 0.5;
-  const int na = a.n_atoms;
-  const int sA = bra.A, sB = bra.B, sC = ket.A, sD = ket.B;
-  const int atA = a.sh_atom[sA], atB = a.sh_atom[sB], atC = a.sh_atom[sC], atD = a.sh_atom[sD];
-  const int lA = a.sh_loc[sA], lB = a.sh_loc[sB], lC = a.sh_loc[sC], lD = a.sh_loc[sD];
-  const int nfC = a.atom_nf[atC], nfD = a.atom_nf[atD];
-  const long long oAC = a.blk_off[atA * na + atC], oAD = a.blk_off[atA * na + atD];
-  const long long oBC = a.blk_off[atB * na + atC], oBD = a.blk_off[atB * na + atD];
-  const bool h1 = oAC >= 0 && oBD >= 0, h2 = oBC >= 0 && oAD >= 0;
-  // P blocks into the (now free) prologue buffer: BD | AC | AD | BC
-  R* pBD = pbuf;
-  R* pAC = pBD + NB * ND;
-  R* pAD = pAC + NA * NC;
-  R* pBC = pAD + NA * ND;
-  for (int e = lane; e < NB * ND; e += 32)
-    pBD[e] = h1 ? R(__ldg(a.P + oBD + (long long)(lB + e / ND) * nfD + lD + e % ND)) : R(0);
-  for (int e = lane; e < NA * NC; e += 32)
-    pAC[e] = h1 ? R(__ldg(a.P + oAC + (long long)(lA + e / NC) * nfC + lC + e % NC)) : R(0);
-  for (int e = lane; e < NA * ND; e += 32)
-    pAD[e] = h2 ? R(__ldg(a.P + oAD + (long long)(lA + e / ND) * nfD + lD + e % ND)) : R(0);
-  for (int e = lane; e < NB * NC; e += 32)
-    pBC[e] = h2 ? R(__ldg(a.P + oBC + (long long)(lB + e / NC) * nfC + lC + e % NC)) : R(0);
-  __syncwarp();
-  constexpr int N1 = NA * NC, N2 = N1 + NB * ND, N3 = N2 + NB * NC, N4 = N3 + NA * ND;
-  for (int o = lane; o < N4; o += 32) {
-    R s = R(0);
-    if (o < N1) {  // K_AC[x][c] += sum_{b,d} g P_BD
-      if (!h1) continue;
-      const int x = o / NC, c = o % NC;
-      for (int b = 0; b < NB; ++b)
-        for (int d = 0; d < ND; ++d) s += ws[__ldg(outs + ((x * NB + b) * NC + c) * ND + d)] * pBD[b * ND + d];
-      atomicAdd(a.K + oAC + (long long)(lA + x) * nfC + lC + c, fac * (double)s);
-    } else if (o < N2) {  // K_BD[b][d] += sum_{x,c} g P_AC
-      if (!h1) continue;
-      const int b = (o - N1) / ND, d = (o - N1) % ND;
-      for (int x = 0; x < NA; ++x)
-        for (int c = 0; c < NC; ++c) s += ws[__ldg(outs + ((x * NB + b) * NC + c) * ND + d)] * pAC[x * NC + c];
-      atomicAdd(a.K + oBD + (long long)(lB + b) * nfD + lD + d, fac * (double)s);
-    } else if (o < N3) {  // K_BC[b][c] += sum_{x,d} g P_AD
-      if (!h2) continue;
-      const int b = (o - N2) / NC, c = (o - N2) % NC;
-      for (int x = 0; x < NA; ++x)
-        for (int d = 0; d < ND; ++d) s += ws[__ldg(outs + ((x * NB + b) * NC + c) * ND + d)] * pAD[x * ND + d];
-      atomicAdd(a.K + oBC + (long long)(lB + b) * nfC + lC + c, fac * (double)s);
-    } else {  // K_AD[x][d] += sum_{b,c} g P_BC
-      if (!h2) continue;
-      const int x = (o - N3) / ND, d = (o - N3) % ND;
-      for (int b = 0; b < NB; ++b)
-        for (int c = 0; c < NC; ++c) s += ws[__ldg(outs + ((x * NB + b) * NC + c) * ND + d)] * pBC[b * NC + c];
-      atomicAdd(a.K + oAD + (long long)(lA + x) * nfD + lD + d, fac * (double)s);
-    }
-  }
-  __syncwarp();
+  quartet_epilogue<C, R>(a, bra, ket, bi, ki, ws, pbuf);
 }
 
 // Persistent cooperative kernel: same device work queue and screening as
@@ -587,6 +599,147 @@ __global__ void __launch_bounds__(kThreadsCoop) k_build_K_coop(const BuildArgs a
         const int j = __ffs(m) - 1;
         m &= m - 1;
         coop_quartet<C, R>(a, ds.bra, kb + j, ws, pbuf, sg, pdone);
+      }
+    }
+  }
+  if (lane == 0 && done) {
+    atomicAdd(a.n_done, done);
+    atomicAdd(a.n_done + 1, pdone);
+  }
+}
+
+
+// ------------------------------------------------------------------ split
+// Classes with a medium-large accumulator set run one warp per shell quartet
+// with the lanes on different primitive quartets: every lane evaluates the
+// generated straight-line vertical recursion of its own primitive quartet and
+// the finished targets are reduced over the warp 32 at a time
+// (reduce_scatter32), so lane j keeps only the accumulators 32k + j.
+// Primitive quartets that survive the bound test are compacted into a
+// per-warp queue first, so passes run with full lanes.
+constexpr int kThreadsSplit = 128;
+
+template <class C, typename R>
+struct SplitLayout {
+  using T = typename C::Coop;
+  static constexpr int PER_WARP = T::HRR_SLOTS + 160;  // HRR workspace + four P blocks
+  static constexpr size_t bytes() { return (size_t)(kThreadsSplit / 32) * PER_WARP * sizeof(R); }
+};
+
+template <class C, typename R>
+__device__ __forceinline__ void split_quartet(const BuildArgs& a, int bi, int ki, R* ws, R* pbuf, int* pq,
+                                              unsigned long long& pdone) {
+  constexpr bool kMixed = sizeof(R) == 4;
+  constexpr int NR = kMixed ? 1 : 2;
+  constexpr int NG = C::L + 1;
+  const int lane = threadIdx.x & 31;
+  const PairRec bra = a.bra_pairs[bi], ket = a.ket_pairs[ki];
+  R acc[C::NCHUNK], comp[C::NCHUNK];
+#pragma unroll
+  for (int k = 0; k < C::NCHUNK; ++k) {
+    acc[k] = R(0);
+    comp[k] = R(0);
+  }
+  const int nk = ket.pcnt, total = bra.pcnt * ket.pcnt;
+  int t0 = 0, qn = 0;
+  for (;;) {
+    while (qn < 32 && t0 < total) {
+      const int t = t0 + lane;
+      bool valid = false;
+      if (t < total) {
+        const int ib = t / nk, ik = t - ib * nk;
+        valid = a.bra_prims[bra.poff + ib].bound * a.ket_prims[ket.poff + ik].bound >= a.eps_prim;
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, valid);
+      if (valid) pq[qn + __popc(m & ((1u << lane) - 1u))] = t;
+      qn += __popc(m);
+      t0 += 32;
+      __syncwarp();
+    }
+    if (qn == 0) break;
+    const int take = qn < 32 ? qn : 32;
+    const int t = lane < take ? pq[lane] : -1;
+    __syncwarp();
+    if (lane < qn - take) pq[lane] = pq[take + lane];
+    __syncwarp();
+    qn -= take;
+    pdone += take;
+    R G[NG], PQ[3] = {R(0), R(0), R(0)}, rinv = R(0);
+#pragma unroll
+    for (int m = 0; m < NG; ++m) G[m] = R(0);
+    VrrGeo<R> g;
+#pragma unroll
+    for (int x = 0; x < 3; ++x) g.PA[x] = g.QC[x] = R(0);
+    g.oo2p = g.oo2q = R(0);
+    R rop = R(0), roq = R(0);
+    if (t >= 0) {
+      const int ib = t / nk, ik = t - ib * nk;
+      const PrimPair& pb = a.bra_prims[bra.poff + ib];
+      const PrimPair& pk = a.ket_prims[ket.poff + ik];
+      if constexpr (kMixed) {
+        prologue_ds<C::L>(a.boysf, a.kernel, a.omega2, pb, pk, G, rinv, PQ);
+      } else {
+        double inv_s;
+        prologue<C::L, NR>(a.boys, a.kernel, a.omega2, pb, pk, G, inv_s, PQ);
+        rinv = inv_s;
+      }
+#pragma unroll
+      for (int x = 0; x < 3; ++x) {
+        g.PA[x] = kMixed ? R(pb.PAf[x]) : R(pb.PA[x]);
+        g.QC[x] = kMixed ? R(pk.PAf[x]) : R(pk.PA[x]);
+      }
+      g.oo2p = kMixed ? R(pb.oo2pf) : R(pb.oo2p);
+      g.oo2q = kMixed ? R(pk.oo2pf) : R(pk.oo2p);
+      rop = (kMixed ? R(pk.pf) : R(pk.p)) * rinv;
+      roq = (kMixed ? R(pb.pf) : R(pb.p)) * rinv;
+    }
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      g.WP[x] = -rop * PQ[x];
+      g.WQ[x] = roq * PQ[x];
+    }
+    g.oo2pq = R(0.5) * rinv;
+    g.rop = rop;
+    g.roq = roq;
+    C::template vrr_split<R>(G, g, acc, comp);
+  }
+  const unsigned short* __restrict__ perm = C::split_perm();
+#pragma unroll
+  for (int k = 0; k < C::NCHUNK; ++k) {
+    const int tt = lane + 32 * k;
+    if (tt < C::NACC) ws[perm[tt]] = kMixed ? acc[k] - comp[k] : acc[k];
+  }
+  __syncwarp();
+  quartet_epilogue<C, R>(a, bra, ket, bi, ki, ws, pbuf);
+}
+
+template <class C, typename R>
+__global__ void __launch_bounds__(kThreadsSplit) k_build_K_split(const BuildArgs a) {
+  using Lay = SplitLayout<C, R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_pq[kThreadsSplit / 32][64];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  R* ws = reinterpret_cast<R*>(smem_raw) + warp * Lay::PER_WARP;
+  R* pbuf = ws + C::Coop::HRR_SLOTS;
+  int* pq = s_pq[warp];
+  unsigned long long done = 0, pdone = 0;
+  for (;;) {
+    int d = 0;
+    if (lane == 0) d = atomicAdd(a.counter, 1);
+    d = __shfl_sync(0xffffffffu, d, 0);
+    if (d >= a.n_desc) break;
+    const Desc ds = a.desc[d];
+    const PairRec bra = a.bra_pairs[ds.bra];
+    for (int kb = ds.k0; kb < ds.k1; kb += 32) {
+      const int k = kb + lane;
+      bool ok = false;
+      if (k < ds.k1) ok = keep_quartet(a, bra, a.ket_pairs[k]);
+      unsigned m = __ballot_sync(0xffffffffu, ok);
+      done += __popc(m);
+      while (m) {
+        const int j = __ffs(m) - 1;
+        m &= m - 1;
+        split_quartet<C, R>(a, ds.bra, kb + j, ws, pbuf, pq, pdone);
       }
     }
   }
@@ -652,6 +805,14 @@ void launch_build_K_t(const BuildArgs& a, int grid, cudaStream_t s) {
       attr = true;
     }
     k_build_K_coop<C, R><<<grid, kThreadsCoop, sm, s>>>(a);
+  } else if constexpr (C::SPLIT) {
+    const size_t sm = SplitLayout<C, R>::bytes();
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_build_K_split<C, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      attr = true;
+    }
+    k_build_K_split<C, R><<<grid, kThreadsSplit, sm, s>>>(a);
   } else {
     k_build_K<C, R><<<grid, kThreadsK, 0, s>>>(a);
   }
@@ -672,6 +833,10 @@ int occupancy_build_K_t() {
     const size_t sm = CoopLayout<C, R>::bytes();
     cudaFuncSetAttribute(k_build_K_coop<C, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_build_K_coop<C, R>, kThreadsCoop, sm);
+  } else if constexpr (C::SPLIT) {
+    const size_t sm = SplitLayout<C, R>::bytes();
+    cudaFuncSetAttribute(k_build_K_split<C, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_build_K_split<C, R>, kThreadsSplit, sm);
   } else {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_build_K<C, R>, kThreadsK, 0);
   }

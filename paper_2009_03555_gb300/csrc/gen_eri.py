@@ -221,13 +221,36 @@ def gen_class(ib, ik, la, lb, lc, ld):
     name = f"Cls{la}{lb}{lc}{ld}"
     NA, NB, NC, ND = (len(comps(x)) for x in (la, lb, lc, ld))
     src = []
-    coop = len(v.E) * len(v.F) >= COOP_MIN_ACC
-    if coop:
+    nacc = len(v.E) * len(v.F)
+    coop = nacc >= COOP_MIN_ACC
+    split = (not coop) and nacc >= SPLIT_MIN_ACC
+    if coop or split:
         src.append(emit_coop(name, coop_tables(la, lb, lc, ld)))
     src.append(f"struct {name} {{")
     src.append(f"  static constexpr bool COOP = {'true' if coop else 'false'};")
-    if coop:
+    src.append(f"  static constexpr bool SPLIT = {'true' if split else 'false'};")
+    if coop or split:
         src.append(f"  using Coop = {name}Coop;")
+    if split:
+        sl, nch, _, perm = gen_vrr_split(la, lb, lc, ld)
+        src.append(f"  static constexpr int NCHUNK = {nch};")
+        src.append("  __device__ static const unsigned short* split_perm() {")
+        src.append("    static const unsigned short kPerm[] = {" + ", ".join(str(x) for x in perm) + "};")
+        src.append("    return kPerm;")
+        src.append("  }")
+        src.append("  template <typename R>")
+        src.append("  __device__ __forceinline__ static void vrr_split(const R* __restrict__ G, const VrrGeo<R>& g,")
+        src.append("                                                 R* __restrict__ acc, R* __restrict__ comp) {")
+        src.append("    const R PAx = g.PA[0], PAy = g.PA[1], PAz = g.PA[2];")
+        src.append("    const R QCx = g.QC[0], QCy = g.QC[1], QCz = g.QC[2];")
+        src.append("    const R WPx = g.WP[0], WPy = g.WP[1], WPz = g.WP[2];")
+        src.append("    const R WQx = g.WQ[0], WQy = g.WQ[1], WQz = g.WQ[2];")
+        src.append("    const R oo2p = g.oo2p, oo2q = g.oo2q, oo2pq = g.oo2pq, rop = g.rop, roq = g.roq;")
+        src.append("    (void)PAx; (void)PAy; (void)PAz; (void)QCx; (void)QCy; (void)QCz;")
+        src.append("    (void)WPx; (void)WPy; (void)WPz; (void)WQx; (void)WQy; (void)WQz;")
+        src.append("    (void)oo2p; (void)oo2q; (void)oo2pq; (void)rop; (void)roq;")
+        src.extend(sl)
+        src.append("  }")
     src.append(f"  static constexpr int la = {la}, lb = {lb}, lc = {lc}, ld = {ld};")
     src.append(f"  static constexpr int bra_class = {ib}, ket_class = {ik};")
     src.append(f"  static constexpr int L = {la + lb + lc + ld};")
@@ -341,7 +364,7 @@ def _write_if_changed(path, text):
 # kind 2 (bra HRR):  v = s0 + AB_i s1;   kind 3 (ket HRR): v = s0 + CD_i s1
 # VRR slots: 0 = constant zero, 1..L+1 = G_0..G_L, then nodes by level
 # (level = |e| + |f|).  HRR slots: 0..NACC-1 = contracted [e0|f0], then nodes.
-COOP_MIN_ACC = 180
+COOP_MIN_ACC = 900
 
 
 def coop_tables(la, lb, lc, ld):
@@ -506,6 +529,96 @@ def emit_coop(name, t):
     lines.append(f"  __device__ static const unsigned short* out() {{ return k{name}_out; }}")
     lines.append("};")
     return "\n".join(lines)
+
+
+
+# ---------------------------------------------------------------- split
+# Medium-large classes run one warp per shell quartet with the lanes on
+# different primitive quartets: each lane evaluates the straight-line vertical
+# recursion of its own primitive quartet, and every 32 finished targets are
+# summed over the warp by a butterfly reduce-scatter, after which lane j holds
+# target (32 k + j).  The targets are emitted e-major (accumulator order) in a
+# depth-first order, which keeps the live set of the recursion small.
+SPLIT_MIN_ACC = 90
+
+
+def _greedy_target_order(v, targets):
+    """Targets in an order that keeps the recursion's live set small: at each
+    step the target whose evaluation needs the fewest not-yet-computed nodes."""
+    deps = {}
+
+    def srcs(e, f, m):
+        out = []
+        if sum(f) > 0:
+            i = next(k for k in range(3) if f[k] > 0)
+            f1 = _sub(f, i)
+            out += [(e, f1, m), (e, f1, m + 1)]
+            if f1[i] > 0:
+                out += [(e, _sub(f1, i), m), (e, _sub(f1, i), m + 1)]
+            if e[i] > 0:
+                out += [(_sub(e, i), f1, m + 1)]
+        elif sum(e) > 0:
+            i = next(k for k in range(3) if e[k] > 0)
+            e1 = _sub(e, i)
+            out += [(e1, f, m), (e1, f, m + 1)]
+            if e1[i] > 0:
+                out += [(_sub(e1, i), f, m), (_sub(e1, i), f, m + 1)]
+        return [x for x in out if sum(x[0]) + sum(x[1]) > 0]
+
+    def collect(k):
+        if k in deps:
+            return
+        deps[k] = srcs(*k)
+        for x in deps[k]:
+            collect(x)
+
+    for (e, f) in targets:
+        collect((e, f, 0))
+    done, order, left = set(), [], list(targets)
+
+    def closure(k, acc):
+        if k in done or k in acc:
+            return
+        for x in deps[k]:
+            closure(x, acc)
+        acc.add(k)
+
+    while left:
+        best = None
+        for t in left:
+            acc = set()
+            closure((t[0], t[1], 0), acc)
+            if best is None or len(acc) < best[0]:
+                best = (len(acc), t, acc)
+        done |= best[2]
+        order.append(best[1])
+        left.remove(best[1])
+    return order
+
+
+def gen_vrr_split(la, lb, lc, ld):
+    v = VRR(la, lb, lc, ld)
+    nf = len(v.F)
+    eidx = {e: i for i, e in enumerate(v.E)}
+    fidx = {f: i for i, f in enumerate(v.F)}
+    targets = _greedy_target_order(v, [(e, f) for e in v.E for f in v.F])
+    perm = [eidx[e] * nf + fidx[f] for (e, f) in targets]
+    lines = []
+    emitted_before = 0
+    nch = (len(targets) + 31) // 32
+    for k in range(nch):
+        chunk = targets[32 * k: 32 * (k + 1)]
+        names = [v.node(e, f, 0) for (e, f) in chunk]
+        new = v.lines[emitted_before:]
+        emitted_before = len(v.lines)
+        lines.extend(new)
+        vals = names + ["R(0)"] * (32 - len(names))
+        lines.append("    {")
+        lines.append("      R c_[32] = {" + ", ".join(vals) + "};")
+        lines.append(f"      kacc<R>(acc[{k}], comp[{k}], reduce_scatter32<R>(c_));")
+        lines.append("    }")
+    v.flops += len(targets)
+    return lines, nch, v.flops, perm
 
 
 if __name__ == "__main__":
