@@ -45,8 +45,9 @@ def _peaks():
 
 
 def fp64_prologue_flops(L, kernel):
-    """FP64 flops (FMA = 2) of the per-primitive-quartet prologue as written in
-    eri_kernels.cuh / eri_common.cuh: argument T, prefactor, Boys function(s)."""
+    """FP64 flops (FMA = 2) of the per-primitive-quartet prologue of the FP64
+    path as written in eri_common.cuh: argument T, prefactor, Boys function(s),
+    erfc difference."""
     boys = 17 + (16 + 3 * L if L > 0 else 0)
     base = 31
     if kernel == 0:
@@ -54,15 +55,25 @@ def fp64_prologue_flops(L, kernel):
     return base + 2 * boys + 1 + 8 + 12 + 4 * (L + 1)
 
 
+def ds_prologue_flops(L, kernel):
+    """FP32 flops of the same prologue in double-single arithmetic
+    (boys_ds.cuh): argument and prefactor ~160, Boys 88 (+67+27L for L > 0),
+    erfc: second Boys, attenuation factor and the per-m difference."""
+    base = 160
+    boys = 88 + (67 + 27 * L if L > 0 else 0)
+    if kernel == 0:
+        return base + boys + 2 * (L + 1)
+    return base + 2 * boys + 101 + 29 * (L + 1)
+
+
 def class_flops(ci, n_q, n_pq, kernel, fp32):
     """(fp64 flops, fp32 flops) of one class launch with n_q quartets and n_pq
     primitive quartets."""
     L = ci.la + ci.lb + ci.lc + ci.ld
-    f64 = n_pq * fp64_prologue_flops(L, kernel)
     rec = n_pq * (ci.vrr_flops + 9) + n_q * (ci.hrr_flops + 8 * ci.n_out)
     if fp32:
-        return f64, rec
-    return f64 + rec, 0
+        return 0, n_pq * ds_prologue_flops(L, kernel) + rec
+    return n_pq * fp64_prologue_flops(L, kernel) + rec, 0
 
 
 class ClockSampler:

@@ -92,6 +92,7 @@ typedef struct {
 
 typedef struct hfx_basis_s hfx_basis;
 typedef struct hfx_quartets_s hfx_quartets;
+typedef struct hfx_batch_s hfx_batch;
 
 /* Statistics of the most recent hfx_build_K on a quartet list. */
 typedef struct {
@@ -170,6 +171,39 @@ hfx_status hfx_boys_eval(hfx_basis* basis, int precision, int mmax, int n, const
 
 /* Statistics (synchronises the device). */
 hfx_status hfx_get_stats(const hfx_quartets* q, hfx_stats* out);
+
+/* ---- Batches: several independent systems in one build ----------------
+ * A batch runs the exchange builds of its members (quartet lists that share
+ * kernel, precision and screening options) together: one launch per quartet
+ * class over the work queues of all members, one launch for each of the small
+ * per-build kernels.  With use_graph the whole build is captured once as a
+ * CUDA graph (class kernels on parallel branches) and replayed afterwards;
+ * P and K pointers are read through a system table that the graph copies from
+ * pinned host memory, so they may change between builds.  Members must outlive
+ * the batch. */
+hfx_status hfx_batch_create(hfx_quartets* const* members, int n, void* stream, hfx_batch** out);
+
+/* One build of every member: P_vals[i], K_vals[i] device arrays of member i's
+ * value count.  Asynchronous on `stream`. */
+hfx_status hfx_batch_build_K(hfx_batch* b, const double* const* P_vals, double* const* K_vals, int use_graph,
+                             void* stream);
+
+/* E_x of every member from the last build (host array of n doubles); syncs. */
+hfx_status hfx_batch_energies(hfx_batch* b, double* E_x, void* stream);
+
+/* Autotuner: times every quartet class alone over the batch for each work-queue
+ * batch size (32, 128, 512 quartets) and persistent grid (1/2, 1, 2 x the
+ * occupancy limit) and keeps the fastest per class.  Leaves K holding trial
+ * sums (the next build zeroes it).  Synchronises. */
+hfx_status hfx_batch_autotune(hfx_batch* b, const double* const* P_vals, double* const* K_vals, void* stream);
+
+/* Per-class batch size and grid in use (arrays of 21; 0 for classes without work). */
+hfx_status hfx_batch_get_tuning(hfx_batch* b, int* n_block, int* grid);
+
+/* Statistics summed over members (synchronises). */
+hfx_status hfx_batch_get_stats(hfx_batch* b, hfx_stats* out);
+
+void hfx_batch_destroy(hfx_batch* b);
 
 /* Static per-class information; cls in [0, 21). */
 hfx_status hfx_get_class_info(int cls, hfx_class_info* out);

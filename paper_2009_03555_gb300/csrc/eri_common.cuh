@@ -44,7 +44,7 @@ struct __align__(16) PairRec {
 // ket class's Q-sorted list.  The batch is the unit handed out by the device
 // work queue (Sec. 3, Algorithms 1-3: the batched ERIs' start/end indexes).
 struct __align__(16) Desc {
-  int bra, k0, k1, pad;
+  int bra, k0, k1, sys;  // sys: index into the build's system table
 };
 
 // Geometry of one primitive quartet for the vertical recursion.

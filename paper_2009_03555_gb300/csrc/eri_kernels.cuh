@@ -18,14 +18,36 @@ namespace hfx {
 constexpr int kThreadsK = 128;
 constexpr int kWarpsK = kThreadsK / 32;
 
+// Everything one system contributes to a build: its pair lists, density and
+// exchange matrices, pattern tables and Pmax.  Kernels read it from a device
+// table indexed by the system id of each batch descriptor, so one launch per
+// quartet class serves any number of systems (a single build is a batch of 1).
+struct SysArgs {
+  const PairRec* pairs[6];  // significant shell pairs per pair class, Q-sorted
+  const PrimPair* prims[6];
+  const double* pmax;       // n_shells x n_shells shell-pair max |P|
+  const double* P;          // block-sparse P values
+  double* K;                // block-sparse K values (accumulated, not symmetrised)
+  const long long* blk_off; // n_atoms x n_atoms block offsets, -1 = absent
+  const int* sh_atom;       // atom of each shell
+  const int* sh_loc;        // first function of each shell within its atom
+  const int* atom_nf;       // functions per atom
+  const int* sh_l;          // angular momentum of each shell
+  const int* blk_x;         // pattern blocks (CSR order): atoms, value offsets
+  const int* blk_y;
+  const long long* blk_val_off;
+  long long n_values;
+  int n_blocks;
+  int ns;
+  int n_atoms;
+};
+
 struct BuildArgs {
-  const PairRec* bra_pairs;
-  const PrimPair* bra_prims;
-  const PairRec* ket_pairs;
-  const PrimPair* ket_prims;
-  const Desc* desc;
+  const SysArgs* sys;     // device table of systems
+  const Desc* desc;       // batches of this quartet class (Desc::sys = system id)
   int n_desc;
   int* counter;           // work-queue head (zeroed before the launch)
+  int bra_class, ket_class;
   int same_class;         // bra class == ket class: canonical k >= bra rank
   const double* boys;     // Boys Taylor tables (FP64)
   const float* boysf;     // the same tables as double-single (mixed path)
@@ -38,15 +60,6 @@ struct BuildArgs {
   float eps_prim;         // primitive quartets with bound_ab bound_cd below this are skipped
   int route;              // 0: all quartets, 1: only bound <= promote, 2: only bound > promote
   double promote;         // FP64 promotion bound on Q_AB Q_CD P_scr
-  const double* pmax;     // n_shells x n_shells shell-pair max |P|
-  int ns;
-  const double* P;        // block-sparse P values
-  double* K;              // block-sparse K values (accumulated, not symmetrised)
-  const long long* blk_off;  // n_atoms x n_atoms block offsets, -1 = absent
-  int n_atoms;
-  const int* sh_atom;     // atom of each shell
-  const int* sh_loc;      // first function of each shell within its atom
-  const int* atom_nf;     // functions per atom
   unsigned long long* n_done;  // [0] quartets computed, [1] primitive quartets computed
 };
 
@@ -153,7 +166,7 @@ __device__ __forceinline__ int contracted_quartet(const PairRec& bra, const Prim
 // build.  Blocks outside the sparsity pattern are skipped (P is zero there and
 // K is not stored there).  Accumulation into K is FP64.
 template <class C, typename R>
-__device__ __forceinline__ void scatter_K(const BuildArgs& a, int sA, int sB, int sC, int sD,
+__device__ __forceinline__ void scatter_K(const SysArgs& a, int sA, int sB, int sC, int sD,
                                           const R* __restrict__ g, double fac) {
   constexpr int NA = C::NA, NB = C::NB, NC = C::NC, ND = C::ND;
   const int na = a.n_atoms;
@@ -234,12 +247,13 @@ __device__ __forceinline__ void scatter_K(const BuildArgs& a, int sA, int sB, in
 
 // Screening of quartet (bra | ket k) (Sec. 2: Eq. schwarz and Eq. dmscreening;
 // exact skip when every P block it touches is zero) and precision routing.
-__device__ __forceinline__ bool keep_quartet(const BuildArgs& a, const PairRec& bra, const PairRec& ket) {
+__device__ __forceinline__ bool keep_quartet(const BuildArgs& a, const SysArgs& S, const PairRec& bra,
+                                             const PairRec& ket) {
   const double qq = bra.Q * ket.Q;
   double pscr = 0.0;
   if (a.screen || a.route) {
-    const double* pm = a.pmax;
-    const int ns = a.ns;
+    const double* pm = S.pmax;
+    const int ns = S.ns;
     pscr = fmax(fmax(__ldg(pm + bra.A * ns + ket.A), __ldg(pm + bra.A * ns + ket.B)),
                 fmax(__ldg(pm + bra.B * ns + ket.A), __ldg(pm + bra.B * ns + ket.B)));
   }
@@ -266,23 +280,24 @@ __device__ __forceinline__ bool keep_quartet(const BuildArgs& a, const PairRec& 
 // on screened-out quartets.
 template <class C, typename R>
 __global__ void __launch_bounds__(kThreadsK) k_build_K(const BuildArgs a) {
-  __shared__ int2 s_queue[kWarpsK][64];
+  __shared__ int4 s_queue[kWarpsK][64];
   const int lane = threadIdx.x & 31;
-  int2* Qw = s_queue[threadIdx.x >> 5];
+  int4* Qw = s_queue[threadIdx.x >> 5];
   int qn = 0;
   unsigned long long done = 0, pdone = 0;
 
-  auto process = [&](int2 it) {
-    const PairRec bra = a.bra_pairs[it.x];
-    const PairRec ket = a.ket_pairs[it.y];
+  auto process = [&](int4 it) {  // (system, bra, ket)
+    const SysArgs& S = a.sys[it.x];
+    const PairRec bra = S.pairs[a.bra_class][it.y];
+    const PairRec ket = S.pairs[a.ket_class][it.z];
     double fac = 1.0;
     if (bra.A == bra.B) fac *= 0.5;
     if (ket.A == ket.B) fac *= 0.5;
-    if (a.same_class && it.x == it.y) fac *= 0.5;
+    if (a.same_class && it.y == it.z) fac *= 0.5;
     R out[C::NOUT];
-    pdone += (unsigned long long)contracted_quartet<C, R>(bra, a.bra_prims, ket, a.ket_prims, a.boys, a.boysf,
-                                                          a.kernel, a.omega2, a.eps_prim, out);
-    scatter_K<C, R>(a, bra.A, bra.B, ket.A, ket.B, out, fac);
+    pdone += (unsigned long long)contracted_quartet<C, R>(bra, S.prims[a.bra_class], ket, S.prims[a.ket_class],
+                                                          a.boys, a.boysf, a.kernel, a.omega2, a.eps_prim, out);
+    scatter_K<C, R>(S, bra.A, bra.B, ket.A, ket.B, out, fac);
     ++done;
   };
 
@@ -292,17 +307,19 @@ __global__ void __launch_bounds__(kThreadsK) k_build_K(const BuildArgs a) {
     d = __shfl_sync(0xffffffffu, d, 0);
     if (d >= a.n_desc) break;
     const Desc ds = a.desc[d];
-    const PairRec bra = a.bra_pairs[ds.bra];
+    const SysArgs& S = a.sys[ds.sys];
+    const PairRec bra = S.pairs[a.bra_class][ds.bra];
+    const PairRec* __restrict__ kets = S.pairs[a.ket_class];
     for (int kb = ds.k0; kb < ds.k1; kb += 32) {
       const int k = kb + lane;
       bool ok = false;
-      if (k < ds.k1) ok = keep_quartet(a, bra, a.ket_pairs[k]);
+      if (k < ds.k1) ok = keep_quartet(a, S, bra, kets[k]);
       const unsigned m = __ballot_sync(0xffffffffu, ok);
-      if (ok) Qw[qn + __popc(m & ((1u << lane) - 1u))] = make_int2(ds.bra, k);
+      if (ok) Qw[qn + __popc(m & ((1u << lane) - 1u))] = make_int4(ds.sys, ds.bra, k, 0);
       qn += __popc(m);
       __syncwarp();
       if (qn >= 32) {
-        const int2 it = Qw[lane];
+        const int4 it = Qw[lane];
         __syncwarp();
         if (lane < qn - 32) Qw[lane] = Qw[32 + lane];
         __syncwarp();
@@ -351,8 +368,8 @@ struct CoopLayout {
 // [e0|f0] held in ws[0..NACC-1], then the four exchange contributions
 // (see scatter_K) spread over the lanes.  Whole warp.
 template <class C, typename R>
-__device__ __forceinline__ void quartet_epilogue(const BuildArgs& a, const PairRec& bra, const PairRec& ket,
-                                                 int bi, int ki, R* ws, R* pbuf) {
+__device__ __forceinline__ void quartet_epilogue(const BuildArgs& a, const SysArgs& S, const PairRec& bra,
+                                                 const PairRec& ket, int bi, int ki, R* ws, R* pbuf) {
   using T = typename C::Coop;
   const int lane = threadIdx.x & 31;
   const uint4* __restrict__ hrr = T::hrr();
@@ -377,13 +394,13 @@ __device__ __forceinline__ void quartet_epilogue(const BuildArgs& a, const PairR
   if (bra.A == bra.B) fac *= 0.5;
   if (ket.A == ket.B) fac *= 0.5;
   if (a.same_class && bi == ki) fac *= 0.5;
-  const int na = a.n_atoms;
+  const int na = S.n_atoms;
   const int sA = bra.A, sB = bra.B, sC = ket.A, sD = ket.B;
-  const int atA = a.sh_atom[sA], atB = a.sh_atom[sB], atC = a.sh_atom[sC], atD = a.sh_atom[sD];
-  const int lA = a.sh_loc[sA], lB = a.sh_loc[sB], lC = a.sh_loc[sC], lD = a.sh_loc[sD];
-  const int nfC = a.atom_nf[atC], nfD = a.atom_nf[atD];
-  const long long oAC = a.blk_off[atA * na + atC], oAD = a.blk_off[atA * na + atD];
-  const long long oBC = a.blk_off[atB * na + atC], oBD = a.blk_off[atB * na + atD];
+  const int atA = S.sh_atom[sA], atB = S.sh_atom[sB], atC = S.sh_atom[sC], atD = S.sh_atom[sD];
+  const int lA = S.sh_loc[sA], lB = S.sh_loc[sB], lC = S.sh_loc[sC], lD = S.sh_loc[sD];
+  const int nfC = S.atom_nf[atC], nfD = S.atom_nf[atD];
+  const long long oAC = S.blk_off[atA * na + atC], oAD = S.blk_off[atA * na + atD];
+  const long long oBC = S.blk_off[atB * na + atC], oBD = S.blk_off[atB * na + atD];
   const bool h1 = oAC >= 0 && oBD >= 0, h2 = oBC >= 0 && oAD >= 0;
   // P blocks into the (now free) prologue buffer: BD | AC | AD | BC
   R* pBD = pbuf;
@@ -391,13 +408,13 @@ __device__ __forceinline__ void quartet_epilogue(const BuildArgs& a, const PairR
   R* pAD = pAC + NA * NC;
   R* pBC = pAD + NA * ND;
   for (int e = lane; e < NB * ND; e += 32)
-    pBD[e] = h1 ? R(__ldg(a.P + oBD + (long long)(lB + e / ND) * nfD + lD + e % ND)) : R(0);
+    pBD[e] = h1 ? R(__ldg(S.P + oBD + (long long)(lB + e / ND) * nfD + lD + e % ND)) : R(0);
   for (int e = lane; e < NA * NC; e += 32)
-    pAC[e] = h1 ? R(__ldg(a.P + oAC + (long long)(lA + e / NC) * nfC + lC + e % NC)) : R(0);
+    pAC[e] = h1 ? R(__ldg(S.P + oAC + (long long)(lA + e / NC) * nfC + lC + e % NC)) : R(0);
   for (int e = lane; e < NA * ND; e += 32)
-    pAD[e] = h2 ? R(__ldg(a.P + oAD + (long long)(lA + e / ND) * nfD + lD + e % ND)) : R(0);
+    pAD[e] = h2 ? R(__ldg(S.P + oAD + (long long)(lA + e / ND) * nfD + lD + e % ND)) : R(0);
   for (int e = lane; e < NB * NC; e += 32)
-    pBC[e] = h2 ? R(__ldg(a.P + oBC + (long long)(lB + e / NC) * nfC + lC + e % NC)) : R(0);
+    pBC[e] = h2 ? R(__ldg(S.P + oBC + (long long)(lB + e / NC) * nfC + lC + e % NC)) : R(0);
   __syncwarp();
   constexpr int N1 = NA * NC, N2 = N1 + NB * ND, N3 = N2 + NB * NC, N4 = N3 + NA * ND;
   for (int o = lane; o < N4; o += 32) {
@@ -407,25 +424,25 @@ __device__ __forceinline__ void quartet_epilogue(const BuildArgs& a, const PairR
       const int x = o / NC, c = o % NC;
       for (int b = 0; b < NB; ++b)
         for (int d = 0; d < ND; ++d) s += ws[__ldg(outs + ((x * NB + b) * NC + c) * ND + d)] * pBD[b * ND + d];
-      atomicAdd(a.K + oAC + (long long)(lA + x) * nfC + lC + c, fac * (double)s);
+      atomicAdd(S.K + oAC + (long long)(lA + x) * nfC + lC + c, fac * (double)s);
     } else if (o < N2) {  // K_BD[b][d] += sum_{x,c} g P_AC
       if (!h1) continue;
       const int b = (o - N1) / ND, d = (o - N1) % ND;
       for (int x = 0; x < NA; ++x)
         for (int c = 0; c < NC; ++c) s += ws[__ldg(outs + ((x * NB + b) * NC + c) * ND + d)] * pAC[x * NC + c];
-      atomicAdd(a.K + oBD + (long long)(lB + b) * nfD + lD + d, fac * (double)s);
+      atomicAdd(S.K + oBD + (long long)(lB + b) * nfD + lD + d, fac * (double)s);
     } else if (o < N3) {  // K_BC[b][c] += sum_{x,d} g P_AD
       if (!h2) continue;
       const int b = (o - N2) / NC, c = (o - N2) % NC;
       for (int x = 0; x < NA; ++x)
         for (int d = 0; d < ND; ++d) s += ws[__ldg(outs + ((x * NB + b) * NC + c) * ND + d)] * pAD[x * ND + d];
-      atomicAdd(a.K + oBC + (long long)(lB + b) * nfC + lC + c, fac * (double)s);
+      atomicAdd(S.K + oBC + (long long)(lB + b) * nfC + lC + c, fac * (double)s);
     } else {  // K_AD[x][d] += sum_{b,c} g P_BC
       if (!h2) continue;
       const int x = (o - N3) / ND, d = (o - N3) % ND;
       for (int b = 0; b < NB; ++b)
         for (int c = 0; c < NC; ++c) s += ws[__ldg(outs + ((x * NB + b) * NC + c) * ND + d)] * pBC[b * NC + c];
-      atomicAdd(a.K + oAD + (long long)(lA + x) * nfD + lD + d, fac * (double)s);
+      atomicAdd(S.K + oAD + (long long)(lA + x) * nfD + lD + d, fac * (double)s);
     }
   }
   __syncwarp();
@@ -433,7 +450,8 @@ __device__ __forceinline__ void quartet_epilogue(const BuildArgs& a, const PairR
 
 
 template <class C, typename R>
-__device__ __forceinline__ void coop_quartet(const BuildArgs& a, int bi, int ki, R* ws, R* pbuf, R* sg,
+__device__ __forceinline__ void coop_quartet(const BuildArgs& a, const SysArgs& S, int bi, int ki, R* ws, R* pbuf,
+                                             R* sg,
                                              unsigned long long& pdone) {
   using T = typename C::Coop;
   using Lay = CoopLayout<C, R>;
@@ -441,7 +459,9 @@ __device__ __forceinline__ void coop_quartet(const BuildArgs& a, int bi, int ki,
   constexpr int NR = kMixed ? 1 : 2;
   constexpr int NG = C::L + 1;
   const int lane = threadIdx.x & 31;
-  const PairRec bra = a.bra_pairs[bi], ket = a.ket_pairs[ki];
+  const PairRec bra = S.pairs[a.bra_class][bi], ket = S.pairs[a.ket_class][ki];
+  const PrimPair* __restrict__ bprims = S.prims[a.bra_class];
+  const PrimPair* __restrict__ kprims = S.prims[a.ket_class];
   R acc[Lay::NPL], comp[Lay::NPL];
 #pragma unroll
   for (int k = 0; k < Lay::NPL; ++k) {
@@ -458,8 +478,8 @@ __device__ __forceinline__ void coop_quartet(const BuildArgs& a, int bi, int ki,
     bool valid = false;
     if (t < total) {
       const int ib = t / nk, ik = t - ib * nk;
-      const PrimPair& pb = a.bra_prims[bra.poff + ib];
-      const PrimPair& pk = a.ket_prims[ket.poff + ik];
+      const PrimPair& pb = bprims[bra.poff + ib];
+      const PrimPair& pk = kprims[ket.poff + ik];
       valid = pb.bound * pk.bound >= a.eps_prim;
       if (valid) {
         R* rec = pbuf + lane * Lay::PB;
@@ -566,7 +586,7 @@ __device__ __forceinline__ void coop_quartet(const BuildArgs& a, int bi, int ki,
     if (tt < C::NACC) ws[tt] = kMixed ? acc[k] - comp[k] : acc[k];
   }
   __syncwarp();
-  quartet_epilogue<C, R>(a, bra, ket, bi, ki, ws, pbuf);
+  quartet_epilogue<C, R>(a, S, bra, ket, bi, ki, ws, pbuf);
 }
 
 // Persistent cooperative kernel: same device work queue and screening as
@@ -588,17 +608,19 @@ __global__ void __launch_bounds__(kThreadsCoop) k_build_K_coop(const BuildArgs a
     d = __shfl_sync(0xffffffffu, d, 0);
     if (d >= a.n_desc) break;
     const Desc ds = a.desc[d];
-    const PairRec bra = a.bra_pairs[ds.bra];
+    const SysArgs& S = a.sys[ds.sys];
+    const PairRec bra = S.pairs[a.bra_class][ds.bra];
+    const PairRec* __restrict__ kets = S.pairs[a.ket_class];
     for (int kb = ds.k0; kb < ds.k1; kb += 32) {
       const int k = kb + lane;
       bool ok = false;
-      if (k < ds.k1) ok = keep_quartet(a, bra, a.ket_pairs[k]);
+      if (k < ds.k1) ok = keep_quartet(a, S, bra, kets[k]);
       unsigned m = __ballot_sync(0xffffffffu, ok);
       done += __popc(m);
       while (m) {
         const int j = __ffs(m) - 1;
         m &= m - 1;
-        coop_quartet<C, R>(a, ds.bra, kb + j, ws, pbuf, sg, pdone);
+        coop_quartet<C, R>(a, S, ds.bra, kb + j, ws, pbuf, sg, pdone);
       }
     }
   }
@@ -627,13 +649,15 @@ struct SplitLayout {
 };
 
 template <class C, typename R>
-__device__ __forceinline__ void split_quartet(const BuildArgs& a, int bi, int ki, R* ws, R* pbuf, int* pq,
-                                              unsigned long long& pdone) {
+__device__ __forceinline__ void split_quartet(const BuildArgs& a, const SysArgs& S, int bi, int ki, R* ws,
+                                              R* pbuf, int* pq, unsigned long long& pdone) {
   constexpr bool kMixed = sizeof(R) == 4;
   constexpr int NR = kMixed ? 1 : 2;
   constexpr int NG = C::L + 1;
   const int lane = threadIdx.x & 31;
-  const PairRec bra = a.bra_pairs[bi], ket = a.ket_pairs[ki];
+  const PairRec bra = S.pairs[a.bra_class][bi], ket = S.pairs[a.ket_class][ki];
+  const PrimPair* __restrict__ bprims = S.prims[a.bra_class];
+  const PrimPair* __restrict__ kprims = S.prims[a.ket_class];
   R acc[C::NCHUNK], comp[C::NCHUNK];
 #pragma unroll
   for (int k = 0; k < C::NCHUNK; ++k) {
@@ -648,7 +672,7 @@ __device__ __forceinline__ void split_quartet(const BuildArgs& a, int bi, int ki
       bool valid = false;
       if (t < total) {
         const int ib = t / nk, ik = t - ib * nk;
-        valid = a.bra_prims[bra.poff + ib].bound * a.ket_prims[ket.poff + ik].bound >= a.eps_prim;
+        valid = bprims[bra.poff + ib].bound * kprims[ket.poff + ik].bound >= a.eps_prim;
       }
       const unsigned m = __ballot_sync(0xffffffffu, valid);
       if (valid) pq[qn + __popc(m & ((1u << lane) - 1u))] = t;
@@ -674,8 +698,8 @@ __device__ __forceinline__ void split_quartet(const BuildArgs& a, int bi, int ki
     R rop = R(0), roq = R(0);
     if (t >= 0) {
       const int ib = t / nk, ik = t - ib * nk;
-      const PrimPair& pb = a.bra_prims[bra.poff + ib];
-      const PrimPair& pk = a.ket_prims[ket.poff + ik];
+      const PrimPair& pb = bprims[bra.poff + ib];
+      const PrimPair& pk = kprims[ket.poff + ik];
       if constexpr (kMixed) {
         prologue_ds<C::L>(a.boysf, a.kernel, a.omega2, pb, pk, G, rinv, PQ);
       } else {
@@ -710,7 +734,7 @@ __device__ __forceinline__ void split_quartet(const BuildArgs& a, int bi, int ki
     if (tt < C::NACC) ws[perm[tt]] = kMixed ? acc[k] - comp[k] : acc[k];
   }
   __syncwarp();
-  quartet_epilogue<C, R>(a, bra, ket, bi, ki, ws, pbuf);
+  quartet_epilogue<C, R>(a, S, bra, ket, bi, ki, ws, pbuf);
 }
 
 template <class C, typename R>
@@ -729,17 +753,19 @@ __global__ void __launch_bounds__(kThreadsSplit) k_build_K_split(const BuildArgs
     d = __shfl_sync(0xffffffffu, d, 0);
     if (d >= a.n_desc) break;
     const Desc ds = a.desc[d];
-    const PairRec bra = a.bra_pairs[ds.bra];
+    const SysArgs& S = a.sys[ds.sys];
+    const PairRec bra = S.pairs[a.bra_class][ds.bra];
+    const PairRec* __restrict__ kets = S.pairs[a.ket_class];
     for (int kb = ds.k0; kb < ds.k1; kb += 32) {
       const int k = kb + lane;
       bool ok = false;
-      if (k < ds.k1) ok = keep_quartet(a, bra, a.ket_pairs[k]);
+      if (k < ds.k1) ok = keep_quartet(a, S, bra, kets[k]);
       unsigned m = __ballot_sync(0xffffffffu, ok);
       done += __popc(m);
       while (m) {
         const int j = __ffs(m) - 1;
         m &= m - 1;
-        split_quartet<C, R>(a, ds.bra, kb + j, ws, pbuf, pq, pdone);
+        split_quartet<C, R>(a, S, ds.bra, kb + j, ws, pbuf, pq, pdone);
       }
     }
   }

@@ -78,6 +78,55 @@ struct hfx_basis_s {
   DBuf<int> sh_l, sh_atom, sh_poff, sh_loc, atom_nf;
 };
 
+
+// A build plan: the systems of one build (a single hfx_quartets, or the members
+// of a batch), their device table, the per-class work-queue batches tagged with
+// system ids, per-class launch shapes, counters and timing events.
+struct Plan {
+  int n = 0;
+  int n_sm = 0;
+  hfx_opts opts{};
+  const double* boys = nullptr;
+  const float* boysf = nullptr;
+  SysArgs* h_sys = nullptr;  // pinned host copy (P and K filled per build)
+  DBuf<SysArgs> d_sys;
+  DBuf<double*> d_pmax;      // per-system Pmax tables
+  const Desc* descp[HFX_NCLASS] = {};
+  DBuf<Desc> desc_own[HFX_NCLASS];
+  int n_desc[HFX_NCLASS] = {0};
+  int n_block[HFX_NCLASS] = {0};
+  int grid[2][HFX_NCLASS] = {{0}};  // persistent grid per (precision, class); 0 = occupancy x SMs
+  long long max_values = 0, max_ns2 = 0;
+  int max_blocks = 0;
+  DBuf<int> counters;                // 2 x HFX_NCLASS
+  DBuf<unsigned long long> n_done;   // 2 x 2 x HFX_NCLASS
+  DBuf<double> energy;               // per system
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEvent_t sys_copied = nullptr;  // the pinned table may be rewritten once this completed
+  cudaEvent_t evk[2][HFX_NCLASS][2] = {};
+  bool ran[2][HFX_NCLASS] = {};
+  // CUDA graph of a whole build (batches)
+  cudaGraphExec_t gexec = nullptr;
+  cudaStream_t side[HFX_NCLASS] = {};
+  cudaEvent_t fork_ev = nullptr, join_ev[HFX_NCLASS] = {};
+  ~Plan() {
+    if (h_sys) cudaFreeHost(h_sys);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    if (sys_copied) cudaEventDestroy(sys_copied);
+    for (auto& p : evk)
+      for (auto& c : p)
+        for (auto& e : c)
+          if (e) cudaEventDestroy(e);
+    if (gexec) cudaGraphExecDestroy(gexec);
+    for (auto& st : side)
+      if (st) cudaStreamDestroy(st);
+    if (fork_ev) cudaEventDestroy(fork_ev);
+    for (auto& e : join_ev)
+      if (e) cudaEventDestroy(e);
+  }
+};
+
 struct hfx_quartets_s {
   hfx_basis* basis = nullptr;
   hfx_opts opts{};
@@ -100,22 +149,10 @@ struct hfx_quartets_s {
   long long n_quartets[HFX_NCLASS] = {0};
   // per-build buffers
   DBuf<double> pmax;                       // n_shells x n_shells
-  DBuf<int> counters;                      // 2 x HFX_NCLASS
-  DBuf<unsigned long long> n_done;         // 2 x 2 x HFX_NCLASS: (pass, class, {quartets, primitive quartets})
   DBuf<double> scratch;                    // energy accumulator
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  cudaEvent_t evk[2][HFX_NCLASS][2] = {};  // per pass / class: start, stop
-  bool ran[2][HFX_NCLASS] = {};
   float ms_setup = 0.f;
-  int grid_cache[2][HFX_NCLASS] = {{0}};
-  ~hfx_quartets_s() {
-    if (ev0) cudaEventDestroy(ev0);
-    if (ev1) cudaEventDestroy(ev1);
-    for (auto& p : evk)
-      for (auto& c : p)
-        for (auto& e : c)
-          if (e) cudaEventDestroy(e);
-  }
+  SysArgs h_sys{};  // this system's entry of a build table (P, K unset)
+  Plan plan;        // single-system build plan
 };
 
 // ------------------------------------------------------------------ kernels
@@ -331,7 +368,7 @@ __global__ void k_desc_count(int nb, const PairRec* bra, int nk, const PairRec* 
 }
 
 __global__ void k_desc_fill(int nb, int nk, const PairRec* bra, const PairRec* ket, int same, int screen,
-                            double tau, int n_block, const int* off, Desc* desc) {
+                            double tau, int n_block, const int* off, Desc* desc, int sys) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= nb) return;
   int k1 = nk;
@@ -353,7 +390,7 @@ __global__ void k_desc_fill(int nb, int nk, const PairRec* bra, const PairRec* k
     d.bra = j;
     d.k0 = k;
     d.k1 = min(k + n_block, k1);
-    d.pad = 0;
+    d.sys = sys;
     desc[o++] = d;
   }
 }
@@ -456,6 +493,89 @@ __global__ void k_pack(int n_blocks, const int* bx, const int* by, const long lo
   }
 }
 
+
+// ---------------------------------------------------------------- batched
+// Small kernels of a build over every system of a batch at once: 2-D grids,
+// blockIdx.y = system, reading the system table.
+__global__ void k_zero_b(const SysArgs* sys, int per_block) {
+  const SysArgs& S = sys[blockIdx.y];
+  const long long base = (long long)blockIdx.x * per_block;
+  for (long long i = base + threadIdx.x; i < base + per_block && i < S.n_values; i += blockDim.x) S.K[i] = 0.0;
+}
+
+// Pmax per shell pair, max |P_ij| over i in I, j in J (Sec. 2, density
+// screening; from the current P, every build).
+__global__ void k_pmax_b(const SysArgs* sys, double* const* pmax) {
+  const SysArgs& S = sys[blockIdx.y];
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int ns = S.ns;
+  if (t >= (long long)ns * ns) return;
+  const int I = (int)(t / ns), J = (int)(t % ns);
+  const int na = S.n_atoms;
+  const long long o = S.blk_off[S.sh_atom[I] * na + S.sh_atom[J]];
+  double mx = 0.0;
+  if (o >= 0) {
+    const int nI = (S.sh_l[I] + 1) * (S.sh_l[I] + 2) / 2, nJ = (S.sh_l[J] + 1) * (S.sh_l[J] + 2) / 2;
+    const int nfJ = S.atom_nf[S.sh_atom[J]];
+    for (int a = 0; a < nI; ++a)
+      for (int b = 0; b < nJ; ++b)
+        mx = fmax(mx, fabs(S.P[o + (long long)(S.sh_loc[I] + a) * nfJ + S.sh_loc[J] + b]));
+  }
+  pmax[blockIdx.y][t] = mx;
+}
+
+// K = K' + K'^T over each system's pattern (the scatter adds four of the
+// eight permutations of a canonical quartet; the other four are transposes).
+__global__ void k_sym_b(const SysArgs* sys) {
+  const SysArgs& S = sys[blockIdx.y];
+  const int b = blockIdx.x;
+  if (b >= S.n_blocks) return;
+  const int X = S.blk_x[b], Y = S.blk_y[b];
+  if (X > Y) return;
+  const int nX = S.atom_nf[X], nY = S.atom_nf[Y];
+  const long long oXY = S.blk_val_off[b];
+  double* K = S.K;
+  if (X == Y) {
+    for (int e = threadIdx.x; e < nX * nX; e += blockDim.x) {
+      const int r = e / nX, c = e % nX;
+      if (r < c) {
+        const double v = K[oXY + r * nX + c] + K[oXY + c * nX + r];
+        K[oXY + r * nX + c] = v;
+        K[oXY + c * nX + r] = v;
+      } else if (r == c) {
+        K[oXY + r * nX + r] *= 2.0;
+      }
+    }
+  } else {
+    const long long oYX = S.blk_off[Y * S.n_atoms + X];
+    for (int e = threadIdx.x; e < nX * nY; e += blockDim.x) {
+      const int r = e / nY, c = e % nY;
+      const double v = K[oXY + r * nY + c] + K[oYX + c * nX + r];
+      K[oXY + r * nY + c] = v;
+      K[oYX + c * nX + r] = v;
+    }
+  }
+}
+
+// E_x[system] += -1/2 sum P_i K_i over a slice (E_x zeroed before).
+__global__ void k_dot_b(const SysArgs* sys, int per_block, double* E) {
+  const SysArgs& S = sys[blockIdx.y];
+  const long long base = (long long)blockIdx.x * per_block;
+  double s = 0.0;
+  for (long long i = base + threadIdx.x; i < base + per_block && i < S.n_values; i += blockDim.x)
+    s = fma(__ldg(S.P + i), __ldg(S.K + i), s);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  __shared__ double ws[8];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+    if (t != 0.0) atomicAdd(E + blockIdx.y, -0.5 * t);
+  }
+}
+
 // ------------------------------------------------------------------ helpers
 static int device_sm_count() {
   int dev = 0, n = 0;
@@ -470,6 +590,245 @@ static cudaError_t upload(DBuf<T>& b, const std::vector<T>& v, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   if (v.empty()) return cudaSuccess;
   return cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+}
+
+
+// ---------------------------------------------------------------- plans
+static void fill_sys(hfx_quartets_s* q) {
+  hfx_basis* b = q->basis;
+  SysArgs& S = q->h_sys;
+  for (int c = 0; c < 6; ++c) {
+    S.pairs[c] = q->pairs[c].p;
+    S.prims[c] = q->prims[c].p;
+  }
+  S.pmax = q->pmax.p;
+  S.P = nullptr;
+  S.K = nullptr;
+  S.blk_off = q->blk_off.p;
+  S.sh_atom = b->sh_atom.p;
+  S.sh_loc = b->sh_loc.p;
+  S.atom_nf = b->atom_nf.p;
+  S.sh_l = b->sh_l.p;
+  S.blk_x = q->blk_x.p;
+  S.blk_y = q->blk_y.p;
+  S.blk_val_off = q->blk_val_off.p;
+  S.n_values = q->n_values;
+  S.n_blocks = q->n_blocks;
+  S.ns = b->n_shells;
+  S.n_atoms = q->n_atoms;
+}
+
+static hfx_status plan_alloc(Plan& pl, const std::vector<hfx_quartets_s*>& m, int n_sm) {
+  pl.n = (int)m.size();
+  pl.n_sm = n_sm;
+  pl.opts = m[0]->opts;
+  pl.boys = m[0]->basis->boys.p;
+  pl.boysf = m[0]->basis->boysf.p;
+  HFX_CK(cudaMallocHost(&pl.h_sys, sizeof(SysArgs) * pl.n));
+  HFX_CK(pl.d_sys.alloc(pl.n));
+  std::vector<double*> pm(pl.n);
+  for (int i = 0; i < pl.n; ++i) {
+    pl.h_sys[i] = m[i]->h_sys;
+    pm[i] = m[i]->pmax.p;
+    pl.max_values = std::max(pl.max_values, m[i]->n_values);
+    pl.max_ns2 = std::max(pl.max_ns2, (long long)m[i]->basis->n_shells * m[i]->basis->n_shells);
+    pl.max_blocks = std::max(pl.max_blocks, m[i]->n_blocks);
+  }
+  HFX_CK(upload(pl.d_pmax, pm, 0));
+  HFX_CK(pl.counters.alloc(2 * HFX_NCLASS));
+  HFX_CK(pl.n_done.alloc(4 * HFX_NCLASS));
+  HFX_CK(cudaMemset(pl.n_done.p, 0, 4 * HFX_NCLASS * sizeof(unsigned long long)));
+  HFX_CK(pl.energy.alloc(pl.n));
+  HFX_CK(cudaEventCreate(&pl.ev0));
+  HFX_CK(cudaEventCreate(&pl.ev1));
+  HFX_CK(cudaEventCreateWithFlags(&pl.sys_copied, cudaEventDisableTiming));
+  for (auto& p : pl.evk)
+    for (auto& c : p)
+      for (auto& e : c) HFX_CK(cudaEventCreate(&e));
+  return HFX_OK;
+}
+
+// Work-queue batches of quartet class `cls` for one system: returns the count;
+// with `out`, also writes them (system id `sys`).
+static hfx_status class_desc(hfx_quartets_s* q, int cls, int n_block, Desc* out, int sys, cudaStream_t s,
+                             long long* n_desc_out, long long* n_quartets_out) {
+  const int cb = hfx_class_table[cls][0], ck = hfx_class_table[cls][1];
+  const int nb = (int)q->n_pairs[cb], nk = (int)q->n_pairs[ck];
+  *n_desc_out = 0;
+  if (n_quartets_out) *n_quartets_out = 0;
+  if (nb == 0 || nk == 0) return HFX_OK;
+  const hfx_opts& o = q->opts;
+  DBuf<int> chunks, off;
+  DBuf<long long> nq, nq_sum;
+  HFX_CK(chunks.alloc(nb));
+  HFX_CK(off.alloc(nb));
+  HFX_CK(nq.alloc(nb));
+  HFX_CK(nq_sum.alloc(1));
+  k_desc_count<<<blocks_for(nb, 128), 128, 0, s>>>(nb, q->pairs[cb].p, nk, q->pairs[ck].p, cb == ck, o.screen, o.tau,
+                                                   n_block, chunks.p, nq.p);
+  size_t t1b = 0, t2b = 0;
+  cub::DeviceScan::ExclusiveSum(nullptr, t1b, chunks.p, off.p, nb, s);
+  cub::DeviceReduce::Sum(nullptr, t2b, nq.p, nq_sum.p, nb, s);
+  DBuf<unsigned char> tmp;
+  HFX_CK(tmp.alloc(std::max(t1b, t2b)));
+  t1b = tmp.n;
+  HFX_CK(cub::DeviceScan::ExclusiveSum(tmp.p, t1b, chunks.p, off.p, nb, s));
+  t2b = tmp.n;
+  HFX_CK(cub::DeviceReduce::Sum(tmp.p, t2b, nq.p, nq_sum.p, nb, s));
+  int last_off = 0, last_chunks = 0;
+  long long total_q = 0;
+  HFX_CK(cudaMemcpyAsync(&last_off, off.p + nb - 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+  HFX_CK(cudaMemcpyAsync(&last_chunks, chunks.p + nb - 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+  HFX_CK(cudaMemcpyAsync(&total_q, nq_sum.p, sizeof(long long), cudaMemcpyDeviceToHost, s));
+  HFX_CK(cudaStreamSynchronize(s));
+  *n_desc_out = (long long)last_off + last_chunks;
+  if (n_quartets_out) *n_quartets_out = total_q;
+  if (out && *n_desc_out > 0)
+    k_desc_fill<<<blocks_for(nb, 128), 128, 0, s>>>(nb, nk, q->pairs[cb].p, q->pairs[ck].p, cb == ck, o.screen, o.tau,
+                                                    n_block, off.p, out, sys);
+  HFX_CK(cudaGetLastError());
+  HFX_CK(cudaStreamSynchronize(s));
+  return HFX_OK;
+}
+
+// The batches of class `cls` for every system of a plan, concatenated.
+static hfx_status plan_class_desc(Plan& pl, const std::vector<hfx_quartets_s*>& m, int cls, int n_block,
+                                  cudaStream_t s) {
+  std::vector<long long> cnt(m.size());
+  long long tot = 0;
+  for (size_t i = 0; i < m.size(); ++i) {
+    hfx_status st = class_desc(m[i], cls, n_block, nullptr, (int)i, s, &cnt[i], nullptr);
+    if (st != HFX_OK) return st;
+    tot += cnt[i];
+  }
+  if (tot > (1LL << 31) - 1) return fail(HFX_ERR_UNSUPPORTED, "too many work-queue batches; raise n_block");
+  HFX_CK(pl.desc_own[cls].alloc(tot));
+  long long o = 0;
+  for (size_t i = 0; i < m.size(); ++i) {
+    long long c = 0;
+    hfx_status st = class_desc(m[i], cls, n_block, pl.desc_own[cls].p + o, (int)i, s, &c, nullptr);
+    if (st != HFX_OK) return st;
+    o += c;
+  }
+  pl.descp[cls] = pl.desc_own[cls].p;
+  pl.n_desc[cls] = (int)tot;
+  pl.n_block[cls] = n_block;
+  return HFX_OK;
+}
+
+static int plan_grid(Plan& pl, int fp32, int cls) {
+  int g = pl.grid[fp32][cls];
+  if (g <= 0) g = pl.grid[fp32][cls] = kClassOps[cls].occupancy_K(fp32) * pl.n_sm;
+  return g;
+}
+
+static BuildArgs plan_args(Plan& pl, int cls) {
+  const hfx_opts& o = pl.opts;
+  BuildArgs a;
+  a.sys = pl.d_sys.p;
+  a.desc = pl.descp[cls];
+  a.n_desc = pl.n_desc[cls];
+  a.bra_class = hfx_class_table[cls][0];
+  a.ket_class = hfx_class_table[cls][1];
+  a.same_class = a.bra_class == a.ket_class;
+  a.boys = pl.boys;
+  a.boysf = pl.boysf;
+  a.kernel = o.kernel;
+  a.omega2 = o.omega * o.omega;
+  a.screen = o.screen;
+  a.tau = o.tau;
+  a.dscreen = o.density_screen;
+  a.eps = o.eps;
+  a.eps_prim = (float)o.prim_cutoff;
+  a.promote = o.fp64_promote_bound;
+  a.route = 0;
+  a.counter = nullptr;
+  a.n_done = nullptr;
+  return a;
+}
+
+// Launches of the class kernels of one build (both precision passes of the
+// mixed path when FP64 promotion is on).  `fork`: each class on its own
+// stream branch (graph capture); `events`: per-launch timing.
+static hfx_status plan_classes(Plan& pl, cudaStream_t s, bool fork, bool events) {
+  const hfx_opts& o = pl.opts;
+  const bool mixed = o.precision == HFX_PREC_MIXED;
+  const bool promote = mixed && std::isfinite(o.fp64_promote_bound);
+  const int passes = promote ? 2 : 1;
+  if (fork) HFX_CK(cudaEventRecord(pl.fork_ev, s));
+  for (int cls = 0; cls < HFX_NCLASS; ++cls) {
+    for (int pass = 0; pass < 2; ++pass) pl.ran[pass][cls] = false;
+    if (pl.n_desc[cls] == 0) continue;
+    cudaStream_t cs = s;
+    if (fork) {
+      cs = pl.side[cls];
+      HFX_CK(cudaStreamWaitEvent(cs, pl.fork_ev, 0));
+    }
+    BuildArgs a = plan_args(pl, cls);
+    for (int pass = 0; pass < passes; ++pass) {
+      const int fp32 = mixed && pass == 0;
+      a.route = promote ? (pass == 0 ? 1 : 2) : 0;
+      a.counter = pl.counters.p + pass * HFX_NCLASS + cls;
+      a.n_done = pl.n_done.p + 2 * (pass * HFX_NCLASS + cls);
+      const int g = plan_grid(pl, fp32, cls);
+      if (events) HFX_CK(cudaEventRecord(pl.evk[pass][cls][0], cs));
+      kClassOps[cls].launch_K(a, fp32, g, cs);
+      if (events) HFX_CK(cudaEventRecord(pl.evk[pass][cls][1], cs));
+      pl.ran[pass][cls] = true;
+    }
+    if (fork) {
+      HFX_CK(cudaEventRecord(pl.join_ev[cls], cs));
+      HFX_CK(cudaStreamWaitEvent(s, pl.join_ev[cls], 0));
+    }
+  }
+  HFX_CK(cudaGetLastError());
+  return HFX_OK;
+}
+
+// One whole build of every system of the plan (Algorithm 4 per system):
+// system table upload, zero K, Pmax, class kernels, symmetrisation, E_x.
+static hfx_status plan_build(Plan& pl, cudaStream_t s, bool fork, bool events) {
+  HFX_CK(cudaMemcpyAsync(pl.d_sys.p, pl.h_sys, sizeof(SysArgs) * pl.n, cudaMemcpyHostToDevice, s));
+  HFX_CK(cudaEventRecord(pl.sys_copied, s));
+  if (events) HFX_CK(cudaEventRecord(pl.ev0, s));
+  const int zper = 8192;
+  if (pl.max_values > 0)
+    k_zero_b<<<dim3((unsigned)((pl.max_values + zper - 1) / zper), pl.n), 256, 0, s>>>(pl.d_sys.p, zper);
+  if (pl.max_ns2 > 0)
+    k_pmax_b<<<dim3((unsigned)((pl.max_ns2 + 255) / 256), pl.n), 256, 0, s>>>(pl.d_sys.p, pl.d_pmax.p);
+  HFX_CK(cudaMemsetAsync(pl.counters.p, 0, 2 * HFX_NCLASS * sizeof(int), s));
+  HFX_CK(cudaMemsetAsync(pl.n_done.p, 0, 4 * HFX_NCLASS * sizeof(unsigned long long), s));
+  hfx_status st = plan_classes(pl, s, fork, events);
+  if (st != HFX_OK) return st;
+  if (pl.max_blocks > 0) k_sym_b<<<dim3(pl.max_blocks, pl.n), 128, 0, s>>>(pl.d_sys.p);
+  HFX_CK(cudaMemsetAsync(pl.energy.p, 0, sizeof(double) * pl.n, s));
+  const int dper = 8192;
+  if (pl.max_values > 0)
+    k_dot_b<<<dim3((unsigned)((pl.max_values + dper - 1) / dper), pl.n), 256, 0, s>>>(pl.d_sys.p, dper,
+                                                                                       pl.energy.p);
+  if (events) HFX_CK(cudaEventRecord(pl.ev1, s));
+  HFX_CK(cudaGetLastError());
+  return HFX_OK;
+}
+
+static void plan_stats(Plan& pl, hfx_stats* out) {
+  unsigned long long done[4 * HFX_NCLASS];
+  cudaMemcpy(done, pl.n_done.p, sizeof(done), cudaMemcpyDeviceToHost);
+  for (int c = 0; c < HFX_NCLASS; ++c) {
+    out->n_quartets_computed[c] = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+      const unsigned long long* d = done + 2 * (pass * HFX_NCLASS + c);
+      out->n_quartets_computed[c] += (long long)d[0];
+      out->n_quartets_pass[pass][c] = (long long)d[0];
+      out->n_prim_quartets_pass[pass][c] = (long long)d[1];
+      float ms = 0.f;
+      if (pl.ran[pass][c] && cudaEventElapsedTime(&ms, pl.evk[pass][c][0], pl.evk[pass][c][1]) == cudaSuccess)
+        out->ms_class_pass[pass][c] = ms;
+    }
+  }
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, pl.ev0, pl.ev1) == cudaSuccess) out->ms_last_build = ms;
+  cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ ABI
@@ -770,7 +1129,7 @@ hfx_status hfx_build_quartets(hfx_basis* b, const hfx_opts* opts_in, const hfx_p
       HFX_CK(q->desc[cls].alloc(nd));
       if (nd > 0)
         k_desc_fill<<<blocks_for(nb, 128), 128, 0, s>>>(nb, nk, q->pairs[cb].p, q->pairs[ck].p, cb == ck, o.screen,
-                                                        o.tau, o.n_block, off.p, q->desc[cls].p);
+                                                        o.tau, o.n_block, off.p, q->desc[cls].p, 0);
       HFX_CK(cudaGetLastError());
     }
   long long npp = 0;
@@ -783,17 +1142,20 @@ hfx_status hfx_build_quartets(hfx_basis* b, const hfx_opts* opts_in, const hfx_p
   }
   q->n_prim_pairs = npp;
 
-  // 6. per-build buffers
+  // 6. per-build buffers and the single-system build plan
   HFX_CK(q->pmax.alloc((size_t)ns * ns));
-  HFX_CK(q->counters.alloc(2 * HFX_NCLASS));
-  HFX_CK(q->n_done.alloc(4 * HFX_NCLASS));
   HFX_CK(q->scratch.alloc(2));
-  HFX_CK(cudaMemsetAsync(q->n_done.p, 0, 4 * HFX_NCLASS * sizeof(unsigned long long), s));
-  HFX_CK(cudaEventCreate(&q->ev0));
-  HFX_CK(cudaEventCreate(&q->ev1));
-  for (auto& p : q->evk)
-    for (auto& c : p)
-      for (auto& e : c) HFX_CK(cudaEventCreate(&e));
+  fill_sys(q);
+  {
+    std::vector<hfx_quartets_s*> one(1, q);
+    hfx_status pst = plan_alloc(q->plan, one, q->n_sm);
+    if (pst != HFX_OK) return pst;
+    for (int cls = 0; cls < HFX_NCLASS; ++cls) {
+      q->plan.descp[cls] = q->desc[cls].p;
+      q->plan.n_desc[cls] = q->n_desc[cls];
+      q->plan.n_block[cls] = o.n_block;
+    }
+  }
   HFX_CK(cudaEventRecord(t1, s));
   HFX_CK(cudaEventSynchronize(t1));
   cudaEventElapsedTime(&q->ms_setup, t0, t1);
@@ -810,69 +1172,12 @@ long long hfx_value_count(const hfx_quartets* q) { return q ? q->n_values : -1; 
 
 hfx_status hfx_build_K(hfx_quartets* q, const double* P, double* K, void* stream) {
   if (!q || !P || !K) return fail(HFX_ERR_INVALID_ARG, "NULL argument");
-  cudaStream_t s = (cudaStream_t)stream;
-  hfx_basis* b = q->basis;
-  const hfx_opts& o = q->opts;
-  const int ns = b->n_shells;
-  HFX_CK(cudaEventRecord(q->ev0, s));
-  HFX_CK(cudaMemsetAsync(K, 0, (size_t)q->n_values * sizeof(double), s));
-  k_pmax<<<blocks_for((long long)ns * ns, 256), 256, 0, s>>>(ns, q->n_atoms, b->sh_atom.p, b->sh_loc.p, b->sh_l.p,
-                                                               b->atom_nf.p, q->blk_off.p, P, q->pmax.p);
-  HFX_CK(cudaMemsetAsync(q->counters.p, 0, 2 * HFX_NCLASS * sizeof(int), s));
-  HFX_CK(cudaMemsetAsync(q->n_done.p, 0, 4 * HFX_NCLASS * sizeof(unsigned long long), s));
-  for (auto& p : q->ran)
-    for (auto& r : p) r = false;
-  const bool mixed = o.precision == HFX_PREC_MIXED;
-  const bool promote = mixed && std::isfinite(o.fp64_promote_bound);
-  for (int cls = 0; cls < HFX_NCLASS; ++cls) {
-    if (q->n_desc[cls] == 0) continue;
-    const int cb = hfx_class_table[cls][0], ck = hfx_class_table[cls][1];
-    BuildArgs a;
-    a.bra_pairs = q->pairs[cb].p;
-    a.bra_prims = q->prims[cb].p;
-    a.ket_pairs = q->pairs[ck].p;
-    a.ket_prims = q->prims[ck].p;
-    a.desc = q->desc[cls].p;
-    a.n_desc = q->n_desc[cls];
-    a.same_class = cb == ck;
-    a.boys = b->boys.p;
-    a.boysf = b->boysf.p;
-    a.kernel = o.kernel;
-    a.omega2 = o.omega * o.omega;
-    a.screen = o.screen;
-    a.tau = o.tau;
-    a.dscreen = o.density_screen;
-    a.eps = o.eps;
-    a.promote = o.fp64_promote_bound;
-    a.eps_prim = (float)o.prim_cutoff;
-    a.pmax = q->pmax.p;
-    a.ns = ns;
-    a.P = P;
-    a.K = K;
-    a.blk_off = q->blk_off.p;
-    a.n_atoms = q->n_atoms;
-    a.sh_atom = b->sh_atom.p;
-    a.sh_loc = b->sh_loc.p;
-    a.atom_nf = b->atom_nf.p;
-    const int passes = promote ? 2 : 1;
-    for (int pass = 0; pass < passes; ++pass) {
-      const int fp32 = mixed && pass == 0;
-      a.route = promote ? (pass == 0 ? 1 : 2) : 0;
-      a.counter = q->counters.p + pass * HFX_NCLASS + cls;
-      a.n_done = q->n_done.p + 2 * (pass * HFX_NCLASS + cls);
-      int& g = q->grid_cache[fp32][cls];
-      if (g == 0) g = kClassOps[cls].occupancy_K(fp32) * q->n_sm;
-      HFX_CK(cudaEventRecord(q->evk[pass][cls][0], s));
-      kClassOps[cls].launch_K(a, fp32, g, s);
-      HFX_CK(cudaEventRecord(q->evk[pass][cls][1], s));
-      q->ran[pass][cls] = true;
-    }
-  }
-  k_symmetrize<<<q->n_blocks, 128, 0, s>>>(q->n_blocks, q->blk_x.p, q->blk_y.p, q->blk_val_off.p, q->n_atoms,
-                                           q->blk_off.p, b->atom_nf.p, K);
-  HFX_CK(cudaEventRecord(q->ev1, s));
-  HFX_CK(cudaGetLastError());
-  return HFX_OK;
+  Plan& pl = q->plan;
+  HFX_CK(cudaEventSynchronize(pl.sys_copied));
+  pl.h_sys[0] = q->h_sys;
+  pl.h_sys[0].P = P;
+  pl.h_sys[0].K = K;
+  return plan_build(pl, (cudaStream_t)stream, false, true);
 }
 
 hfx_status hfx_exchange_energy(hfx_quartets* q, const double* P, const double* K, double* E_x, void* stream) {
@@ -1022,27 +1327,195 @@ hfx_status hfx_get_stats(const hfx_quartets* q, hfx_stats* out) {
   if (!q || !out) return fail(HFX_ERR_INVALID_ARG, "NULL argument");
   std::memset(out, 0, sizeof(*out));
   HFX_CK(cudaDeviceSynchronize());
-  unsigned long long done[4 * HFX_NCLASS];
-  HFX_CK(cudaMemcpy(done, q->n_done.p, sizeof(done), cudaMemcpyDeviceToHost));
   for (int c = 0; c < 6; ++c) out->n_pairs_significant[c] = q->n_pairs[c];
-  for (int c = 0; c < HFX_NCLASS; ++c) {
-    out->n_quartets_schwarz[c] = q->n_quartets[c];
-    for (int pass = 0; pass < 2; ++pass) {
-      const unsigned long long* d = done + 2 * (pass * HFX_NCLASS + c);
-      out->n_quartets_computed[c] += (long long)d[0];
-      out->n_quartets_pass[pass][c] = (long long)d[0];
-      out->n_prim_quartets_pass[pass][c] = (long long)d[1];
-      float ms = 0.f;
-      if (q->ran[pass][c] && cudaEventElapsedTime(&ms, q->evk[pass][c][0], q->evk[pass][c][1]) == cudaSuccess)
-        out->ms_class_pass[pass][c] = ms;
-    }
-  }
+  for (int c = 0; c < HFX_NCLASS; ++c) out->n_quartets_schwarz[c] = q->n_quartets[c];
   out->n_prim_pairs = q->n_prim_pairs;
   out->n_values = q->n_values;
   out->ms_setup = q->ms_setup;
-  float ms = 0.f;
-  if (cudaEventElapsedTime(&ms, q->ev0, q->ev1) == cudaSuccess) out->ms_last_build = ms;
-  cudaGetLastError();
+  plan_stats(const_cast<hfx_quartets_s*>(q)->plan, out);
+  return HFX_OK;
+}
+
+// ------------------------------------------------------------------ batches
+struct hfx_batch_s {
+  std::vector<hfx_quartets_s*> members;
+  Plan plan;
+  bool tuned = false;
+};
+
+hfx_status hfx_batch_create(hfx_quartets* const* members, int n, void* stream, hfx_batch** out) {
+  if (!out || !members || n <= 0) return fail(HFX_ERR_INVALID_ARG, "need at least one member");
+  *out = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  std::unique_ptr<hfx_batch_s> b(new hfx_batch_s());
+  for (int i = 0; i < n; ++i) {
+    if (!members[i]) return fail(HFX_ERR_INVALID_ARG, "NULL member");
+    const hfx_opts &o0 = members[0]->opts, &oi = members[i]->opts;
+    if (oi.kernel != o0.kernel || oi.omega != o0.omega || oi.precision != o0.precision ||
+        oi.screen != o0.screen || oi.tau != o0.tau || oi.density_screen != o0.density_screen ||
+        oi.eps != o0.eps || oi.prim_cutoff != o0.prim_cutoff ||
+        !(oi.fp64_promote_bound == o0.fp64_promote_bound))
+      return fail(HFX_ERR_INVALID_ARG, "batch members must share kernel, precision and screening options");
+    b->members.push_back(members[i]);
+  }
+  hfx_status st = plan_alloc(b->plan, b->members, members[0]->n_sm);
+  if (st != HFX_OK) return st;
+  for (int cls = 0; cls < HFX_NCLASS; ++cls) {
+    st = plan_class_desc(b->plan, b->members, cls, members[0]->opts.n_block, s);
+    if (st != HFX_OK) return st;
+  }
+  for (int cls = 0; cls < HFX_NCLASS; ++cls) {
+    HFX_CK(cudaStreamCreateWithFlags(&b->plan.side[cls], cudaStreamNonBlocking));
+    HFX_CK(cudaEventCreateWithFlags(&b->plan.join_ev[cls], cudaEventDisableTiming));
+  }
+  HFX_CK(cudaEventCreateWithFlags(&b->plan.fork_ev, cudaEventDisableTiming));
+  *out = b.release();
+  return HFX_OK;
+}
+
+void hfx_batch_destroy(hfx_batch* b) { delete b; }
+
+static void batch_set_pointers(hfx_batch_s* b, const double* const* P, double* const* K) {
+  for (int i = 0; i < b->plan.n; ++i) {
+    b->plan.h_sys[i] = b->members[i]->h_sys;
+    b->plan.h_sys[i].P = P[i];
+    b->plan.h_sys[i].K = K[i];
+  }
+}
+
+hfx_status hfx_batch_build_K(hfx_batch* b, const double* const* P_vals, double* const* K_vals, int use_graph,
+                             void* stream) {
+  if (!b || !P_vals || !K_vals) return fail(HFX_ERR_INVALID_ARG, "NULL argument");
+  for (int i = 0; i < b->plan.n; ++i)
+    if (!P_vals[i] || !K_vals[i]) return fail(HFX_ERR_INVALID_ARG, "NULL P or K of a member");
+  cudaStream_t s = (cudaStream_t)stream;
+  Plan& pl = b->plan;
+  HFX_CK(cudaEventSynchronize(pl.sys_copied));
+  batch_set_pointers(b, P_vals, K_vals);
+  if (!use_graph) return plan_build(pl, s, false, true);
+  if (!pl.gexec) {
+    // the graph reads P and K through the system table, copied from pinned
+    // host memory by its first node, so one capture serves every later build
+    for (int f = 0; f < 2; ++f)
+      for (int cls = 0; cls < HFX_NCLASS; ++cls)
+        if (pl.n_desc[cls]) plan_grid(pl, f, cls);
+    cudaStream_t cap;
+    HFX_CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    HFX_CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed));
+    hfx_status st = plan_build(pl, cap, true, false);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cap, &g);
+    cudaStreamDestroy(cap);
+    if (st != HFX_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    if (e != cudaSuccess) return fail(HFX_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&pl.gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(HFX_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  }
+  HFX_CK(cudaEventRecord(pl.ev0, s));
+  HFX_CK(cudaGraphLaunch(pl.gexec, s));
+  HFX_CK(cudaEventRecord(pl.sys_copied, s));
+  HFX_CK(cudaEventRecord(pl.ev1, s));
+  for (auto& p : pl.ran)
+    for (auto& r : p) r = false;
+  return HFX_OK;
+}
+
+hfx_status hfx_batch_energies(hfx_batch* b, double* E_x, void* stream) {
+  if (!b || !E_x) return fail(HFX_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  HFX_CK(cudaMemcpyAsync(E_x, b->plan.energy.p, sizeof(double) * b->plan.n, cudaMemcpyDeviceToHost, s));
+  HFX_CK(cudaStreamSynchronize(s));
+  return HFX_OK;
+}
+
+hfx_status hfx_batch_get_stats(hfx_batch* b, hfx_stats* out) {
+  if (!b || !out) return fail(HFX_ERR_INVALID_ARG, "NULL argument");
+  std::memset(out, 0, sizeof(*out));
+  HFX_CK(cudaDeviceSynchronize());
+  for (auto* q : b->members) {
+    for (int c = 0; c < 6; ++c) out->n_pairs_significant[c] += q->n_pairs[c];
+    for (int c = 0; c < HFX_NCLASS; ++c) out->n_quartets_schwarz[c] += q->n_quartets[c];
+    out->n_prim_pairs += q->n_prim_pairs;
+    out->n_values += q->n_values;
+    out->ms_setup += q->ms_setup;
+  }
+  plan_stats(b->plan, out);
+  return HFX_OK;
+}
+
+// Autotuner: for every quartet class with work, time the class kernel alone on
+// the batch (current P, K) for every (batch size, persistent grid) candidate
+// and keep the fastest; the choice is reported through hfx_batch_get_tuning.
+// The trial launches accumulate into K, which the next build zeroes.
+hfx_status hfx_batch_autotune(hfx_batch* b, const double* const* P_vals, double* const* K_vals, void* stream) {
+  if (!b || !P_vals || !K_vals) return fail(HFX_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  Plan& pl = b->plan;
+  HFX_CK(cudaEventSynchronize(pl.sys_copied));
+  batch_set_pointers(b, P_vals, K_vals);
+  hfx_status st = plan_build(pl, s, false, false);  // Pmax and a warm cache
+  if (st != HFX_OK) return st;
+  HFX_CK(cudaStreamSynchronize(s));
+  const bool mixed = pl.opts.precision == HFX_PREC_MIXED;
+  const int fp32 = mixed ? 1 : 0;
+  const int nblocks[3] = {32, 128, 512};
+  cudaEvent_t e0, e1;
+  HFX_CK(cudaEventCreate(&e0));
+  HFX_CK(cudaEventCreate(&e1));
+  for (int cls = 0; cls < HFX_NCLASS; ++cls) {
+    if (pl.n_desc[cls] == 0) continue;
+    const int occ = kClassOps[cls].occupancy_K(fp32);
+    const int grids[3] = {occ * pl.n_sm, std::max(1, occ / 2) * pl.n_sm, 2 * occ * pl.n_sm};
+    float best = 1e30f;
+    int best_nb = pl.n_block[cls], best_g = grids[0];
+    for (int inb = 0; inb < 3; ++inb) {
+      st = plan_class_desc(pl, b->members, cls, nblocks[inb], s);
+      if (st != HFX_OK) return st;
+      for (int ig = 0; ig < 3; ++ig) {
+        BuildArgs a = plan_args(pl, cls);
+        a.route = 0;
+        a.counter = pl.counters.p + cls;
+        a.n_done = pl.n_done.p + 2 * cls;
+        HFX_CK(cudaMemsetAsync(pl.counters.p + cls, 0, sizeof(int), s));
+        HFX_CK(cudaEventRecord(e0, s));
+        kClassOps[cls].launch_K(a, fp32, grids[ig], s);
+        HFX_CK(cudaEventRecord(e1, s));
+        HFX_CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+          best = ms;
+          best_nb = nblocks[inb];
+          best_g = grids[ig];
+        }
+      }
+    }
+    st = plan_class_desc(pl, b->members, cls, best_nb, s);
+    if (st != HFX_OK) return st;
+    pl.grid[fp32][cls] = best_g;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (pl.gexec) {  // launch shapes changed: capture again on the next graph build
+    cudaGraphExecDestroy(pl.gexec);
+    pl.gexec = nullptr;
+  }
+  b->tuned = true;
+  HFX_CK(cudaGetLastError());
+  return HFX_OK;
+}
+
+hfx_status hfx_batch_get_tuning(hfx_batch* b, int* n_block, int* grid) {
+  if (!b || !n_block || !grid) return fail(HFX_ERR_INVALID_ARG, "NULL argument");
+  const int fp32 = b->plan.opts.precision == HFX_PREC_MIXED ? 1 : 0;
+  for (int c = 0; c < HFX_NCLASS; ++c) {
+    n_block[c] = b->plan.n_desc[c] ? b->plan.n_block[c] : 0;
+    grid[c] = b->plan.n_desc[c] ? plan_grid(b->plan, fp32, c) : 0;
+  }
   return HFX_OK;
 }
 

@@ -72,7 +72,9 @@ class ClassInfo(ctypes.Structure):
 
 EXPORTED = ["hfx_create_basis", "hfx_build_quartets", "hfx_value_count", "hfx_build_K", "hfx_exchange_energy",
             "hfx_pack_dense", "hfx_unpack_dense", "hfx_eval_quartets", "hfx_boys_eval", "hfx_get_stats",
-            "hfx_get_class_info",
+            "hfx_get_class_info", "hfx_batch_create", "hfx_batch_build_K",
+            "hfx_batch_energies", "hfx_batch_autotune", "hfx_batch_get_tuning", "hfx_batch_get_stats",
+            "hfx_batch_destroy",
             "hfx_destroy_basis", "hfx_destroy_quartets", "hfx_last_error"]
 
 _lib = None
@@ -98,6 +100,14 @@ def load(path: str = LIB_PATH):
     lib.hfx_unpack_dense.argtypes = [V, V, V, V]
     lib.hfx_eval_quartets.argtypes = [V, I, D, I, I, V, V, V, V]
     lib.hfx_boys_eval.argtypes = [V, I, I, I, V, V, V]
+    lib.hfx_batch_create.argtypes = [V, I, V, PV]
+    lib.hfx_batch_build_K.argtypes = [V, V, V, I, V]
+    lib.hfx_batch_energies.argtypes = [V, V, V]
+    lib.hfx_batch_autotune.argtypes = [V, V, V, V]
+    lib.hfx_batch_get_tuning.argtypes = [V, V, V]
+    lib.hfx_batch_get_stats.argtypes = [V, ctypes.POINTER(Stats)]
+    lib.hfx_batch_destroy.argtypes = [V]
+    lib.hfx_batch_destroy.restype = None
     lib.hfx_get_stats.argtypes = [V, ctypes.POINTER(Stats)]
     lib.hfx_get_class_info.argtypes = [I, ctypes.POINTER(ClassInfo)]
     lib.hfx_destroy_basis.argtypes = [V]
@@ -106,7 +116,8 @@ def load(path: str = LIB_PATH):
     lib.hfx_destroy_quartets.restype = None
     lib.hfx_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
-        if name not in ("hfx_value_count", "hfx_destroy_basis", "hfx_destroy_quartets", "hfx_last_error"):
+        if name not in ("hfx_value_count", "hfx_destroy_basis", "hfx_destroy_quartets", "hfx_last_error",
+                        "hfx_batch_destroy"):
             getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -314,4 +325,50 @@ class Quartets:
         h = getattr(self, "handle", None)
         if h is not None and _lib is not None:
             _lib.hfx_destroy_quartets(h)
+            self.handle = None
+
+
+class Batch:
+    """Owns an hfx_batch over several Quartets (members must stay alive)."""
+
+    def __init__(self, members, stream=None):
+        self.members = list(members)
+        arr = (ctypes.c_void_p * len(self.members))(*[m.handle.value for m in self.members])
+        self._arr = arr
+        h = ctypes.c_void_p()
+        _check(load().hfx_batch_create(arr, len(self.members), _stream(stream), ctypes.byref(h)))
+        self.handle = h
+
+    def _ptrs(self, tensors):
+        return (ctypes.c_void_p * len(tensors))(*[t.data_ptr() for t in tensors])
+
+    def build_K(self, P_vals, K_vals, use_graph=True, stream=None):
+        self._keep = (self._ptrs(P_vals), self._ptrs(K_vals))
+        _check(load().hfx_batch_build_K(self.handle, self._keep[0], self._keep[1], int(bool(use_graph)),
+                                        _stream(stream)))
+
+    def energies(self, stream=None):
+        out = np.zeros(len(self.members))
+        _check(load().hfx_batch_energies(self.handle, _ptr(out), _stream(stream)))
+        return out
+
+    def autotune(self, P_vals, K_vals, stream=None):
+        p, k = self._ptrs(P_vals), self._ptrs(K_vals)
+        _check(load().hfx_batch_autotune(self.handle, p, k, _stream(stream)))
+
+    def tuning(self):
+        nb = np.zeros(N_CLASSES, dtype=np.int32)
+        g = np.zeros(N_CLASSES, dtype=np.int32)
+        _check(load().hfx_batch_get_tuning(self.handle, _ptr(nb), _ptr(g)))
+        return nb, g
+
+    def stats(self) -> Stats:
+        st = Stats()
+        _check(load().hfx_batch_get_stats(self.handle, ctypes.byref(st)))
+        return st
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and _lib is not None:
+            _lib.hfx_batch_destroy(h)
             self.handle = None
