@@ -169,6 +169,21 @@ hfx_status hfx_eval_quartets(hfx_basis* basis, int kernel, double omega, int pre
 hfx_status hfx_boys_eval(hfx_basis* basis, int precision, int mmax, int n, const double* T, double* F,
                          void* stream);
 
+/* E_x = -1/2 sum_i P_val[i] K_val[i] without allocating any device memory
+ * (no counterpart in the paper).  For callers that cannot call cudaMalloc --
+ * processes held to a fixed device-memory budget, hosts whose allocator owns
+ * every device allocation, plugins that must not allocate -- and that have no
+ * quartet-list handle.  P_val, K_val: device arrays of n_values doubles;
+ * E_x: device pointer to one double, written asynchronously on `stream`.
+ * Scratch is a static device array of 2^16 doubles (512 KiB, held on every
+ * GPU that loads the library until exit); n_values above 2^28 is rejected with
+ * HFX_ERR_INVALID_ARG.  The first call on a device looks up the array's device
+ * address (no allocation); make that first call before any stream capture.
+ * Every call shares the array, so calls that overlap on the GPU race: serialise
+ * them.  The reduction order is fixed (two passes, no atomics). */
+hfx_status hfx_exchange_energy_noalloc(const double* P_val, const double* K_val, long long n_values, double* E_x,
+                                       void* stream);
+
 /* Statistics (synchronises the device). */
 hfx_status hfx_get_stats(const hfx_quartets* q, hfx_stats* out);
 

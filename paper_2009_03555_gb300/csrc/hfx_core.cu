@@ -30,6 +30,9 @@ static hfx_status fail(hfx_status s, const std::string& m) {
   return s;
 }
 
+// Shared with the other translation units of the library.
+void hfx_set_last_error(const std::string& m) { g_err = m; }
+
 #define HFX_CK(x)                                                                          \
   do {                                                                                     \
     cudaError_t e_ = (x);                                                                  \

@@ -72,7 +72,7 @@ class ClassInfo(ctypes.Structure):
 
 EXPORTED = ["hfx_create_basis", "hfx_build_quartets", "hfx_value_count", "hfx_build_K", "hfx_exchange_energy",
             "hfx_pack_dense", "hfx_unpack_dense", "hfx_eval_quartets", "hfx_boys_eval", "hfx_get_stats",
-            "hfx_get_class_info", "hfx_batch_create", "hfx_batch_build_K",
+            "hfx_get_class_info", "hfx_exchange_energy_noalloc", "hfx_batch_create", "hfx_batch_build_K",
             "hfx_batch_energies", "hfx_batch_autotune", "hfx_batch_get_tuning", "hfx_batch_get_stats",
             "hfx_batch_destroy",
             "hfx_destroy_basis", "hfx_destroy_quartets", "hfx_last_error"]
@@ -100,6 +100,7 @@ def load(path: str = LIB_PATH):
     lib.hfx_unpack_dense.argtypes = [V, V, V, V]
     lib.hfx_eval_quartets.argtypes = [V, I, D, I, I, V, V, V, V]
     lib.hfx_boys_eval.argtypes = [V, I, I, I, V, V, V]
+    lib.hfx_exchange_energy_noalloc.argtypes = [V, V, LL, V, V]
     lib.hfx_batch_create.argtypes = [V, I, V, PV]
     lib.hfx_batch_build_K.argtypes = [V, V, V, I, V]
     lib.hfx_batch_energies.argtypes = [V, V, V]
@@ -236,6 +237,12 @@ def hfx_eval_quartets(basis, kernel, omega, precision, quartets, out_off, out, s
 def hfx_boys_eval(basis, precision, mmax, T, F, stream=None):
     _check(load().hfx_boys_eval(basis, int(precision), int(mmax), int(T.numel()), _ptr(T), _ptr(F),
                                 _stream(stream)))
+
+
+def hfx_exchange_energy_noalloc(P_val, K_val, n_values, E_x_dev, stream=None):
+    """E_x into a device double without any device allocation (see hfx.h)."""
+    _check(load().hfx_exchange_energy_noalloc(_ptr(P_val), _ptr(K_val), int(n_values), _ptr(E_x_dev),
+                                              _stream(stream)))
 
 
 def hfx_get_stats(q) -> Stats:
