@@ -17,6 +17,10 @@ LIB = os.path.join(HERE, "libhfx.so")
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", CSRC, "-I", GEN, "-I", INCLUDE]
+# HFX_CHECKED=1: a diagnostic build whose kernels test every global index of
+# the exchange-build path and report (printf) and skip out-of-range accesses.
+if os.environ.get("HFX_CHECKED", "0") not in ("", "0"):
+    FLAGS = FLAGS + ["-DHFX_CHECKED"]
 
 
 def _sources():
@@ -86,6 +90,11 @@ def build(verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    keep = set(objs)
+    for f in os.listdir(OBJ):  # objects of earlier source versions
+        path = os.path.join(OBJ, f)
+        if path not in keep and f.endswith(".o"):
+            os.remove(path)
     if verbose:
         print(f"built {LIB} from {len(objs)} objects")
     return LIB

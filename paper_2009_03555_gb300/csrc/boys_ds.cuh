@@ -105,6 +105,9 @@ template <int L>
 __device__ __forceinline__ void boys_ds(const float* __restrict__ tab, ds T, ds* F) {
   if (T.hi < (float)kBoysTmax) {
     const int it = __float2int_rn(T.hi * 16.0f);
+#ifdef HFX_CHECKED
+    if (!HFX_IN(it, kBoysNT, "boys_ds grid", L)) return;
+#endif
     const float Tk = (float)it * 0.0625f;
     const ds xs = two_sum(Tk, -T.hi);
     const ds x = fast_two_sum(xs.hi, __fadd_rn(xs.lo, -T.lo));
@@ -145,11 +148,12 @@ __device__ __forceinline__ void boys_ds(const float* __restrict__ tab, ds T, ds*
 // Primitive-quartet prologue of the mixed path, FP64-accurate in
 // double-single: T = rho |PQ|^2 from double-single P, Q, p, q; the Boys
 // function(s); the erfc difference F_m(T) - f^{m+1/2} F_m(f T) taken before
-// rounding; then G_m = pref * D_m rounded to FP32 (the prefactor
+// rounding; then G_m = pref * D_m rounded to FP32 (w2 = omega^2 as a
+// double-single pair formed once per launch; the prefactor
 // 2 pi^{5/2} K_ab K_cd / (p q sqrt(p+q)) needs no more: K_ab and K_cd were
 // formed in FP64 when the pairs were built).  Also returns FP32 1/(p+q) and PQ.
 template <int L>
-__device__ __forceinline__ void prologue_ds(const float* __restrict__ tab, int kernel, double omega2,
+__device__ __forceinline__ void prologue_ds(const float* __restrict__ tab, int kernel, ds w2,
                                             const PrimPair& pb, const PrimPair& pk, float* G, float& inv_s,
                                             float* PQf) {
   const ds p = {pb.pf, pb.plo}, q = {pk.pf, pk.plo};
@@ -176,7 +180,6 @@ __device__ __forceinline__ void prologue_ds(const float* __restrict__ tab, int k
       return;
     }
   }
-  const ds w2 = ds_from_double(omega2);
   const ds f = ds_mul(w2, ds_rcp(ds_add(w2, rho)));
   ds Fw[L + 1];
   boys_ds<L>(tab, ds_mul(f, T), Fw);

@@ -7,6 +7,26 @@
 
 namespace hfx {
 
+// Checked builds (compiled with -DHFX_CHECKED): every global index of the
+// split-kernel path is tested before use; an index outside its array is
+// reported with printf and the access is skipped.  Release builds compile the
+// tests away.
+#ifdef HFX_CHECKED
+}  // namespace hfx
+#include <cstdio>
+namespace hfx {
+static __device__ __noinline__ bool hfx_oob(const char* what, long long i, long long n, int cls) {
+  printf("HFX_CHECKED class %d %s: index %lld outside [0, %lld) (block %d thread %d)\n", cls, what, i, n,
+         (int)blockIdx.x, (int)threadIdx.x);
+  return false;
+}
+#define HFX_IN(i, n, what, cls) \
+  (((long long)(i) >= 0 && (long long)(i) < (long long)(n)) || hfx_oob(what, (long long)(i), (long long)(n), cls))
+#else
+#define HFX_IN(i, n, what, cls) true
+#endif
+
+
 constexpr int kMaxL = 2;                 // s, p, d shells
 constexpr int kMaxLtot = 4 * kMaxL;      // highest quartet angular momentum
 constexpr double kTwoPi52 = 34.98683665524972497;  // 2 pi^{5/2}
@@ -132,6 +152,9 @@ template <int L, int RSQ_STEPS>
 __device__ __forceinline__ void boys_fp64(const double* __restrict__ tab, double T, double* F) {
   if (T < kBoysTmax) {
     const int it = __double2int_rn(T * 16.0);
+#ifdef HFX_CHECKED
+    if (!HFX_IN(it, kBoysNT, "boys_fp64 grid", L)) return;
+#endif
     const double x = fma((double)it, kBoysStep, -T);  // T_k - T
     const double* row = tab + ((size_t)L * kBoysNT + it) * kBoysCols;
     const double2* r2 = reinterpret_cast<const double2*>(row);

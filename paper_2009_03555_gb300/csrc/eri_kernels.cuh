@@ -40,12 +40,15 @@ struct SysArgs {
   int n_blocks;
   int ns;
   int n_atoms;
+  int n_pairs[6];           // entries of pairs[c]
+  long long n_prims[6];     // entries of prims[c]
 };
 
 struct BuildArgs {
   const SysArgs* sys;     // device table of systems
   const Desc* desc;       // batches of this quartet class (Desc::sys = system id)
   int n_desc;
+  int n_sys;              // entries of sys
   int* counter;           // work-queue head (zeroed before the launch)
   int bra_class, ket_class;
   int same_class;         // bra class == ket class: canonical k >= bra rank
@@ -53,6 +56,7 @@ struct BuildArgs {
   const float* boysf;     // the same tables as double-single (mixed path)
   int kernel;             // Kernel
   double omega2;          // omega^2 of the attenuated kernels
+  float omega2_hi, omega2_lo;  // the same as a double-single pair (mixed path)
   int screen;             // Schwarz + P_scr > 0 tests on
   double tau;             // Schwarz threshold
   int dscreen;            // density screening on
@@ -87,6 +91,7 @@ struct EvalArgs {
   const float* boysf;
   int kernel;
   double omega2;
+  float omega2_hi, omega2_lo;
   double* out;
 };
 
@@ -102,7 +107,7 @@ __device__ __forceinline__ int contracted_quartet(const PairRec& bra, const Prim
                                                   const PairRec& ket, const PrimPair* __restrict__ kprims,
                                                   const double* __restrict__ boys,
                                                   const float* __restrict__ boysf, int kernel, double omega2,
-                                                  float eps_prim, R* __restrict__ out) {
+                                                  ds w2, float eps_prim, R* __restrict__ out) {
   constexpr bool kMixed = sizeof(R) == 4;
   constexpr int NR = kMixed ? 1 : 2;
   R acc[C::NACC], comp[C::NACC];
@@ -122,7 +127,7 @@ __device__ __forceinline__ int contracted_quartet(const PairRec& bra, const Prim
       ++n;
       R G[C::L + 1], PQ[3], rinv;
       if constexpr (kMixed) {
-        prologue_ds<C::L>(boysf, kernel, omega2, pb, pk, G, rinv, PQ);
+        prologue_ds<C::L>(boysf, kernel, w2, pb, pk, G, rinv, PQ);
       } else {
         double inv_s;
         prologue<C::L, NR>(boys, kernel, omega2, pb, pk, G, inv_s, PQ);
@@ -296,7 +301,8 @@ __global__ void __launch_bounds__(kThreadsK) k_build_K(const BuildArgs a) {
     if (a.same_class && it.y == it.z) fac *= 0.5;
     R out[C::NOUT];
     pdone += (unsigned long long)contracted_quartet<C, R>(bra, S.prims[a.bra_class], ket, S.prims[a.ket_class],
-                                                          a.boys, a.boysf, a.kernel, a.omega2, a.eps_prim, out);
+                                                          a.boys, a.boysf, a.kernel, a.omega2,
+                                                          ds{a.omega2_hi, a.omega2_lo}, a.eps_prim, out);
     scatter_K<C, R>(S, bra.A, bra.B, ket.A, ket.B, out, fac);
     ++done;
   };
@@ -364,6 +370,19 @@ struct CoopLayout {
   static constexpr size_t bytes() { return (size_t)(kThreadsCoop / 32) * PER_WARP * sizeof(R); }
 };
 
+#ifdef HFX_CHECKED
+// Checked builds: the n1 x n2 sub-block at rows l1.., columns l2.. of the
+// pattern block at offset o (row length nf) lies inside the value array.
+template <class C>
+__device__ __forceinline__ bool ep_blocks_ok(const SysArgs& S, const BuildArgs& a, long long o, int l1, int n1, int nf, int l2,
+                             int n2, const char* what) {
+  const int cc = a.bra_class * 10 + a.ket_class;
+  return HFX_IN(o + (long long)l1 * nf + l2, S.n_values, what, cc) &&
+         HFX_IN(o + (long long)(l1 + n1 - 1) * nf + l2 + n2 - 1, S.n_values, what, cc) &&
+         HFX_IN(l2 + n2 - 1, nf, what, cc);
+}
+#endif
+
 // Horizontal recursion (node tables, shared memory) on the contracted
 // [e0|f0] held in ws[0..NACC-1], then the four exchange contributions
 // (see scatter_K) spread over the lanes.  Whole warp.
@@ -396,12 +415,31 @@ __device__ __forceinline__ void quartet_epilogue(const BuildArgs& a, const SysAr
   if (a.same_class && bi == ki) fac *= 0.5;
   const int na = S.n_atoms;
   const int sA = bra.A, sB = bra.B, sC = ket.A, sD = ket.B;
+#ifdef HFX_CHECKED
+  {
+    const int cc = a.bra_class * 10 + a.ket_class;
+    if (!HFX_IN(sA, S.ns, "ep sA", cc) || !HFX_IN(sB, S.ns, "ep sB", cc) || !HFX_IN(sC, S.ns, "ep sC", cc) ||
+        !HFX_IN(sD, S.ns, "ep sD", cc))
+      return;
+    const int t0 = S.sh_atom[sA], t1 = S.sh_atom[sB], t2 = S.sh_atom[sC], t3 = S.sh_atom[sD];
+    if (!HFX_IN(t0, na, "ep atA", cc) || !HFX_IN(t1, na, "ep atB", cc) || !HFX_IN(t2, na, "ep atC", cc) ||
+        !HFX_IN(t3, na, "ep atD", cc))
+      return;
+  }
+#endif
   const int atA = S.sh_atom[sA], atB = S.sh_atom[sB], atC = S.sh_atom[sC], atD = S.sh_atom[sD];
   const int lA = S.sh_loc[sA], lB = S.sh_loc[sB], lC = S.sh_loc[sC], lD = S.sh_loc[sD];
   const int nfC = S.atom_nf[atC], nfD = S.atom_nf[atD];
   const long long oAC = S.blk_off[atA * na + atC], oAD = S.blk_off[atA * na + atD];
   const long long oBC = S.blk_off[atB * na + atC], oBD = S.blk_off[atB * na + atD];
+#ifdef HFX_CHECKED
+  const bool h1 = oAC >= 0 && oBD >= 0 && ep_blocks_ok<C>(S, a, oAC, lA, C::NA, nfC, lC, C::NC, "AC") &&
+                  ep_blocks_ok<C>(S, a, oBD, lB, C::NB, nfD, lD, C::ND, "BD");
+  const bool h2 = oBC >= 0 && oAD >= 0 && ep_blocks_ok<C>(S, a, oBC, lB, C::NB, nfC, lC, C::NC, "BC") &&
+                  ep_blocks_ok<C>(S, a, oAD, lA, C::NA, nfD, lD, C::ND, "AD");
+#else
   const bool h1 = oAC >= 0 && oBD >= 0, h2 = oBC >= 0 && oAD >= 0;
+#endif
   // P blocks into the (now free) prologue buffer: BD | AC | AD | BC
   R* pBD = pbuf;
   R* pAC = pBD + NB * ND;
@@ -485,7 +523,7 @@ __device__ __forceinline__ void coop_quartet(const BuildArgs& a, const SysArgs& 
         R* rec = pbuf + lane * Lay::PB;
         R G[NG], PQ[3], rinv;
         if constexpr (kMixed) {
-          prologue_ds<C::L>(a.boysf, a.kernel, a.omega2, pb, pk, G, rinv, PQ);
+          prologue_ds<C::L>(a.boysf, a.kernel, ds{a.omega2_hi, a.omega2_lo}, pb, pk, G, rinv, PQ);
         } else {
           double inv_s;
           prologue<C::L, NR>(a.boys, a.kernel, a.omega2, pb, pk, G, inv_s, PQ);
@@ -608,6 +646,17 @@ __global__ void __launch_bounds__(kThreadsCoop) k_build_K_coop(const BuildArgs a
     d = __shfl_sync(0xffffffffu, d, 0);
     if (d >= a.n_desc) break;
     const Desc ds = a.desc[d];
+#ifdef HFX_CHECKED
+    {
+      const int cc = a.bra_class * 10 + a.ket_class;
+      if (!HFX_IN(ds.sys, a.n_sys, "desc.sys", cc)) continue;
+      const SysArgs& S0 = a.sys[ds.sys];
+      if (!HFX_IN(ds.bra, S0.n_pairs[a.bra_class], "desc.bra", cc)) continue;
+      if (ds.k1 > ds.k0 && (!HFX_IN(ds.k0, S0.n_pairs[a.ket_class], "desc.k0", cc) ||
+                            !HFX_IN(ds.k1 - 1, S0.n_pairs[a.ket_class], "desc.k1", cc)))
+        continue;
+    }
+#endif
     const SysArgs& S = a.sys[ds.sys];
     const PairRec bra = S.pairs[a.bra_class][ds.bra];
     const PairRec* __restrict__ kets = S.pairs[a.ket_class];
@@ -658,6 +707,20 @@ __device__ __forceinline__ void split_quartet(const BuildArgs& a, const SysArgs&
   const PairRec bra = S.pairs[a.bra_class][bi], ket = S.pairs[a.ket_class][ki];
   const PrimPair* __restrict__ bprims = S.prims[a.bra_class];
   const PrimPair* __restrict__ kprims = S.prims[a.ket_class];
+#ifdef HFX_CHECKED
+  {
+    const int cc = a.bra_class * 10 + a.ket_class;
+    if (bra.pcnt < 0 || ket.pcnt < 0 || bra.pcnt > 64 || ket.pcnt > 64) {
+      hfx_oob("pcnt", bra.pcnt * 1000LL + ket.pcnt, 64, cc);
+      return;
+    }
+    if ((bra.pcnt > 0 && (!HFX_IN(bra.poff, S.n_prims[a.bra_class], "bra.poff", cc) ||
+                          !HFX_IN(bra.poff + bra.pcnt - 1, S.n_prims[a.bra_class], "bra.poff+pcnt", cc))) ||
+        (ket.pcnt > 0 && (!HFX_IN(ket.poff, S.n_prims[a.ket_class], "ket.poff", cc) ||
+                          !HFX_IN(ket.poff + ket.pcnt - 1, S.n_prims[a.ket_class], "ket.poff+pcnt", cc))))
+      return;
+  }
+#endif
   R acc[C::NCHUNK], comp[C::NCHUNK];
 #pragma unroll
   for (int k = 0; k < C::NCHUNK; ++k) {
@@ -701,7 +764,7 @@ __device__ __forceinline__ void split_quartet(const BuildArgs& a, const SysArgs&
       const PrimPair& pb = bprims[bra.poff + ib];
       const PrimPair& pk = kprims[ket.poff + ik];
       if constexpr (kMixed) {
-        prologue_ds<C::L>(a.boysf, a.kernel, a.omega2, pb, pk, G, rinv, PQ);
+        prologue_ds<C::L>(a.boysf, a.kernel, ds{a.omega2_hi, a.omega2_lo}, pb, pk, G, rinv, PQ);
       } else {
         double inv_s;
         prologue<C::L, NR>(a.boys, a.kernel, a.omega2, pb, pk, G, inv_s, PQ);
@@ -753,6 +816,17 @@ __global__ void __launch_bounds__(kThreadsSplit) k_build_K_split(const BuildArgs
     d = __shfl_sync(0xffffffffu, d, 0);
     if (d >= a.n_desc) break;
     const Desc ds = a.desc[d];
+#ifdef HFX_CHECKED
+    {
+      const int cc = a.bra_class * 10 + a.ket_class;
+      if (!HFX_IN(ds.sys, a.n_sys, "desc.sys", cc)) continue;
+      const SysArgs& S0 = a.sys[ds.sys];
+      if (!HFX_IN(ds.bra, S0.n_pairs[a.bra_class], "desc.bra", cc)) continue;
+      if (ds.k1 > ds.k0 && (!HFX_IN(ds.k0, S0.n_pairs[a.ket_class], "desc.k0", cc) ||
+                            !HFX_IN(ds.k1 - 1, S0.n_pairs[a.ket_class], "desc.k1", cc)))
+        continue;
+    }
+#endif
     const SysArgs& S = a.sys[ds.sys];
     const PairRec bra = S.pairs[a.bra_class][ds.bra];
     const PairRec* __restrict__ kets = S.pairs[a.ket_class];
@@ -785,7 +859,8 @@ __global__ void __launch_bounds__(64) k_schwarz(const SchwarzArgs a) {
     if (i >= a.n_pairs || a.pair_class[i] != a.cls) return;
     const PairRec pr = a.pairs[i];
     double out[C::NOUT];
-    contracted_quartet<C, double>(pr, a.prims, pr, a.prims, a.boys, nullptr, a.kernel, a.omega2, 0.f, out);
+    contracted_quartet<C, double>(pr, a.prims, pr, a.prims, a.boys, nullptr, a.kernel, a.omega2, ds{0.f, 0.f}, 0.f,
+                                  out);
     double mx = 0.0;
 #pragma unroll
     for (int x = 0; x < C::NA; ++x)
@@ -806,7 +881,8 @@ __global__ void __launch_bounds__(64) k_eval(const EvalArgs a) {
   if (q.z != a.cls) return;
   const PairRec bra = a.pairs[q.x], ket = a.pairs[q.y];
   R out[C::NOUT];
-  contracted_quartet<C, R>(bra, a.prims, ket, a.prims, a.boys, a.boysf, a.kernel, a.omega2, 0.f, out);
+  contracted_quartet<C, R>(bra, a.prims, ket, a.prims, a.boys, a.boysf, a.kernel, a.omega2,
+                           ds{a.omega2_hi, a.omega2_lo}, 0.f, out);
   const int4 st = a.strides[i];
   double* o = a.out + a.out_off[i];
 #pragma unroll

@@ -603,6 +603,8 @@ static void fill_sys(hfx_quartets_s* q) {
   for (int c = 0; c < 6; ++c) {
     S.pairs[c] = q->pairs[c].p;
     S.prims[c] = q->prims[c].p;
+    S.n_pairs[c] = (int)q->n_pairs[c];
+    S.n_prims[c] = (long long)q->prims[c].n;
   }
   S.pmax = q->pmax.p;
   S.P = nullptr;
@@ -731,6 +733,7 @@ static BuildArgs plan_args(Plan& pl, int cls) {
   a.sys = pl.d_sys.p;
   a.desc = pl.descp[cls];
   a.n_desc = pl.n_desc[cls];
+  a.n_sys = pl.n;
   a.bra_class = hfx_class_table[cls][0];
   a.ket_class = hfx_class_table[cls][1];
   a.same_class = a.bra_class == a.ket_class;
@@ -738,6 +741,8 @@ static BuildArgs plan_args(Plan& pl, int cls) {
   a.boysf = pl.boysf;
   a.kernel = o.kernel;
   a.omega2 = o.omega * o.omega;
+  a.omega2_hi = (float)a.omega2;
+  a.omega2_lo = (float)(a.omega2 - (double)a.omega2_hi);
   a.screen = o.screen;
   a.tau = o.tau;
   a.dscreen = o.density_screen;
@@ -776,6 +781,18 @@ static hfx_status plan_classes(Plan& pl, cudaStream_t s, bool fork, bool events)
       const int g = plan_grid(pl, fp32, cls);
       if (events) HFX_CK(cudaEventRecord(pl.evk[pass][cls][0], cs));
       kClassOps[cls].launch_K(a, fp32, g, cs);
+#ifdef HFX_CHECKED
+      {  // checked builds: finish each class kernel before the next (outside capture)
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing(cs, &cap);
+        if (cap == cudaStreamCaptureStatusNone) {
+          const cudaError_t e = cudaStreamSynchronize(cs);
+          if (e != cudaSuccess)
+            return fail(HFX_ERR_CUDA, "class " + std::to_string(cls) + " pass " + std::to_string(pass) + ": " +
+                                          cudaGetErrorString(e));
+        }
+      }
+#endif
       if (events) HFX_CK(cudaEventRecord(pl.evk[pass][cls][1], cs));
       pl.ran[pass][cls] = true;
     }
@@ -1295,6 +1312,8 @@ hfx_status hfx_eval_quartets(hfx_basis* b, int kernel, double omega, int precisi
     a.boysf = b->boysf.p;
     a.kernel = kernel;
     a.omega2 = omega * omega;
+    a.omega2_hi = (float)a.omega2;
+    a.omega2_lo = (float)(a.omega2 - (double)a.omega2_hi);
     a.out = out;
     kClassOps[cls].launch_eval(a, precision == HFX_PREC_MIXED, s);
   }
