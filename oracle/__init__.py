@@ -63,6 +63,8 @@ def _load():
         lib.oracle_schwarz.argtypes = [I, P, P, P, P, P, P, I, D, P]
         lib.oracle_build_K.argtypes = [I, P, P, P, P, P, P, P, I, D, I, D, I, D, I, I, I, I, P]
         lib.oracle_build_K.restype = ctypes.c_longlong
+        lib.oracle_K_shell_pairs.argtypes = [I, P, P, P, P, P, P, P, I, D, I, D, I, D, I, P, P, I, P, P, P]
+        lib.oracle_K_shell_pairs.restype = ctypes.c_longlong
         lib.oracle_max_threads.restype = I
         _lib = lib
     return _lib
@@ -152,6 +154,33 @@ def build_K(basis, P, kernel: int = KERNEL_COULOMB, omega: float = 0.11, screen:
                                float(tau), int(bool(density_screen)), float(eps), int(bool(brute)),
                                int(bra_stride), int(bra_offset), nt, _p(K))
     return K, int(n)
+
+
+def K_shell_pairs(basis, P, pairs, kernel: int = KERNEL_COULOMB, omega: float = 0.11,
+                  screen: bool = False, tau: float = 1e-8, density_screen: bool = False,
+                  eps: float = 1e-8, nthreads: int | None = None):
+    """Exchange blocks K_IJ of the listed shell pairs (I, J) straight from the
+    definition (all ordered (K, L) whose quartet (I K | J L) survives).
+    Returns (blocks, W1, W0, n): lists of (nI, nJ) arrays -- K, the weights
+    sum Q_IK Q_JL sum|P_kl| and sum |P_kl| over the surviving (K, L) -- and the
+    number of surviving ordered shell quartets."""
+    b = _basis(basis)
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    assert P.shape == (b.nbf, b.nbf)
+    pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+    nf = np.diff(b.func_off)
+    sizes = (nf[pr[:, 0]] * nf[pr[:, 1]]).astype(np.int64)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    K = np.zeros(int(off[-1]))
+    W1 = np.zeros_like(K)
+    W0 = np.zeros_like(K)
+    nt = max_threads() if nthreads is None else int(nthreads)
+    n = _load().oracle_K_shell_pairs(*b.args(), _p(P), int(kernel), float(omega), int(bool(screen)),
+                                     float(tau), int(bool(density_screen)), float(eps), int(pr.shape[0]),
+                                     _p(pr), _p(off), nt, _p(K), _p(W1), _p(W0))
+    shp = [(int(nf[i]), int(nf[j])) for i, j in pr]
+    cut = lambda a: [a[off[q]:off[q + 1]].reshape(shp[q]) for q in range(pr.shape[0])]
+    return cut(K), cut(W1), cut(W0), int(n)
 
 
 def exchange_energy(P, K) -> float:

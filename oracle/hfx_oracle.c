@@ -470,6 +470,104 @@ long long oracle_build_K(int n_shells, const double *xyz, const int *l, const in
   return count;
 }
 
+/* The exchange block K_IJ (functions of shell I x functions of shell J) of a
+ * list of shell pairs, straight from the definition (Eq. H-HFX without -1/2):
+ * K_ij = sum over all ordered shell pairs (K, L) whose quartet (I K | J L)
+ * survives the screening, of sum_{k in K, l in L} (ik|jl) P_kl.
+ * Only the Schwarz bounds Q_IK and Q_JL of the listed shells are computed,
+ * so single blocks of large systems cost O(n_shells^2) predicate tests and
+ * one shell quartet per surviving (K, L).
+ * out_off[p]: start of pair p's nI x nJ block in K_out (row-major).
+ * W1_out, W0_out (same layout, may be NULL): over the same surviving (K, L),
+ *   W1_ij = sum Q_IK Q_JL sum_{k,l} |P_kl|   and   W0_ij = sum sum_{k,l} |P_kl|,
+ * the weights with which a per-integral error bound (relative to Q_IK Q_JL,
+ * or absolute) carries into K_ij.
+ * Returns the number of surviving ordered shell quartets. */
+long long oracle_K_shell_pairs(int n_shells, const double *xyz, const int *l, const int *prim_off,
+                               const double *alpha, const double *coef, const long long *func_off,
+                               const double *P, int kernel, double omega, int screen, double tau,
+                               int dscreen, double eps, int n_pairs, const int *pairs /* n x 2 */,
+                               const long long *out_off, int nthreads, double *K_out, double *W1_out,
+                               double *W0_out) {
+  basis_t B;
+  fill_basis(&B, n_shells, xyz, l, prim_off, alpha, coef, func_off);
+  int ns = n_shells, nbf = B.nbf;
+  double *Pm = (double *)calloc((size_t)ns * ns, sizeof(double));
+  double *Q = (double *)calloc((size_t)ns * ns, sizeof(double));
+  shell_pmax(&B, P, Pm);
+  if (nthreads <= 0) nthreads = 1;
+  long long count = 0;
+  for (int q = 0; q < n_pairs; ++q) {
+    const int I = pairs[2 * q], J = pairs[2 * q + 1];
+    const int nI = ncart(l[I]), nJ = ncart(l[J]);
+    /* Schwarz rows of I and J (the run's kernel), written into the dense table
+     * the screening predicate reads */
+    if (screen) {
+      const int rows[2] = {I, J};
+      for (int r = 0; r < 2; ++r) {
+        const int X = rows[r];
+#pragma omp parallel for num_threads(nthreads) schedule(dynamic, 8)
+        for (int Y = 0; Y < ns; ++Y) {
+          double buf[MAXC * MAXC * MAXC * MAXC];
+          shell_quartet(&B, X, Y, X, Y, kernel, omega, buf);
+          int nX = ncart(l[X]), nY = ncart(l[Y]);
+          double mx = 0.0;
+          for (int a = 0; a < nX; ++a)
+            for (int b = 0; b < nY; ++b) {
+              double v = fabs(buf[((a * nY + b) * nX + a) * nY + b]);
+              if (v > mx) mx = v;
+            }
+          Q[X * ns + Y] = Q[Y * ns + X] = sqrt(mx);
+        }
+      }
+    }
+    double *Kb = K_out + out_off[q];
+    memset(Kb, 0, sizeof(double) * nI * nJ);
+    if (W1_out) memset(W1_out + out_off[q], 0, sizeof(double) * nI * nJ);
+    if (W0_out) memset(W0_out + out_off[q], 0, sizeof(double) * nI * nJ);
+    long long cnt = 0;
+#pragma omp parallel num_threads(nthreads) reduction(+ : cnt)
+    {
+      double kt[MAXC * MAXC] = {0}, w1[MAXC * MAXC] = {0}, w0[MAXC * MAXC] = {0};
+      double g[MAXC * MAXC * MAXC * MAXC];
+#pragma omp for schedule(dynamic, 1)
+      for (int Ks = 0; Ks < ns; ++Ks)
+        for (int Ls = 0; Ls < ns; ++Ls) {
+          if (!survives(ns, Q, Pm, screen, tau, dscreen, eps, I, Ks, J, Ls)) continue;
+          ++cnt;
+          shell_quartet(&B, I, Ks, J, Ls, kernel, omega, g);
+          const int nK = ncart(l[Ks]), nL = ncart(l[Ls]);
+          double pabs = 0.0;
+          for (int k = 0; k < nK; ++k)
+            for (int d = 0; d < nL; ++d) pabs += fabs(P[(func_off[Ks] + k) * nbf + func_off[Ls] + d]);
+          const double qq = screen ? Q[I * ns + Ks] * Q[J * ns + Ls] : 0.0;
+          for (int a = 0; a < nI; ++a)
+            for (int b = 0; b < nJ; ++b) {
+              double s = 0.0;
+              for (int k = 0; k < nK; ++k)
+                for (int d = 0; d < nL; ++d)
+                  s += g[((a * nK + k) * nJ + b) * nL + d] * P[(func_off[Ks] + k) * nbf + func_off[Ls] + d];
+              kt[a * nJ + b] += s;
+              w1[a * nJ + b] += qq * pabs;
+              w0[a * nJ + b] += pabs;
+            }
+        }
+#pragma omp critical
+      {
+        for (int x = 0; x < nI * nJ; ++x) {
+          Kb[x] += kt[x];
+          if (W1_out) W1_out[out_off[q] + x] += w1[x];
+          if (W0_out) W0_out[out_off[q] + x] += w0[x];
+        }
+      }
+    }
+    count += cnt;
+  }
+  free(Q);
+  free(Pm);
+  return count;
+}
+
 int oracle_max_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();

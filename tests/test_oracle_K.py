@@ -140,3 +140,38 @@ def test_screening_error_bound(tiny):
     bound = dropped * 8 * 36 * max(tau * np.abs(P).max(), eps)
     diff = np.abs(Ks - Kf).max()
     assert 0.0 < diff <= bound
+
+
+def test_K_shell_pairs_equals_full_tensor(tiny):
+    """Single exchange blocks from the definition equal the full ERI tensor
+    contracted with P (unscreened), for every shell pair, with W0 = sum |P|."""
+    s, P, b = tiny
+    G = _full_tensor(s, b, oracle.KERNEL_ERFC)
+    Kref = np.einsum("ikjl,kl->ij", G, P)
+    fo = s.func_off
+    pairs = [(I, J) for I in range(s.n_shells) for J in range(s.n_shells)]
+    blocks, _, W0, n = oracle.K_shell_pairs(b, P, pairs, kernel=oracle.KERNEL_ERFC)
+    assert n == s.n_shells ** 4
+    for (I, J), k, w0 in zip(pairs, blocks, W0):
+        np.testing.assert_allclose(k, Kref[fo[I]:fo[I + 1], fo[J]:fo[J + 1]], rtol=0,
+                                   atol=1e-13 * np.abs(Kref).max())
+        np.testing.assert_allclose(w0, np.abs(P).sum(), rtol=1e-13)
+
+
+def test_K_shell_pairs_screened_equals_brute(tiny):
+    """With Schwarz and density screening the blocks equal the brute-force K
+    (all ordered quartets, same predicate) and count the same quartets."""
+    s, P, b = tiny
+    kw = dict(kernel=oracle.KERNEL_ERFC, screen=True, tau=1e-5, density_screen=True, eps=1e-5)
+    Kb, nb = oracle.build_K(b, P, brute=True, **kw)
+    fo = s.func_off
+    pairs = [(I, J) for I in range(s.n_shells) for J in range(s.n_shells)]
+    blocks, W1, W0, n = oracle.K_shell_pairs(b, P, pairs, **kw)
+    assert n == nb
+    Q = oracle.schwarz(b, oracle.KERNEL_ERFC)
+    for (I, J), k, w1, w0 in zip(pairs, blocks, W1, W0):
+        np.testing.assert_allclose(k, Kb[fo[I]:fo[I + 1], fo[J]:fo[J + 1]], rtol=0,
+                                   atol=1e-13 * np.abs(Kb).max())
+        # Schwarz: |K_ij| <= sum over surviving (K,L) of Q_IK Q_JL sum |P_kl| = W1
+        assert np.all(np.abs(k) <= w1 * (1 + 1e-12) + 1e-300)
+        assert np.all(w1 <= Q.max() ** 2 * w0 * (1 + 1e-12))
