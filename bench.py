@@ -220,7 +220,8 @@ def run_ours(args, rank, world):
         u64, u32 = a64 / FP64_PEAK_TFLOPS, a32 / FP32_PEAK_TFLOPS
         pipe = "fp64" if u64 >= u32 else "fp32"
         roof = {"bound": "alu", "pipe": pipe,
-                "kernel": f"k_build_K<Cls{ci.la}{ci.lb}{ci.lc}{ci.ld},{'float' if fp32 else 'double'}>",
+                "kernel": f"{hfx.KERNEL_KIND_NAMES[ci.kernel_kind]}<Cls{ci.la}{ci.lb}{ci.lc}{ci.ld}, "
+                          f"{'float' if fp32 else 'double'}>",
                 "achieved": round(a64 if pipe == "fp64" else a32, 4),
                 "peak": round(FP64_PEAK_TFLOPS if pipe == "fp64" else FP32_PEAK_TFLOPS, 3),
                 "unit": "TFLOP/s", "frac": round(max(u64, u32), 4),
@@ -250,7 +251,8 @@ def run_ours(args, rank, world):
         "quartets_per_build": n_q, "prim_quartets_per_build": n_pq,
         "eri_quartets_per_s": world * n_q / (ms * 1e-3),
         "E_x": E, "setup_ms": st.ms_setup,
-        "gpu_launches": args.steps * (3 + sum(1 for p in range(2) for c in range(hfx.N_CLASSES)
+        # per step: zero K, Pmax, the class kernels, symmetrise, E_x partials (build), E_x (energy call)
+        "gpu_launches": args.steps * (5 + sum(1 for p in range(2) for c in range(hfx.N_CLASSES)
                                             if st.n_quartets_pass[p][c] > 0 or st.ms_class_pass[p][c] > 0)),
         "clocks": clocks, "e2e": e2e, "roofline": roof, "per_class": per_class,
     }
@@ -316,6 +318,82 @@ def run_reference(args, rank, world):
             "e2e": {"value": value, "unit": "builds/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_serve(args):
+    """--serve: continuous batching of a seeded stream of SCF-like requests
+    (chains and slabs, `--serve-builds` builds each with P perturbed by 1e-3
+    per build, Poisson arrivals) through hfx_server_*; latency is measured
+    from each request's scheduled arrival to the end of its last build."""
+    import torch
+    from paper_2009_03555_gb300 import hfx
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    rng = np.random.default_rng(2009_03555 + 4)
+    n = args.serve_requests
+    arrivals = np.cumsum(rng.exponential(1.0 / args.serve_rate, size=n))
+    c0, c1 = (int(x) for x in args.serve_chain.split(","))
+    s0, s1 = (int(x) for x in args.serve_slab.split(","))
+    kinds = rng.integers(0, 2, size=n)
+    sizes = [int(rng.integers(c0, c1 + 1)) if k == 0 else int(rng.integers(s0, s1 + 1)) for k in kinds]
+    prec = hfx.HFX_PREC_MIXED if args.precision == "mixed" else hfx.HFX_PREC_FP64
+    opts = hfx.make_opts(kernel=hfx.HFX_KERNEL_ERFC, omega=0.11, screen=True, tau=1e-8, density_screen=True,
+                         eps=1e-8, prim_cutoff=args.prim_cutoff, precision=prec, n_block=args.n_block)
+    reqs = []
+    for i, (k, na) in enumerate(zip(kinds, sizes)):
+        s = synth.ch_chain(na, sub=i) if k == 0 else synth.ch_slab(na, sub=i)
+        mask = synth.atom_pair_mask(s, 14.0)
+        P = synth.density_matrix(s, 4, cutoff=14.0, sub=i)
+        pr = np.random.default_rng(2009_03555 + 1000 + i)
+        Ps = [P]
+        for _ in range(args.serve_builds - 1):
+            Ps.append(synth.perturb_density(Ps[-1], pr))
+        reqs.append((s, mask, Ps))
+
+    def serve(use_graph, m):
+        srv = hfx.Server(use_graph=use_graph)
+        tickets = [None] * m
+        t0 = time.perf_counter()
+        nxt, finished, lat = 0, 0, [None] * m
+        while finished < m:
+            now = time.perf_counter() - t0
+            while nxt < m and arrivals[nxt] <= now:
+                s, mask, Ps = reqs[nxt]
+                tickets[nxt] = srv.submit(s, mask, opts, Ps, want_K=False)
+                nxt += 1
+            info = srv.info()
+            if info.n_active == 0 and info.n_queued == 0:
+                if nxt < m:
+                    time.sleep(max(0.0, arrivals[nxt] - (time.perf_counter() - t0)))
+                continue
+            srv.step()
+            for i in range(nxt):
+                if lat[i] is None:
+                    ri, _ = srv.poll(tickets[i])
+                    if ri.state in (hfx.HFX_REQ_DONE, hfx.HFX_REQ_FAILED):
+                        lat[i] = (time.perf_counter() - t0) - arrivals[i]
+                        finished += 1
+        makespan = time.perf_counter() - t0
+        return srv.info(), makespan, np.array(lat)
+
+    serve(args.serve_graph, min(n, 4))  # warm-up (library load, first launches)
+    torch.cuda.synchronize()
+    clk = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clk.start()
+    info, makespan, lat = serve(args.serve_graph, n)
+    clocks = clk.stop()
+    builds = n * args.serve_builds
+    return {"metric": "hfx_serving_builds_per_s", "value": builds / makespan, "unit": "builds/s", "n_gpus": 1,
+            "higher_is_better": True, "dtype": "f32+f64" if prec == hfx.HFX_PREC_MIXED else "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{n} requests, Poisson {args.serve_rate}/s, {args.serve_builds} builds each "
+                                   f"(P perturbed 1e-3), C/H chains {c0}-{c1} atoms and slabs {s0}-{s1} atoms, "
+                                   f"HSE erfc w=0.11, Schwarz 1e-8 + density screening, {args.precision}",
+                       "use_graph": bool(args.serve_graph), "precision": args.precision},
+            "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3),
+                           "max": float(lat.max() * 1e3), "mean": float(lat.mean() * 1e3)},
+            "makespan_s": makespan, "builds": builds, "max_active": info.max_active_seen,
+            "peak_device_bytes": info.peak_used_bytes, "steps": info.steps, "clocks": clocks}
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -331,7 +409,17 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--ref-quartets-per-build", type=float, default=None)
+    ap.add_argument("--serve", action="store_true", help="continuous-batching serving stream instead of one build")
+    ap.add_argument("--serve-requests", type=int, default=64)
+    ap.add_argument("--serve-rate", type=float, default=50.0)
+    ap.add_argument("--serve-builds", type=int, default=5)
+    ap.add_argument("--serve-chain", default="50,200", help="chain sizes (atoms), min,max")
+    ap.add_argument("--serve-slab", default="36,100", help="slab sizes (atoms), min,max")
+    ap.add_argument("--serve-graph", type=int, default=0)
     args = ap.parse_args()
+    if args.serve:
+        print(json.dumps(run_serve(args)), flush=True)
+        return 0
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":

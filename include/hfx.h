@@ -117,6 +117,8 @@ typedef struct {
   int n_out;                  /* Cartesian integrals per quartet */
   int vrr_flops;              /* flops of the vertical recursion per primitive quartet */
   int hrr_flops;              /* flops of the horizontal recursion per quartet */
+  int n_acc;                  /* contracted [e0|f0] accumulators per quartet */
+  int kernel_kind;            /* 0 per-thread k_build_K, 1 warp-split k_build_K_split, 2 cooperative k_build_K_coop */
 } hfx_class_info;
 
 /* Basis creation (setup).  Copies shells, normalises contraction coefficients
@@ -219,6 +221,98 @@ hfx_status hfx_batch_get_tuning(hfx_batch* b, int* n_block, int* grid);
 hfx_status hfx_batch_get_stats(hfx_batch* b, hfx_stats* out);
 
 void hfx_batch_destroy(hfx_batch* b);
+
+/* ---- Memory accounting and host-side value layout ---------------------- */
+
+/* Device bytes held by a quartet list (pairs, primitive pairs, work queues,
+ * pattern tables, Pmax, build plan) or by a basis; -1 for NULL. */
+long long hfx_quartets_device_bytes(const hfx_quartets* q);
+long long hfx_basis_device_bytes(const hfx_basis* basis);
+
+/* Number of P / K values of a pattern over these shells (host only; the same
+ * count hfx_value_count reports once the quartet list exists); -1 when the
+ * shells or the pattern are inconsistent. */
+long long hfx_pattern_value_count(const hfx_shell_desc* shells, int n_shells, const hfx_pattern* pattern);
+
+/* Host-side pack of a dense nbf x nbf row-major matrix into the pattern's
+ * value layout (blocks in CSR order, row-major inside a block). */
+hfx_status hfx_pack_dense_host(const hfx_shell_desc* shells, int n_shells, const hfx_pattern* pattern,
+                               const double* dense, double* val);
+
+/* Upper estimate of the device bytes a basis plus hfx_build_quartets need at
+ * their peak for these shells and pattern (all shell pairs with their
+ * primitive pairs during setup, plus what stays resident); -1 on bad input. */
+long long hfx_setup_bytes_estimate(const hfx_shell_desc* shells, int n_shells, const hfx_pattern* pattern);
+
+/* ---- Serving: continuous batching of independent requests -------------
+ * No counterpart in the paper, whose runs build one system's K once per SCF
+ * iteration; a server interleaves many such SCF-like runs on one GPU.
+ * A request is one system with n_builds density matrices; it is set up once
+ * (basis, Schwarz pair lists, work queues: Sec. 2) and its builds run while
+ * it stays resident.  hfx_server_step() admits queued requests in arrival
+ * order while their estimated device memory (hfx_setup_bytes_estimate plus
+ * the P and K arrays) fits under mem_budget -- a request larger than the
+ * whole budget fails with HFX_ERR_OOM, otherwise the queue head waits for
+ * retirements --, runs one build of every active request (requests sharing
+ * kernel, precision and screening options share one batched build, see the
+ * batch functions), and retires finished requests.  One host thread drives a
+ * server (not thread-safe); all work is on the stream given at creation, and
+ * hfx_server_step() synchronises it. */
+typedef struct hfx_server_s hfx_server;
+
+typedef enum { HFX_REQ_QUEUED = 0, HFX_REQ_ACTIVE = 1, HFX_REQ_DONE = 2, HFX_REQ_FAILED = 3 } hfx_request_state;
+
+typedef struct {
+  long long mem_budget; /* device bytes for admitted requests; <= 0: 80% of the free memory at creation */
+  int max_active;       /* at most this many active requests; <= 0: 64 */
+  int use_graph;        /* capture each batched build as a CUDA graph (re-captured when the active set changes) */
+  int reserved[4];
+} hfx_server_opts;
+
+typedef struct {
+  int state;              /* hfx_request_state */
+  int status;             /* hfx_status of a failed request (HFX_OK otherwise) */
+  int builds_done;
+  int n_builds;
+  double t_submit;        /* seconds since hfx_server_create; -1 = not yet */
+  double t_admit;
+  double t_done;
+  long long device_bytes; /* device bytes held while active */
+} hfx_request_info;
+
+typedef struct {
+  long long mem_budget;
+  long long used_bytes;      /* held by active requests */
+  long long peak_used_bytes;
+  long long builds_done;
+  long long steps;
+  int n_queued, n_active, max_active_seen, reserved;
+} hfx_server_info;
+
+hfx_status hfx_server_create(const hfx_server_opts* opts, void* stream, hfx_server** out);
+
+/* Queue a request.  shells, atom_xyz, pattern, opts: copied.  P_host: host
+ * array of n_builds x value-count doubles (build i reads row i), owned by the
+ * caller and read until the request is done.  K_out: host array of
+ * value-count doubles receiving the K of the last build (may be NULL), owned
+ * by the caller.  *ticket identifies the request. */
+hfx_status hfx_server_submit(hfx_server* srv, const hfx_shell_desc* shells, int n_shells, const double* atom_xyz,
+                             int n_atoms, const hfx_pattern* pattern, const hfx_opts* opts, int n_builds,
+                             const double* P_host, double* K_out, long long* ticket);
+
+/* Admission, one build of every active request, retirement (see above).
+ * *n_active (may be NULL): active requests after the step. */
+hfx_status hfx_server_step(hfx_server* srv, int* n_active);
+
+/* State of a request; E_x (may be NULL): host array of n_builds, the energies
+ * of the builds done so far. */
+hfx_status hfx_server_poll(hfx_server* srv, long long ticket, hfx_request_info* info, double* E_x);
+
+/* Forget a finished (done or failed) request; HFX_ERR_BUSY otherwise. */
+hfx_status hfx_server_release(hfx_server* srv, long long ticket);
+
+hfx_status hfx_server_get_info(hfx_server* srv, hfx_server_info* out);
+void hfx_server_destroy(hfx_server* srv);
 
 /* Static per-class information; cls in [0, 21). */
 hfx_status hfx_get_class_info(int cls, hfx_class_info* out);

@@ -280,7 +280,8 @@ def gen_class(ib, ik, la, lb, lc, ld):
     src.append("  }")
     src.append("};")
     info = dict(name=name, ib=ib, ik=ik, la=la, lb=lb, lc=lc, ld=ld, L=la + lb + lc + ld,
-                nout=NA * NB * NC * ND, nacc=len(v.E) * len(v.F), vrr_flops=v.flops, hrr_flops=h.flops)
+                nout=NA * NB * NC * ND, nacc=len(v.E) * len(v.F), vrr_flops=v.flops, hrr_flops=h.flops,
+                kind=2 if coop else (1 if split else 0))
     return "\n".join(src), info
 
 
@@ -303,11 +304,12 @@ def generate(outdir):
     # class table (host + device readable)
     tab = ["// GENERATED by gen_eri.py -- do not edit.", "#pragma once",
            f"#define HFX_NCLASS {len(classes)}",
-           "static const int hfx_class_table[HFX_NCLASS][10] = {",
-           "  // bra_class, ket_class, la, lb, lc, ld, L, nout, vrr_flops, hrr_flops"]
+           "static const int hfx_class_table[HFX_NCLASS][12] = {",
+           "  // bra_class, ket_class, la, lb, lc, ld, L, nout, vrr_flops, hrr_flops, n_acc,",
+           "  // kernel kind (0 per-thread k_build_K, 1 split k_build_K_split, 2 cooperative k_build_K_coop)"]
     for c in infos:
         tab.append(f"  {{{c['ib']}, {c['ik']}, {c['la']}, {c['lb']}, {c['lc']}, {c['ld']}, {c['L']}, "
-                   f"{c['nout']}, {c['vrr_flops']}, {c['hrr_flops']}}},")
+                   f"{c['nout']}, {c['vrr_flops']}, {c['hrr_flops']}, {c['nacc']}, {c['kind']}}},")
     tab.append("};")
     _write_if_changed(os.path.join(outdir, "class_table.h"), "\n".join(tab) + "\n")
     # launcher declarations and dispatch table, in class order

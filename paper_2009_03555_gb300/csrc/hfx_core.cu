@@ -868,6 +868,8 @@ hfx_status hfx_get_class_info(int cls, hfx_class_info* out) {
   out->n_out = t[7];
   out->vrr_flops = t[8];
   out->hrr_flops = t[9];
+  out->n_acc = t[10];
+  out->kernel_kind = t[11];
   return HFX_OK;
 }
 
@@ -1189,6 +1191,107 @@ hfx_status hfx_build_quartets(hfx_basis* b, const hfx_opts* opts_in, const hfx_p
 void hfx_destroy_quartets(hfx_quartets* q) { delete q; }
 
 long long hfx_value_count(const hfx_quartets* q) { return q ? q->n_values : -1; }
+
+}  // extern "C"
+
+template <typename T>
+static long long dbytes(const DBuf<T>& b) {
+  return (long long)(b.n * sizeof(T));
+}
+
+// Function count of every atom from a shell list (host); false on bad input.
+static bool atom_function_counts(const hfx_shell_desc* shells, int n_shells, int n_atoms, std::vector<long long>& nf) {
+  nf.assign((size_t)n_atoms, 0);
+  for (int i = 0; i < n_shells; ++i) {
+    const int a = shells[i].atom, l = shells[i].l;
+    if (a < 0 || a >= n_atoms || l < 0 || l > 2) return false;
+    nf[(size_t)a] += ncart(l);
+  }
+  return true;
+}
+
+extern "C" {
+
+long long hfx_quartets_device_bytes(const hfx_quartets* q) {
+  if (!q) return -1;
+  long long n = dbytes(q->blk_off) + dbytes(q->blk_x) + dbytes(q->blk_y) + dbytes(q->blk_val_off) +
+                dbytes(q->pmax) + dbytes(q->scratch);
+  for (int c = 0; c < 6; ++c) n += dbytes(q->pairs[c]) + dbytes(q->prims[c]);
+  for (int c = 0; c < HFX_NCLASS; ++c) n += dbytes(q->desc[c]) + dbytes(q->plan.desc_own[c]);
+  const Plan& pl = q->plan;
+  n += dbytes(pl.d_sys) + dbytes(pl.d_pmax) + dbytes(pl.counters) + dbytes(pl.n_done) + dbytes(pl.energy);
+  return n;
+}
+
+long long hfx_basis_device_bytes(const hfx_basis* b) {
+  if (!b) return -1;
+  return dbytes(b->sh_xyz) + dbytes(b->alpha) + dbytes(b->coef) + dbytes(b->boys) + dbytes(b->boysf) +
+         dbytes(b->sh_l) + dbytes(b->sh_atom) + dbytes(b->sh_poff) + dbytes(b->sh_loc) + dbytes(b->atom_nf);
+}
+
+long long hfx_pattern_value_count(const hfx_shell_desc* shells, int n_shells, const hfx_pattern* pattern) {
+  if (!shells || n_shells <= 0 || !pattern || !pattern->row_ptr || !pattern->col || pattern->n_atoms <= 0) return -1;
+  std::vector<long long> nf;
+  if (!atom_function_counts(shells, n_shells, pattern->n_atoms, nf)) return -1;
+  long long nv = 0;
+  for (int X = 0; X < pattern->n_atoms; ++X)
+    for (int k = pattern->row_ptr[X]; k < pattern->row_ptr[X + 1]; ++k) {
+      const int Y = pattern->col[k];
+      if (Y < 0 || Y >= pattern->n_atoms) return -1;
+      nv += nf[(size_t)X] * nf[(size_t)Y];
+    }
+  return nv;
+}
+
+hfx_status hfx_pack_dense_host(const hfx_shell_desc* shells, int n_shells, const hfx_pattern* pattern,
+                               const double* dense, double* val) {
+  if (!dense || !val) return fail(HFX_ERR_INVALID_ARG, "NULL argument");
+  if (hfx_pattern_value_count(shells, n_shells, pattern) < 0)
+    return fail(HFX_ERR_INVALID_ARG, "inconsistent shells or pattern");
+  std::vector<long long> nf, foff((size_t)pattern->n_atoms + 1, 0);
+  atom_function_counts(shells, n_shells, pattern->n_atoms, nf);
+  for (int X = 0; X < pattern->n_atoms; ++X) foff[X + 1] = foff[X] + nf[(size_t)X];
+  const long long nbf = foff[pattern->n_atoms];
+  long long v = 0;
+  for (int X = 0; X < pattern->n_atoms; ++X)
+    for (int k = pattern->row_ptr[X]; k < pattern->row_ptr[X + 1]; ++k) {
+      const int Y = pattern->col[k];
+      for (long long i = 0; i < nf[(size_t)X]; ++i)
+        for (long long j = 0; j < nf[(size_t)Y]; ++j) val[v++] = dense[(foff[X] + i) * nbf + foff[Y] + j];
+    }
+  return HFX_OK;
+}
+
+long long hfx_setup_bytes_estimate(const hfx_shell_desc* shells, int n_shells, const hfx_pattern* pattern) {
+  if (!shells || n_shells <= 0 || !pattern || !pattern->row_ptr || !pattern->col || pattern->n_atoms <= 0) return -1;
+  std::vector<long long> nf;
+  if (!atom_function_counts(shells, n_shells, pattern->n_atoms, nf)) return -1;
+  long long nv = 0, nblk = 0;
+  for (int X = 0; X < pattern->n_atoms; ++X)
+    for (int k = pattern->row_ptr[X]; k < pattern->row_ptr[X + 1]; ++k) {
+      const int Y = pattern->col[k];
+      if (Y < 0 || Y >= pattern->n_atoms) return -1;
+      nv += nf[(size_t)X] * nf[(size_t)Y];
+      ++nblk;
+    }
+  int max_nprim = 1;
+  for (int i = 0; i < n_shells; ++i) max_nprim = std::max(max_nprim, shells[i].nprim);
+  const long long ns = n_shells, na = pattern->n_atoms, npair = ns * (ns + 1) / 2;
+  const long long stride = (long long)max_nprim * max_nprim;
+  const long long pair_bytes = (long long)sizeof(PairRec) + stride * (long long)sizeof(PrimPair);
+  // basis: shells, primitives, the two Boys tables
+  const long long basis = ns * 64 + (long long)n_shells * max_nprim * 16 +
+                          (long long)kBoysNL * kBoysNT * kBoysCols * (8 + 8);
+  // setup peak: every shell pair with its primitive pairs, sort keys and
+  // indexes (about 64 B per pair) and the class-sorted copy of the pairs (at
+  // most as large); persistent: pattern tables, Pmax, work-queue batches (a
+  // generous cap of two 16 B descriptors per shell pair)
+  const long long pairs_all = npair * (pair_bytes + 64);
+  const long long persistent = na * na * 8 + nblk * 16 + ns * ns * 8 + npair * pair_bytes +
+                               npair * 2 * (long long)sizeof(Desc);
+  (void)nv;
+  return basis + pairs_all + persistent;
+}
 
 hfx_status hfx_build_K(hfx_quartets* q, const double* P, double* K, void* stream) {
   if (!q || !P || !K) return fail(HFX_ERR_INVALID_ARG, "NULL argument");

@@ -1,0 +1,363 @@
+// hfx_server.cu -- continuous-batching exchange server.
+//
+// Requests are independent systems, each asking for a short sequence of
+// exchange builds (an SCF-like run: one build per density matrix it supplies,
+// with the pair lists and work queues of the system set up once and kept
+// resident on the device between its builds; Sec. 2 sets the screening lists
+// up before the SCF loop for the same reason).
+//
+// Each hfx_server_step():
+//   1. admits queued requests in arrival order while the device memory they
+//      are estimated to need fits under the server's budget (a request that
+//      could never fit fails with HFX_ERR_OOM; the head of the queue waits
+//      otherwise), and runs their setup;
+//   2. runs one build of every active request: requests with the same kernel,
+//      precision and screening options share one batched build (one launch
+//      per quartet class over all of their work queues, hfx_batch_*), whose
+//      plan is rebuilt only when the active set changes;
+//   3. retires the requests whose last build is done: copies their last K to
+//      the caller's host array, frees their device memory.
+//
+// One host thread drives a server; its calls are not thread-safe.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <deque>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "hfx.h"
+
+void hfx_set_last_error(const std::string& m);
+
+namespace {
+
+hfx_status srv_fail(hfx_status s, const std::string& m) {
+  hfx_set_last_error(m);
+  return s;
+}
+
+bool same_options(const hfx_opts& a, const hfx_opts& b) {
+  return a.kernel == b.kernel && a.omega == b.omega && a.precision == b.precision && a.screen == b.screen &&
+         a.tau == b.tau && a.density_screen == b.density_screen && a.eps == b.eps && a.prim_cutoff == b.prim_cutoff &&
+         (a.fp64_promote_bound == b.fp64_promote_bound ||
+          (a.fp64_promote_bound != a.fp64_promote_bound && b.fp64_promote_bound != b.fp64_promote_bound));
+}
+
+struct Request {
+  long long ticket = 0;
+  hfx_request_info info{};
+  // inputs (host copies; P and the K destination stay owned by the caller)
+  std::vector<hfx_shell_desc> shells;
+  std::vector<double> prim;  // alpha then coef of every shell, back to back
+  std::vector<double> xyz;
+  int n_atoms = 0;
+  std::vector<int> row_ptr, col;
+  hfx_opts opts{};
+  const double* P_host = nullptr;  // n_builds x n_values
+  double* K_out = nullptr;         // n_values, written when the last build is done
+  long long n_values = 0;
+  long long estimate = 0;
+  std::vector<double> E;
+  // device state while active
+  hfx_basis* basis = nullptr;
+  hfx_quartets* q = nullptr;
+  double* P = nullptr;
+  double* K = nullptr;
+
+  hfx_pattern pattern() const {
+    hfx_pattern p;
+    p.n_atoms = n_atoms;
+    p.row_ptr = row_ptr.data();
+    p.col = col.data();
+    return p;
+  }
+  void release_device() {
+    if (q) hfx_destroy_quartets(q);
+    if (basis) hfx_destroy_basis(basis);
+    if (P) cudaFree(P);
+    if (K) cudaFree(K);
+    q = nullptr;
+    basis = nullptr;
+    P = K = nullptr;
+  }
+  ~Request() { release_device(); }
+};
+
+struct Group {
+  hfx_opts opts{};
+  std::vector<Request*> members;
+  hfx_batch* batch = nullptr;
+};
+
+}  // namespace
+
+struct hfx_server_s {
+  hfx_server_opts o{};
+  cudaStream_t stream = nullptr;
+  std::chrono::steady_clock::time_point t0;
+  long long next_ticket = 1;
+  std::deque<Request*> queue;
+  std::vector<Request*> active;
+  std::map<long long, std::unique_ptr<Request>> all;
+  std::vector<Group> groups;
+  bool dirty = true;
+  hfx_server_info stats{};
+
+  double now() const {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  void drop_groups() {
+    for (auto& g : groups)
+      if (g.batch) hfx_batch_destroy(g.batch);
+    groups.clear();
+    dirty = true;
+  }
+  ~hfx_server_s() { drop_groups(); }
+};
+
+namespace {
+
+void finish(hfx_server_s* s, Request* r, int state, hfx_status st) {
+  r->info.state = state;
+  r->info.status = st;
+  r->info.t_done = s->now();
+  if (r->info.device_bytes > 0) s->stats.used_bytes -= r->info.device_bytes;
+  r->release_device();
+}
+
+// Setup of an admitted request: basis, quartet lists, P and K buffers.
+hfx_status setup_request(hfx_server_s* s, Request* r) {
+  hfx_status st = hfx_create_basis(r->shells.data(), (int)r->shells.size(), r->xyz.data(), r->n_atoms, s->stream,
+                                   &r->basis);
+  if (st != HFX_OK) return st;
+  const hfx_pattern pat = r->pattern();
+  st = hfx_build_quartets(r->basis, &r->opts, &pat, s->stream, &r->q);
+  if (st != HFX_OK) return st;
+  const size_t bytes = (size_t)std::max<long long>(r->n_values, 1) * sizeof(double);
+  cudaError_t e = cudaMalloc(&r->P, bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&r->K, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return srv_fail(e == cudaErrorMemoryAllocation ? HFX_ERR_OOM : HFX_ERR_CUDA,
+                    std::string("request buffers: ") + cudaGetErrorString(e));
+  }
+  r->info.device_bytes = hfx_basis_device_bytes(r->basis) + hfx_quartets_device_bytes(r->q) + 2 * (long long)bytes;
+  return HFX_OK;
+}
+
+hfx_status admit(hfx_server_s* s) {
+  while (!s->queue.empty() && (int)s->active.size() < s->o.max_active) {
+    Request* r = s->queue.front();
+    if (r->estimate > s->o.mem_budget) {
+      s->queue.pop_front();
+      finish(s, r, HFX_REQ_FAILED, HFX_ERR_OOM);
+      continue;
+    }
+    if (s->stats.used_bytes + r->estimate > s->o.mem_budget && !s->active.empty()) break;  // wait for retirements
+    s->queue.pop_front();
+    r->info.t_admit = s->now();
+    const hfx_status st = setup_request(s, r);
+    if (st != HFX_OK) {
+      r->info.device_bytes = 0;
+      finish(s, r, HFX_REQ_FAILED, st);
+      continue;
+    }
+    r->info.state = HFX_REQ_ACTIVE;
+    s->stats.used_bytes += r->info.device_bytes;
+    s->stats.peak_used_bytes = std::max(s->stats.peak_used_bytes, s->stats.used_bytes);
+    s->active.push_back(r);
+    s->dirty = true;
+  }
+  s->stats.max_active_seen = std::max(s->stats.max_active_seen, (int)s->active.size());
+  return HFX_OK;
+}
+
+hfx_status regroup(hfx_server_s* s) {
+  s->drop_groups();
+  for (Request* r : s->active) {
+    Group* g = nullptr;
+    for (auto& x : s->groups)
+      if (same_options(x.opts, r->opts)) g = &x;
+    if (!g) {
+      s->groups.emplace_back();
+      g = &s->groups.back();
+      g->opts = r->opts;
+    }
+    g->members.push_back(r);
+  }
+  for (auto& g : s->groups) {
+    std::vector<hfx_quartets*> m;
+    for (Request* r : g.members) m.push_back(r->q);
+    const hfx_status st = hfx_batch_create(m.data(), (int)m.size(), s->stream, &g.batch);
+    if (st != HFX_OK) return st;
+  }
+  s->dirty = false;
+  return HFX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+hfx_status hfx_server_create(const hfx_server_opts* opts, void* stream, hfx_server** out) {
+  if (!out) return srv_fail(HFX_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  std::unique_ptr<hfx_server_s> s(new hfx_server_s());
+  if (opts) s->o = *opts;
+  if (s->o.max_active <= 0) s->o.max_active = 64;
+  if (s->o.mem_budget <= 0) {
+    size_t fr = 0, tot = 0;
+    const cudaError_t e = cudaMemGetInfo(&fr, &tot);
+    if (e != cudaSuccess) return srv_fail(HFX_ERR_CUDA, std::string("cudaMemGetInfo: ") + cudaGetErrorString(e));
+    s->o.mem_budget = (long long)(0.8 * (double)fr);
+  }
+  s->stream = (cudaStream_t)stream;
+  s->t0 = std::chrono::steady_clock::now();
+  s->stats.mem_budget = s->o.mem_budget;
+  *out = s.release();
+  return HFX_OK;
+}
+
+hfx_status hfx_server_submit(hfx_server* s, const hfx_shell_desc* shells, int n_shells, const double* atom_xyz,
+                             int n_atoms, const hfx_pattern* pattern, const hfx_opts* opts, int n_builds,
+                             const double* P_host, double* K_out, long long* ticket) {
+  if (!s || !shells || n_shells <= 0 || !atom_xyz || n_atoms <= 0 || !pattern || !opts || !P_host || !ticket)
+    return srv_fail(HFX_ERR_INVALID_ARG, "NULL or empty argument");
+  if (n_builds < 1) return srv_fail(HFX_ERR_INVALID_ARG, "n_builds must be >= 1");
+  if (pattern->n_atoms != n_atoms) return srv_fail(HFX_ERR_INVALID_ARG, "pattern must cover the atoms");
+  const long long nv = hfx_pattern_value_count(shells, n_shells, pattern);
+  if (nv < 0) return srv_fail(HFX_ERR_INVALID_ARG, "inconsistent shells or pattern");
+  std::unique_ptr<Request> r(new Request());
+  r->ticket = s->next_ticket++;
+  r->n_atoms = n_atoms;
+  r->xyz.assign(atom_xyz, atom_xyz + 3 * (size_t)n_atoms);
+  r->row_ptr.assign(pattern->row_ptr, pattern->row_ptr + n_atoms + 1);
+  r->col.assign(pattern->col, pattern->col + r->row_ptr[n_atoms]);
+  size_t np = 0;
+  for (int i = 0; i < n_shells; ++i) {
+    if (shells[i].nprim < 1 || !shells[i].alpha || !shells[i].coef)
+      return srv_fail(HFX_ERR_INVALID_ARG, "shell without primitives");
+    np += (size_t)shells[i].nprim;
+  }
+  r->prim.resize(2 * np);
+  r->shells.assign(shells, shells + n_shells);
+  size_t k = 0;
+  for (auto& d : r->shells) {  // point the copies at the server's own primitive arrays
+    std::copy(d.alpha, d.alpha + d.nprim, r->prim.begin() + k);
+    std::copy(d.coef, d.coef + d.nprim, r->prim.begin() + np + k);
+    d.alpha = r->prim.data() + k;
+    d.coef = r->prim.data() + np + k;
+    k += (size_t)d.nprim;
+  }
+  r->opts = *opts;
+  r->P_host = P_host;
+  r->K_out = K_out;
+  r->n_values = nv;
+  r->estimate = hfx_setup_bytes_estimate(shells, n_shells, pattern) + 2 * std::max<long long>(nv, 1) * 8;
+  r->E.assign((size_t)n_builds, 0.0);
+  r->info.state = HFX_REQ_QUEUED;
+  r->info.n_builds = n_builds;
+  r->info.t_submit = s->now();
+  r->info.t_admit = r->info.t_done = -1.0;
+  *ticket = r->ticket;
+  s->queue.push_back(r.get());
+  s->all[r->ticket] = std::move(r);
+  return HFX_OK;
+}
+
+hfx_status hfx_server_step(hfx_server* s, int* n_active) {
+  if (!s) return srv_fail(HFX_ERR_INVALID_ARG, "NULL server");
+  hfx_status st = admit(s);
+  if (st != HFX_OK) return st;
+  if (n_active) *n_active = (int)s->active.size();
+  if (s->active.empty()) return HFX_OK;
+  if (s->dirty) {
+    st = regroup(s);
+    if (st != HFX_OK) return st;
+  }
+  // this build's density of every active request
+  for (Request* r : s->active) {
+    const double* src = r->P_host + (size_t)r->info.builds_done * (size_t)r->n_values;
+    const cudaError_t e =
+        cudaMemcpyAsync(r->P, src, (size_t)r->n_values * sizeof(double), cudaMemcpyHostToDevice, s->stream);
+    if (e != cudaSuccess) return srv_fail(HFX_ERR_CUDA, std::string("P upload: ") + cudaGetErrorString(e));
+  }
+  std::vector<double> E;
+  for (auto& g : s->groups) {
+    std::vector<const double*> Ps;
+    std::vector<double*> Ks;
+    for (Request* r : g.members) {
+      Ps.push_back(r->P);
+      Ks.push_back(r->K);
+    }
+    st = hfx_batch_build_K(g.batch, Ps.data(), Ks.data(), s->o.use_graph, s->stream);
+    if (st != HFX_OK) return st;
+    E.assign(g.members.size(), 0.0);
+    st = hfx_batch_energies(g.batch, E.data(), s->stream);
+    if (st != HFX_OK) return st;
+    for (size_t i = 0; i < g.members.size(); ++i) {
+      Request* r = g.members[i];
+      r->E[(size_t)r->info.builds_done] = E[i];
+      r->info.builds_done += 1;
+      s->stats.builds_done += 1;
+    }
+  }
+  s->stats.steps += 1;
+  // retire finished requests
+  std::vector<Request*> still;
+  for (Request* r : s->active) {
+    if (r->info.builds_done < r->info.n_builds) {
+      still.push_back(r);
+      continue;
+    }
+    if (r->K_out) {
+      const cudaError_t e =
+          cudaMemcpyAsync(r->K_out, r->K, (size_t)r->n_values * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+      if (e == cudaSuccess) cudaStreamSynchronize(s->stream);
+      if (e != cudaSuccess) return srv_fail(HFX_ERR_CUDA, std::string("K download: ") + cudaGetErrorString(e));
+    }
+    finish(s, r, HFX_REQ_DONE, HFX_OK);
+    s->dirty = true;
+  }
+  if (s->dirty) s->drop_groups();
+  s->active.swap(still);
+  if (n_active) *n_active = (int)s->active.size();
+  return HFX_OK;
+}
+
+hfx_status hfx_server_poll(hfx_server* s, long long ticket, hfx_request_info* info, double* E_x) {
+  if (!s || !info) return srv_fail(HFX_ERR_INVALID_ARG, "NULL argument");
+  auto it = s->all.find(ticket);
+  if (it == s->all.end()) return srv_fail(HFX_ERR_INVALID_ARG, "unknown ticket");
+  const Request* r = it->second.get();
+  *info = r->info;
+  if (E_x)
+    for (int i = 0; i < r->info.builds_done; ++i) E_x[i] = r->E[(size_t)i];
+  return HFX_OK;
+}
+
+hfx_status hfx_server_release(hfx_server* s, long long ticket) {
+  if (!s) return srv_fail(HFX_ERR_INVALID_ARG, "NULL server");
+  auto it = s->all.find(ticket);
+  if (it == s->all.end()) return srv_fail(HFX_ERR_INVALID_ARG, "unknown ticket");
+  const int st = it->second->info.state;
+  if (st != HFX_REQ_DONE && st != HFX_REQ_FAILED) return srv_fail(HFX_ERR_BUSY, "request not finished");
+  s->all.erase(it);
+  return HFX_OK;
+}
+
+hfx_status hfx_server_get_info(hfx_server* s, hfx_server_info* out) {
+  if (!s || !out) return srv_fail(HFX_ERR_INVALID_ARG, "NULL argument");
+  *out = s->stats;
+  out->n_queued = (int)s->queue.size();
+  out->n_active = (int)s->active.size();
+  return HFX_OK;
+}
+
+void hfx_server_destroy(hfx_server* s) { delete s; }
+
+}  // extern "C"

@@ -67,17 +67,43 @@ class Stats(ctypes.Structure):
 class ClassInfo(ctypes.Structure):
     _fields_ = [("bra_class", ctypes.c_int), ("ket_class", ctypes.c_int), ("la", ctypes.c_int),
                 ("lb", ctypes.c_int), ("lc", ctypes.c_int), ("ld", ctypes.c_int), ("n_out", ctypes.c_int),
-                ("vrr_flops", ctypes.c_int), ("hrr_flops", ctypes.c_int)]
+                ("vrr_flops", ctypes.c_int), ("hrr_flops", ctypes.c_int), ("n_acc", ctypes.c_int),
+                ("kernel_kind", ctypes.c_int)]
+
+KERNEL_KIND_NAMES = ("k_build_K", "k_build_K_split", "k_build_K_coop")
 
 
 EXPORTED = ["hfx_create_basis", "hfx_build_quartets", "hfx_value_count", "hfx_build_K", "hfx_exchange_energy",
             "hfx_pack_dense", "hfx_unpack_dense", "hfx_eval_quartets", "hfx_boys_eval", "hfx_get_stats",
             "hfx_get_class_info", "hfx_exchange_energy_noalloc", "hfx_batch_create", "hfx_batch_build_K",
             "hfx_batch_energies", "hfx_batch_autotune", "hfx_batch_get_tuning", "hfx_batch_get_stats",
-            "hfx_batch_destroy",
+            "hfx_batch_destroy", "hfx_quartets_device_bytes", "hfx_basis_device_bytes", "hfx_pattern_value_count",
+            "hfx_pack_dense_host", "hfx_setup_bytes_estimate", "hfx_server_create", "hfx_server_submit",
+            "hfx_server_step", "hfx_server_poll", "hfx_server_release", "hfx_server_get_info", "hfx_server_destroy",
             "hfx_destroy_basis", "hfx_destroy_quartets", "hfx_last_error"]
 
 _lib = None
+
+
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("mem_budget", ctypes.c_longlong), ("max_active", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("reserved", ctypes.c_int * 4)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int), ("status", ctypes.c_int), ("builds_done", ctypes.c_int),
+                ("n_builds", ctypes.c_int), ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_done", ctypes.c_double), ("device_bytes", ctypes.c_longlong)]
+
+
+class ServerInfo(ctypes.Structure):
+    _fields_ = [("mem_budget", ctypes.c_longlong), ("used_bytes", ctypes.c_longlong),
+                ("peak_used_bytes", ctypes.c_longlong), ("builds_done", ctypes.c_longlong),
+                ("steps", ctypes.c_longlong), ("n_queued", ctypes.c_int), ("n_active", ctypes.c_int),
+                ("max_active_seen", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+
+HFX_REQ_QUEUED, HFX_REQ_ACTIVE, HFX_REQ_DONE, HFX_REQ_FAILED = 0, 1, 2, 3
 
 
 def load(path: str = LIB_PATH):
@@ -116,9 +142,26 @@ def load(path: str = LIB_PATH):
     lib.hfx_destroy_quartets.argtypes = [V]
     lib.hfx_destroy_quartets.restype = None
     lib.hfx_last_error.restype = ctypes.c_char_p
+    lib.hfx_quartets_device_bytes.argtypes = [V]
+    lib.hfx_basis_device_bytes.argtypes = [V]
+    lib.hfx_pattern_value_count.argtypes = [ctypes.POINTER(ShellDesc), I, ctypes.POINTER(Pattern)]
+    lib.hfx_pack_dense_host.argtypes = [ctypes.POINTER(ShellDesc), I, ctypes.POINTER(Pattern), V, V]
+    lib.hfx_setup_bytes_estimate.argtypes = [ctypes.POINTER(ShellDesc), I, ctypes.POINTER(Pattern)]
+    lib.hfx_server_create.argtypes = [ctypes.POINTER(ServerOpts), V, PV]
+    lib.hfx_server_submit.argtypes = [V, ctypes.POINTER(ShellDesc), I, V, I, ctypes.POINTER(Pattern),
+                                      ctypes.POINTER(Opts), I, V, V, ctypes.POINTER(LL)]
+    lib.hfx_server_step.argtypes = [V, ctypes.POINTER(I)]
+    lib.hfx_server_poll.argtypes = [V, LL, ctypes.POINTER(RequestInfo), V]
+    lib.hfx_server_release.argtypes = [V, LL]
+    lib.hfx_server_get_info.argtypes = [V, ctypes.POINTER(ServerInfo)]
+    lib.hfx_server_destroy.argtypes = [V]
+    lib.hfx_server_destroy.restype = None
     for name in EXPORTED:
-        if name not in ("hfx_value_count", "hfx_destroy_basis", "hfx_destroy_quartets", "hfx_last_error",
-                        "hfx_batch_destroy"):
+        if name in ("hfx_quartets_device_bytes", "hfx_basis_device_bytes", "hfx_pattern_value_count",
+                    "hfx_setup_bytes_estimate"):
+            getattr(lib, name).restype = LL
+        elif name not in ("hfx_value_count", "hfx_destroy_basis", "hfx_destroy_quartets", "hfx_last_error",
+                          "hfx_batch_destroy", "hfx_server_destroy"):
             getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -153,13 +196,12 @@ def _stream(stream):
 
 
 # ----------------------------------------------------------------- C names
-def hfx_create_basis(shell_l, shell_atom, prim_off, alpha, coef, atom_xyz, stream=None):
-    """Shells from flat arrays (host numpy).  Returns the raw handle."""
-    lib = load()
+def shell_descs(shell_l, shell_atom, prim_off, alpha, coef):
+    """hfx_shell_desc array from flat shell arrays.  Returns (descs, keep):
+    ``keep`` holds the primitive arrays the descriptors point into."""
     n = len(shell_l)
     alpha = np.ascontiguousarray(alpha, dtype=np.float64)
     coef = np.ascontiguousarray(coef, dtype=np.float64)
-    xyz = np.ascontiguousarray(atom_xyz, dtype=np.float64)
     descs = (ShellDesc * n)()
     base_a, base_c = alpha.ctypes.data, coef.ctypes.data
     for i in range(n):
@@ -169,8 +211,17 @@ def hfx_create_basis(shell_l, shell_atom, prim_off, alpha, coef, atom_xyz, strea
         descs[i].atom = int(shell_atom[i])
         descs[i].alpha = base_a + 8 * p0
         descs[i].coef = base_c + 8 * p0
+    return descs, (alpha, coef)
+
+
+def hfx_create_basis(shell_l, shell_atom, prim_off, alpha, coef, atom_xyz, stream=None):
+    """Shells from flat arrays (host numpy).  Returns the raw handle."""
+    lib = load()
+    descs, _keep = shell_descs(shell_l, shell_atom, prim_off, alpha, coef)
+    xyz = np.ascontiguousarray(atom_xyz, dtype=np.float64)
     h = ctypes.c_void_p()
-    _check(lib.hfx_create_basis(descs, n, _ptr(xyz), int(xyz.shape[0]), _stream(stream), ctypes.byref(h)))
+    _check(lib.hfx_create_basis(descs, len(shell_l), _ptr(xyz), int(xyz.shape[0]), _stream(stream),
+                                ctypes.byref(h)))
     return h
 
 
@@ -378,4 +429,93 @@ class Batch:
         h = getattr(self, "handle", None)
         if h is not None and _lib is not None:
             _lib.hfx_batch_destroy(h)
+            self.handle = None
+
+
+class _SystemInput:
+    """Shell descriptors, coordinates and CSR pattern of one system (host)."""
+
+    def __init__(self, system, mask):
+        self.descs, self._keep = shell_descs(system.shell_l, system.shell_atom, system.prim_off, system.alpha,
+                                             system.coef)
+        self.n_shells = len(system.shell_l)
+        self.xyz = np.ascontiguousarray(system.atom_xyz, dtype=np.float64)
+        self.row_ptr, self.col = pattern_from_mask(mask)
+        self.pattern = Pattern()
+        self.pattern.n_atoms = int(self.xyz.shape[0])
+        self.pattern.row_ptr = self.row_ptr.ctypes.data
+        self.pattern.col = self.col.ctypes.data
+
+    def value_count(self) -> int:
+        n = load().hfx_pattern_value_count(self.descs, self.n_shells, ctypes.byref(self.pattern))
+        if n < 0:
+            raise HFXError(1, "inconsistent shells or pattern")
+        return int(n)
+
+    def pack(self, dense) -> np.ndarray:
+        dense = np.ascontiguousarray(dense, dtype=np.float64)
+        out = np.empty(self.value_count())
+        _check(load().hfx_pack_dense_host(self.descs, self.n_shells, ctypes.byref(self.pattern), _ptr(dense),
+                                          _ptr(out)))
+        return out
+
+    def setup_bytes_estimate(self) -> int:
+        return int(load().hfx_setup_bytes_estimate(self.descs, self.n_shells, ctypes.byref(self.pattern)))
+
+
+class Server:
+    """Owns an hfx_server (continuous batching of SCF-like requests)."""
+
+    def __init__(self, mem_budget=0, max_active=64, use_graph=False, stream=None):
+        o = ServerOpts()
+        o.mem_budget, o.max_active, o.use_graph = int(mem_budget), int(max_active), int(bool(use_graph))
+        h = ctypes.c_void_p()
+        _check(load().hfx_server_create(ctypes.byref(o), _stream(stream), ctypes.byref(h)))
+        self.handle = h
+        self._req = {}
+
+    def submit(self, system, mask, opts: Opts, P_list, want_K=True) -> int:
+        """Queue one system with one dense density matrix per build."""
+        inp = _SystemInput(system, mask)
+        nv = inp.value_count()
+        P = np.empty((len(P_list), nv))
+        for i, Pi in enumerate(P_list):
+            P[i] = inp.pack(Pi)
+        K = np.zeros(nv) if want_K else None
+        t = ctypes.c_longlong()
+        _check(load().hfx_server_submit(self.handle, inp.descs, inp.n_shells, _ptr(inp.xyz), int(inp.xyz.shape[0]),
+                                        ctypes.byref(inp.pattern), ctypes.byref(opts), len(P_list), _ptr(P),
+                                        _ptr(K), ctypes.byref(t)))
+        self._req[t.value] = (inp, P, K, len(P_list))
+        return t.value
+
+    def step(self) -> int:
+        n = ctypes.c_int()
+        _check(load().hfx_server_step(self.handle, ctypes.byref(n)))
+        return n.value
+
+    def poll(self, ticket):
+        """(RequestInfo, energies of the builds done so far)."""
+        info = RequestInfo()
+        E = np.zeros(self._req[ticket][3])
+        _check(load().hfx_server_poll(self.handle, int(ticket), ctypes.byref(info), _ptr(E)))
+        return info, E[:info.builds_done]
+
+    def K_values(self, ticket):
+        """K values (pattern layout) of the last build of a finished request."""
+        return self._req[ticket][2]
+
+    def release(self, ticket):
+        _check(load().hfx_server_release(self.handle, int(ticket)))
+        self._req.pop(ticket, None)
+
+    def info(self) -> ServerInfo:
+        i = ServerInfo()
+        _check(load().hfx_server_get_info(self.handle, ctypes.byref(i)))
+        return i
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and _lib is not None:
+            _lib.hfx_server_destroy(h)
             self.handle = None

@@ -50,6 +50,12 @@ def test_class_table(lib):
         assert ci.la >= ci.lb and ci.lc >= ci.ld and ci.bra_class >= ci.ket_class
         n = lambda l: (l + 1) * (l + 2) // 2
         assert ci.n_out == n(ci.la) * n(ci.lb) * n(ci.lc) * n(ci.ld)
+        # [e0|f0] accumulators: e over la..la+lb, f over lc..lc+ld
+        ne = sum(n(l) for l in range(ci.la, ci.la + ci.lb + 1))
+        nf = sum(n(l) for l in range(ci.lc, ci.lc + ci.ld + 1))
+        assert ci.n_acc == ne * nf
+        # kernel family by accumulator count: per-thread < 90 <= warp-split < 900 <= cooperative
+        assert ci.kernel_kind == (2 if ci.n_acc >= 900 else (1 if ci.n_acc >= 90 else 0))
         seen.add((ci.la, ci.lb, ci.lc, ci.ld))
     assert len(seen) == 21
     with pytest.raises(hfx.HFXError):
