@@ -125,6 +125,17 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(ms, world, device):
+    """The slowest rank's step time (every rank gets it); world 1: unchanged."""
+    if world <= 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    torch.distributed.barrier()
+    return float(t.item())
+
+
 def workload(atoms):
     s, P = synth.config2(atoms)
     mask = synth.atom_pair_mask(s, 14.0)
@@ -175,12 +186,7 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     clocks = clk.stop()
     st = q.stats()
-    ms = sum(times) / len(times)
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.barrier()
-        ms = float(t.item())
+    ms = max_over_ranks(sum(times) / len(times), world, dev)
 
     # end to end through the public API with host buffers: pinned P in, K and E_x out
     e2e = None
@@ -394,6 +400,75 @@ def run_serve(args):
             "peak_device_bytes": info.peak_used_bytes, "steps": info.steps, "clocks": clocks}
 
 
+def run_batch(args):
+    """--batch: many independent systems per build (C/H clusters of N ~ U{lo..hi}
+    atoms at the 400-atom cluster's density): one batched build (one launch per
+    quartet class over every member; CUDA graph), against the same systems
+    built one after another through hfx_build_K, and the autotuned batch."""
+    import torch
+    from paper_2009_03555_gb300 import hfx
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dev = torch.device("cuda")
+    rng = np.random.default_rng(2009_03555 + 3)
+    lo, hi = (int(x) for x in args.batch_atoms.split(","))
+    sizes = rng.integers(lo, hi + 1, size=args.batch_systems)
+    prec = hfx.HFX_PREC_MIXED if args.precision == "mixed" else hfx.HFX_PREC_FP64
+    opts = hfx.make_opts(kernel=hfx.HFX_KERNEL_ERFC, omega=0.11, screen=True, tau=1e-8, density_screen=True,
+                         eps=1e-8, prim_cutoff=args.prim_cutoff, precision=prec, n_block=args.n_block)
+    mem = []
+    for i, na in enumerate(sizes):
+        s = synth.ch_cluster(int(na), 3, sub=i)
+        mask = synth.atom_pair_mask(s, 14.0)
+        P = synth.density_matrix(s, 3, cutoff=14.0, sub=i)
+        b = hfx.Basis(s)
+        q = hfx.Quartets(b, opts, mask)
+        Pv = torch.empty(q.n_values, dtype=torch.float64, device=dev)
+        q.pack(torch.from_numpy(P).to(dev), Pv)
+        mem.append((b, q, Pv, torch.empty_like(Pv)))
+    Ps, Ks = [m[2] for m in mem], [m[3] for m in mem]
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    def sequential():
+        for b, q, Pv, Kv in mem:
+            q.build_K(Pv, Kv)
+
+    batch = hfx.Batch([m[1] for m in mem])
+    ms_seq = timed(sequential, args.steps)
+    ms_batch = timed(lambda: batch.build_K(Ps, Ks, use_graph=True), args.steps)
+    E_batch = batch.energies()
+    t0 = time.perf_counter()
+    batch.autotune(Ps, Ks)
+    tune_s = time.perf_counter() - t0
+    nb, grid = batch.tuning()  # autotune drops the old graph; the next build captures the tuned shapes
+    ms_tuned = timed(lambda: batch.build_K(Ps, Ks, use_graph=True), args.steps)
+    E_tuned = batch.energies()
+    n = len(mem)
+    return {"metric": "hfx_batched_builds_per_s", "value": n * 1000.0 / ms_batch, "unit": "system-builds/s",
+            "n_gpus": 1, "higher_is_better": True, "steps": args.steps, "warmup": args.warmup,
+            "dtype": "f32+f64" if prec == hfx.HFX_PREC_MIXED else "f64", "data": "synthetic",
+            "config": {"workload": f"{n} C/H clusters of {lo}-{hi} atoms (sum {int(sizes.sum())} atoms), HSE erfc "
+                                   f"w=0.11, Schwarz 1e-8 + density screening, P cut 14 bohr, {args.precision}",
+                       "systems": n, "atoms_total": int(sizes.sum()), "precision": args.precision},
+            "ms_batched_graph": ms_batch, "ms_sequential": ms_seq, "ms_autotuned_graph": ms_tuned,
+            "speedup_vs_sequential": ms_seq / ms_batch, "autotune_s": tune_s,
+            "autotuned_vs_default": ms_batch / ms_tuned,
+            "tuning": {"n_block": nb.tolist(), "grid": grid.tolist()},
+            "max_dE_tuned_vs_default": float(np.abs(E_tuned - E_batch).max())}
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -416,7 +491,13 @@ def main():
     ap.add_argument("--serve-chain", default="50,200", help="chain sizes (atoms), min,max")
     ap.add_argument("--serve-slab", default="36,100", help="slab sizes (atoms), min,max")
     ap.add_argument("--serve-graph", type=int, default=0)
+    ap.add_argument("--batch", action="store_true", help="many small systems per build (batched vs sequential)")
+    ap.add_argument("--batch-systems", type=int, default=64)
+    ap.add_argument("--batch-atoms", default="8,24", help="cluster sizes (atoms), min,max")
     args = ap.parse_args()
+    if args.batch:
+        print(json.dumps(run_batch(args)), flush=True)
+        return 0
     if args.serve:
         print(json.dumps(run_serve(args)), flush=True)
         return 0

@@ -688,160 +688,219 @@ __global__ void __launch_bounds__(kThreadsCoop) k_build_K_coop(const BuildArgs a
 // (reduce_scatter32), so lane j keeps only the accumulators 32k + j.
 // Primitive quartets that survive the bound test are compacted into a
 // per-warp queue first, so passes run with full lanes.
-constexpr int kThreadsSplit = 128;
+//
+// The recursion of these classes is thousands of straight-line instructions,
+// more than the SM's instruction cache holds, so warps that run it at
+// different places each stream their own instructions from L2 and stall on
+// instruction fetch.  The warps of a block therefore advance in rounds: in
+// each round every warp with work runs one pass (or the epilogue of a finished
+// quartet, or finds its next quartet), then the block meets at a barrier.  The
+// passes of one round start together and run the same code, so one
+// instruction stream serves the whole block.  One block of kSplitWarps warps
+// per SM.
+#ifndef HFX_SPLIT_WARPS
+#define HFX_SPLIT_WARPS 8
+#endif
+constexpr int kSplitWarps = HFX_SPLIT_WARPS;
+constexpr int kThreadsSplit = 32 * kSplitWarps;
 
 template <class C, typename R>
 struct SplitLayout {
   using T = typename C::Coop;
   static constexpr int PER_WARP = T::HRR_SLOTS + 160;  // HRR workspace + four P blocks
-  static constexpr size_t bytes() { return (size_t)(kThreadsSplit / 32) * PER_WARP * sizeof(R); }
+  static constexpr size_t bytes() { return (size_t)kSplitWarps * PER_WARP * sizeof(R); }
 };
 
+// One pass: prologue and vertical recursion of primitive quartet t of the
+// shell quartet (bra | ket) on every lane (t < 0: idle lane, zero inputs),
+// targets reduced over the warp into acc/comp.
 template <class C, typename R>
-__device__ __forceinline__ void split_quartet(const BuildArgs& a, const SysArgs& S, int bi, int ki, R* ws,
-                                              R* pbuf, int* pq, unsigned long long& pdone) {
+__device__ __forceinline__ void split_pass(const BuildArgs& a, const PrimPair* __restrict__ bprims,
+                                           const PrimPair* __restrict__ kprims, int bpoff, int kpoff, int nk, int t,
+                                           R* acc, R* comp) {
   constexpr bool kMixed = sizeof(R) == 4;
   constexpr int NR = kMixed ? 1 : 2;
   constexpr int NG = C::L + 1;
-  const int lane = threadIdx.x & 31;
-  const PairRec bra = S.pairs[a.bra_class][bi], ket = S.pairs[a.ket_class][ki];
-  const PrimPair* __restrict__ bprims = S.prims[a.bra_class];
-  const PrimPair* __restrict__ kprims = S.prims[a.ket_class];
-#ifdef HFX_CHECKED
-  {
-    const int cc = a.bra_class * 10 + a.ket_class;
-    if (bra.pcnt < 0 || ket.pcnt < 0 || bra.pcnt > 64 || ket.pcnt > 64) {
-      hfx_oob("pcnt", bra.pcnt * 1000LL + ket.pcnt, 64, cc);
-      return;
-    }
-    if ((bra.pcnt > 0 && (!HFX_IN(bra.poff, S.n_prims[a.bra_class], "bra.poff", cc) ||
-                          !HFX_IN(bra.poff + bra.pcnt - 1, S.n_prims[a.bra_class], "bra.poff+pcnt", cc))) ||
-        (ket.pcnt > 0 && (!HFX_IN(ket.poff, S.n_prims[a.ket_class], "ket.poff", cc) ||
-                          !HFX_IN(ket.poff + ket.pcnt - 1, S.n_prims[a.ket_class], "ket.poff+pcnt", cc))))
-      return;
-  }
-#endif
-  R acc[C::NCHUNK], comp[C::NCHUNK];
+  R G[NG], PQ[3] = {R(0), R(0), R(0)}, rinv = R(0);
 #pragma unroll
-  for (int k = 0; k < C::NCHUNK; ++k) {
-    acc[k] = R(0);
-    comp[k] = R(0);
-  }
-  const int nk = ket.pcnt, total = bra.pcnt * ket.pcnt;
-  int t0 = 0, qn = 0;
-  for (;;) {
-    while (qn < 32 && t0 < total) {
-      const int t = t0 + lane;
-      bool valid = false;
-      if (t < total) {
-        const int ib = t / nk, ik = t - ib * nk;
-        valid = bprims[bra.poff + ib].bound * kprims[ket.poff + ik].bound >= a.eps_prim;
-      }
-      const unsigned m = __ballot_sync(0xffffffffu, valid);
-      if (valid) pq[qn + __popc(m & ((1u << lane) - 1u))] = t;
-      qn += __popc(m);
-      t0 += 32;
-      __syncwarp();
-    }
-    if (qn == 0) break;
-    const int take = qn < 32 ? qn : 32;
-    const int t = lane < take ? pq[lane] : -1;
-    __syncwarp();
-    if (lane < qn - take) pq[lane] = pq[take + lane];
-    __syncwarp();
-    qn -= take;
-    pdone += take;
-    R G[NG], PQ[3] = {R(0), R(0), R(0)}, rinv = R(0);
+  for (int m = 0; m < NG; ++m) G[m] = R(0);
+  VrrGeo<R> g;
 #pragma unroll
-    for (int m = 0; m < NG; ++m) G[m] = R(0);
-    VrrGeo<R> g;
-#pragma unroll
-    for (int x = 0; x < 3; ++x) g.PA[x] = g.QC[x] = R(0);
-    g.oo2p = g.oo2q = R(0);
-    R rop = R(0), roq = R(0);
-    if (t >= 0) {
-      const int ib = t / nk, ik = t - ib * nk;
-      const PrimPair& pb = bprims[bra.poff + ib];
-      const PrimPair& pk = kprims[ket.poff + ik];
-      if constexpr (kMixed) {
-        prologue_ds<C::L>(a.boysf, a.kernel, ds{a.omega2_hi, a.omega2_lo}, pb, pk, G, rinv, PQ);
-      } else {
-        double inv_s;
-        prologue<C::L, NR>(a.boys, a.kernel, a.omega2, pb, pk, G, inv_s, PQ);
-        rinv = inv_s;
-      }
-#pragma unroll
-      for (int x = 0; x < 3; ++x) {
-        g.PA[x] = kMixed ? R(pb.PAf[x]) : R(pb.PA[x]);
-        g.QC[x] = kMixed ? R(pk.PAf[x]) : R(pk.PA[x]);
-      }
-      g.oo2p = kMixed ? R(pb.oo2pf) : R(pb.oo2p);
-      g.oo2q = kMixed ? R(pk.oo2pf) : R(pk.oo2p);
-      rop = (kMixed ? R(pk.pf) : R(pk.p)) * rinv;
-      roq = (kMixed ? R(pb.pf) : R(pb.p)) * rinv;
+  for (int x = 0; x < 3; ++x) g.PA[x] = g.QC[x] = R(0);
+  g.oo2p = g.oo2q = R(0);
+  R rop = R(0), roq = R(0);
+  if (t >= 0) {
+    const int ib = t / nk, ik = t - ib * nk;
+    const PrimPair& pb = bprims[bpoff + ib];
+    const PrimPair& pk = kprims[kpoff + ik];
+    if constexpr (kMixed) {
+      prologue_ds<C::L>(a.boysf, a.kernel, ds{a.omega2_hi, a.omega2_lo}, pb, pk, G, rinv, PQ);
+    } else {
+      double inv_s;
+      prologue<C::L, NR>(a.boys, a.kernel, a.omega2, pb, pk, G, inv_s, PQ);
+      rinv = inv_s;
     }
 #pragma unroll
     for (int x = 0; x < 3; ++x) {
-      g.WP[x] = -rop * PQ[x];
-      g.WQ[x] = roq * PQ[x];
+      g.PA[x] = kMixed ? R(pb.PAf[x]) : R(pb.PA[x]);
+      g.QC[x] = kMixed ? R(pk.PAf[x]) : R(pk.PA[x]);
     }
-    g.oo2pq = R(0.5) * rinv;
-    g.rop = rop;
-    g.roq = roq;
-    C::template vrr_split<R>(G, g, acc, comp);
+    g.oo2p = kMixed ? R(pb.oo2pf) : R(pb.oo2p);
+    g.oo2q = kMixed ? R(pk.oo2pf) : R(pk.oo2p);
+    rop = (kMixed ? R(pk.pf) : R(pk.p)) * rinv;
+    roq = (kMixed ? R(pb.pf) : R(pb.p)) * rinv;
   }
-  const unsigned short* __restrict__ perm = C::split_perm();
 #pragma unroll
-  for (int k = 0; k < C::NCHUNK; ++k) {
-    const int tt = lane + 32 * k;
-    if (tt < C::NACC) ws[perm[tt]] = kMixed ? acc[k] - comp[k] : acc[k];
+  for (int x = 0; x < 3; ++x) {
+    g.WP[x] = -rop * PQ[x];
+    g.WQ[x] = roq * PQ[x];
   }
-  __syncwarp();
-  quartet_epilogue<C, R>(a, S, bra, ket, bi, ki, ws, pbuf);
+  g.oo2pq = R(0.5) * rinv;
+  g.rop = rop;
+  g.roq = roq;
+  C::template vrr_split<R>(G, g, acc, comp);
 }
 
+#ifdef HFX_CHECKED
+// Checked builds: the work-queue batch and the primitive ranges it leads to.
+__device__ __forceinline__ bool split_desc_ok(const BuildArgs& a, const Desc& ds) {
+  const int cc = a.bra_class * 10 + a.ket_class;
+  if (!HFX_IN(ds.sys, a.n_sys, "desc.sys", cc)) return false;
+  const SysArgs& S0 = a.sys[ds.sys];
+  if (!HFX_IN(ds.bra, S0.n_pairs[a.bra_class], "desc.bra", cc)) return false;
+  if (ds.k1 > ds.k0 && (!HFX_IN(ds.k0, S0.n_pairs[a.ket_class], "desc.k0", cc) ||
+                        !HFX_IN(ds.k1 - 1, S0.n_pairs[a.ket_class], "desc.k1", cc)))
+    return false;
+  return true;
+}
+__device__ __forceinline__ bool split_prims_ok(const BuildArgs& a, const SysArgs& S, const PairRec& bra,
+                                               const PairRec& ket) {
+  const int cc = a.bra_class * 10 + a.ket_class;
+  if (bra.pcnt < 0 || ket.pcnt < 0 || bra.pcnt > 64 || ket.pcnt > 64) return hfx_oob("pcnt", bra.pcnt, 64, cc);
+  if (bra.pcnt > 0 && (!HFX_IN(bra.poff, S.n_prims[a.bra_class], "bra.poff", cc) ||
+                       !HFX_IN(bra.poff + bra.pcnt - 1, S.n_prims[a.bra_class], "bra.poff+pcnt", cc)))
+    return false;
+  if (ket.pcnt > 0 && (!HFX_IN(ket.poff, S.n_prims[a.ket_class], "ket.poff", cc) ||
+                       !HFX_IN(ket.poff + ket.pcnt - 1, S.n_prims[a.ket_class], "ket.poff+pcnt", cc)))
+    return false;
+  return true;
+}
+#endif
+
 template <class C, typename R>
-__global__ void __launch_bounds__(kThreadsSplit) k_build_K_split(const BuildArgs a) {
+__global__ void __launch_bounds__(kThreadsSplit, 1) k_build_K_split(const BuildArgs a) {
   using Lay = SplitLayout<C, R>;
+  constexpr bool kMixed = sizeof(R) == 4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int s_pq[kThreadsSplit / 32][64];
+  __shared__ int s_pq[kSplitWarps][64];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   R* ws = reinterpret_cast<R*>(smem_raw) + warp * Lay::PER_WARP;
   R* pbuf = ws + C::Coop::HRR_SLOTS;
   int* pq = s_pq[warp];
   unsigned long long done = 0, pdone = 0;
+  // work-queue position of this warp (uniform over its lanes)
+  bool exhausted = false, cur_ok = false;
+  Desc cur{0, 0, 0, 0};
+  int kb = 0;
+  unsigned pend = 0u;  // kept kets of the current 32-ket window, not yet started
+  // current shell quartet
+  bool have = false;
+  int bi = 0, ki = 0, bpoff = 0, kpoff = 0, nk = 1, total = 0, t0 = 0, qn = 0;
+  R acc[C::NCHUNK], comp[C::NCHUNK];
   for (;;) {
-    int d = 0;
-    if (lane == 0) d = atomicAdd(a.counter, 1);
-    d = __shfl_sync(0xffffffffu, d, 0);
-    if (d >= a.n_desc) break;
-    const Desc ds = a.desc[d];
+    // A. the next shell quartet: next kept ket of the window, next window of
+    //    the batch, or the next batch from the queue (Algorithms 1-3)
+    while (!have && !exhausted) {
+      if (pend) {
+        const int j = __ffs(pend) - 1;
+        pend &= pend - 1;
+        const SysArgs& S = a.sys[cur.sys];
+        bi = cur.bra;
+        ki = kb + j;
+        const PairRec bra = S.pairs[a.bra_class][bi], ket = S.pairs[a.ket_class][ki];
 #ifdef HFX_CHECKED
-    {
-      const int cc = a.bra_class * 10 + a.ket_class;
-      if (!HFX_IN(ds.sys, a.n_sys, "desc.sys", cc)) continue;
-      const SysArgs& S0 = a.sys[ds.sys];
-      if (!HFX_IN(ds.bra, S0.n_pairs[a.bra_class], "desc.bra", cc)) continue;
-      if (ds.k1 > ds.k0 && (!HFX_IN(ds.k0, S0.n_pairs[a.ket_class], "desc.k0", cc) ||
-                            !HFX_IN(ds.k1 - 1, S0.n_pairs[a.ket_class], "desc.k1", cc)))
-        continue;
-    }
+        if (!split_prims_ok(a, S, bra, ket)) continue;
 #endif
-    const SysArgs& S = a.sys[ds.sys];
-    const PairRec bra = S.pairs[a.bra_class][ds.bra];
-    const PairRec* __restrict__ kets = S.pairs[a.ket_class];
-    for (int kb = ds.k0; kb < ds.k1; kb += 32) {
-      const int k = kb + lane;
-      bool ok = false;
-      if (k < ds.k1) ok = keep_quartet(a, S, bra, kets[k]);
-      unsigned m = __ballot_sync(0xffffffffu, ok);
-      done += __popc(m);
-      while (m) {
-        const int j = __ffs(m) - 1;
-        m &= m - 1;
-        split_quartet<C, R>(a, S, ds.bra, kb + j, ws, pbuf, pq, pdone);
+        bpoff = bra.poff;
+        kpoff = ket.poff;
+        nk = ket.pcnt > 0 ? ket.pcnt : 1;
+        total = bra.pcnt * ket.pcnt;
+        t0 = 0;
+        qn = 0;
+#pragma unroll
+        for (int k = 0; k < C::NCHUNK; ++k) acc[k] = comp[k] = R(0);
+        have = true;
+      } else {
+        if (cur_ok && kb + 32 < cur.k1) {
+          kb += 32;
+        } else {
+          int d = 0;
+          if (lane == 0) d = atomicAdd(a.counter, 1);
+          d = __shfl_sync(0xffffffffu, d, 0);
+          if (d >= a.n_desc) {
+            exhausted = true;
+            break;
+          }
+          cur = a.desc[d];
+          cur_ok = true;
+#ifdef HFX_CHECKED
+          cur_ok = split_desc_ok(a, cur);
+          if (!cur_ok) continue;
+#endif
+          kb = cur.k0;
+        }
+        const SysArgs& S = a.sys[cur.sys];
+        const PairRec bra = S.pairs[a.bra_class][cur.bra];
+        const int k = kb + lane;
+        bool ok = false;
+        if (k < cur.k1) ok = keep_quartet(a, S, bra, S.pairs[a.ket_class][k]);
+        pend = __ballot_sync(0xffffffffu, ok);
+        done += __popc(pend);
       }
     }
+    // B. one pass of the current quartet, or its epilogue once every
+    //    surviving primitive quartet has been through a pass
+    if (have) {
+      const SysArgs& S = a.sys[cur.sys];
+      const PrimPair* __restrict__ bprims = S.prims[a.bra_class];
+      const PrimPair* __restrict__ kprims = S.prims[a.ket_class];
+      while (qn < 32 && t0 < total) {
+        const int t = t0 + lane;
+        bool valid = false;
+        if (t < total) {
+          const int ib = t / nk, ik = t - ib * nk;
+          valid = bprims[bpoff + ib].bound * kprims[kpoff + ik].bound >= a.eps_prim;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, valid);
+        if (valid) pq[qn + __popc(m & ((1u << lane) - 1u))] = t;
+        qn += __popc(m);
+        t0 += 32;
+        __syncwarp();
+      }
+      if (qn == 0) {
+        const unsigned short* __restrict__ perm = C::split_perm();
+#pragma unroll
+        for (int k = 0; k < C::NCHUNK; ++k) {
+          const int tt = lane + 32 * k;
+          if (tt < C::NACC) ws[perm[tt]] = kMixed ? acc[k] - comp[k] : acc[k];
+        }
+        __syncwarp();
+        const PairRec bra = S.pairs[a.bra_class][bi], ket = S.pairs[a.ket_class][ki];
+        quartet_epilogue<C, R>(a, S, bra, ket, bi, ki, ws, pbuf);
+        have = false;
+      } else {
+        const int take = qn < 32 ? qn : 32;
+        const int t = lane < take ? pq[lane] : -1;
+        __syncwarp();
+        if (lane < qn - take) pq[lane] = pq[take + lane];
+        __syncwarp();
+        qn -= take;
+        pdone += take;
+        split_pass<C, R>(a, bprims, kprims, bpoff, kpoff, nk, t, acc, comp);
+      }
+    }
+    // C. the round ends for the whole block; stop once no warp has work left
+    if (!__syncthreads_or(have || !exhausted)) break;
   }
   if (lane == 0 && done) {
     atomicAdd(a.n_done, done);

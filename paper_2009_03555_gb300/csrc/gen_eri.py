@@ -233,11 +233,10 @@ def gen_class(ib, ik, la, lb, lc, ld):
         src.append(f"  using Coop = {name}Coop;")
     if split:
         sl, nch, _, perm = gen_vrr_split(la, lb, lc, ld)
+        # a namespace-scope device table, like the other node tables
+        src.insert(0, f"__device__ const unsigned short k{name}_perm[] = {{" + ", ".join(str(x) for x in perm) + "};")
         src.append(f"  static constexpr int NCHUNK = {nch};")
-        src.append("  __device__ static const unsigned short* split_perm() {")
-        src.append("    static const unsigned short kPerm[] = {" + ", ".join(str(x) for x in perm) + "};")
-        src.append("    return kPerm;")
-        src.append("  }")
+        src.append(f"  __device__ static const unsigned short* split_perm() {{ return k{name}_perm; }}")
         src.append("  template <typename R>")
         src.append("  __device__ __forceinline__ static void vrr_split(const R* __restrict__ G, const VrrGeo<R>& g,")
         src.append("                                                 R* __restrict__ acc, R* __restrict__ comp) {")

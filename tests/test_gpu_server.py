@@ -120,21 +120,29 @@ def test_admission_by_memory():
     for s, mask, Ps in reqs:
         inp = hfx._SystemInput(s, mask)
         est.append(inp.setup_bytes_estimate() + 2 * 8 * inp.value_count())
-    srv = hfx.Server(mem_budget=max(est) + 1)
-    res = _run(srv, reqs, opts)
+    # three copies of one request under a budget of one estimate: once the
+    # first is admitted (holding its actual bytes) the next estimate no longer
+    # fits, so the copies run one after another, with equal results
+    same = [reqs[0]] * 3
+    srv = hfx.Server(mem_budget=est[0] + 1)
+    res = _run(srv, same, opts)
     info = srv.info()
-    assert info.max_active_seen == 1
-    assert all(r[0].state == hfx.HFX_REQ_DONE for r in res.values())
+    assert info.max_active_seen == 1 and info.steps == 3 * len(reqs[0][2])
     assert info.peak_used_bytes <= info.mem_budget
-    # one request larger than the whole budget fails, the others complete
+    for i in range(3):
+        assert res[i][0].state == hfx.HFX_REQ_DONE
+        np.testing.assert_allclose(res[i][1], res[0][1], rtol=1e-9, atol=0)
+    assert res[0][0].t_done <= res[1][0].t_admit and res[1][0].t_done <= res[2][0].t_admit
+    # a request larger than the whole budget fails, the others complete
+    big = int(np.argmax(est))
     srv2 = hfx.Server(mem_budget=sorted(est)[1] + 1)
     res2 = _run(srv2, reqs, opts)
-    big = int(np.argmax(est))
     assert res2[big][0].state == hfx.HFX_REQ_FAILED and res2[big][0].status == 2
+    ref = _run(hfx.Server(), reqs, opts)
     for i in range(len(reqs)):
         if i != big:
             assert res2[i][0].state == hfx.HFX_REQ_DONE
-            np.testing.assert_allclose(res2[i][1], res[i][1], rtol=1e-9, atol=0)
+            np.testing.assert_allclose(res2[i][1], ref[i][1], rtol=1e-9, atol=0)
 
 
 def test_graph_replay_equals_launches():
