@@ -239,9 +239,15 @@ def run_ours(args, rank, world):
         for c in range(hfx.N_CLASSES):
             if st.n_quartets_pass[p][c] > 0:
                 ci = hfx.hfx_get_class_info(c)
+                t = st.ms_class_pass[p][c]
+                fp32 = (prec == hfx.HFX_PREC_MIXED and p == 0)
+                f64, f32 = class_flops(ci, st.n_quartets_pass[p][c], st.n_prim_quartets_pass[p][c], 1, fp32)
+                frac = (f32 / FP32_PEAK_TFLOPS if fp32 else f64 / FP64_PEAK_TFLOPS) / (t * 1e-3) / 1e12 if t > 0 else 0
                 per_class.append({"class": f"({ci.la}{ci.lb}|{ci.lc}{ci.ld})", "pass": p,
-                                  "ms": round(st.ms_class_pass[p][c], 3), "quartets": int(st.n_quartets_pass[p][c]),
-                                  "prim_quartets": int(st.n_prim_quartets_pass[p][c])})
+                                  "kernel": hfx.KERNEL_KIND_NAMES[ci.kernel_kind],
+                                  "ms": round(t, 3), "quartets": int(st.n_quartets_pass[p][c]),
+                                  "prim_quartets": int(st.n_prim_quartets_pass[p][c]),
+                                  "alu_frac": round(frac, 4)})
     n_q = int(sum(st.n_quartets_computed))
     n_pq = int(sum(st.n_prim_quartets_pass[0]) + sum(st.n_prim_quartets_pass[1]))
     res = {
@@ -257,6 +263,8 @@ def run_ours(args, rank, world):
         "quartets_per_build": n_q, "prim_quartets_per_build": n_pq,
         "eri_quartets_per_s": world * n_q / (ms * 1e-3),
         "E_x": E, "setup_ms": st.ms_setup,
+        "setup_phase_ms": dict(zip(("pairs", "schwarz", "sorted_lists", "work_queues"),
+                                   (round(x, 3) for x in st.ms_setup_phase))),
         # per step: zero K, Pmax, the class kernels, symmetrise, E_x partials (build), E_x (energy call)
         "gpu_launches": args.steps * (5 + sum(1 for p in range(2) for c in range(hfx.N_CLASSES)
                                             if st.n_quartets_pass[p][c] > 0 or st.ms_class_pass[p][c] > 0)),
@@ -485,11 +493,11 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--ref-quartets-per-build", type=float, default=None)
     ap.add_argument("--serve", action="store_true", help="continuous-batching serving stream instead of one build")
-    ap.add_argument("--serve-requests", type=int, default=64)
-    ap.add_argument("--serve-rate", type=float, default=50.0)
+    ap.add_argument("--serve-requests", type=int, default=48)
+    ap.add_argument("--serve-rate", type=float, default=1.5)
     ap.add_argument("--serve-builds", type=int, default=5)
-    ap.add_argument("--serve-chain", default="50,200", help="chain sizes (atoms), min,max")
-    ap.add_argument("--serve-slab", default="36,100", help="slab sizes (atoms), min,max")
+    ap.add_argument("--serve-chain", default="20,60", help="chain sizes (atoms), min,max")
+    ap.add_argument("--serve-slab", default="16,36", help="slab sizes (atoms), min,max")
     ap.add_argument("--serve-graph", type=int, default=0)
     ap.add_argument("--batch", action="store_true", help="many small systems per build (batched vs sequential)")
     ap.add_argument("--batch-systems", type=int, default=64)

@@ -108,6 +108,7 @@ typedef struct {
   long long n_quartets_pass[2][21];
   long long n_prim_quartets_pass[2][21]; /* primitive quartets evaluated */
   float ms_class_pass[2][21];            /* device time of each class kernel (events) */
+  float ms_setup_phase[4];               /* setup: pairs, Schwarz bounds, sorted pair lists, work queues */
 } hfx_stats;
 
 /* Class table entry (for throughput and roofline accounting). */

@@ -39,6 +39,7 @@ def _sources():
 def _digest(src, extra):
     h = hashlib.sha256()
     h.update(" ".join(FLAGS + extra).encode())
+    h.update(os.environ.get("HFX_COOP_MIN_ACC", "").encode())  # generator switch
     own = [os.path.join(GEN, os.path.basename(src).replace("tu_", "cls_").replace(".cu", ".cuh"))]
     own = [p for p in own if os.path.exists(p)]
     if os.path.basename(src) == "hfx_core.cu":

@@ -10,6 +10,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "boys_ds.cuh"
 #include "eri_common.cuh"
 
@@ -66,6 +68,20 @@ struct BuildArgs {
   double promote;         // FP64 promotion bound on Q_AB Q_CD P_scr
   unsigned long long* n_done;  // [0] quartets computed, [1] primitive quartets computed
 };
+
+// What the primitive prologue and recursion read besides the pair data.
+struct EriParams {
+  const double* boys;
+  const float* boysf;
+  int kernel;
+  double omega2;
+  ds w2;           // omega^2 as a double-single pair (mixed path)
+  float eps_prim;  // primitive quartets with bound_ab bound_cd below this are skipped
+};
+
+__device__ __forceinline__ EriParams eri_params(const BuildArgs& a) {
+  return EriParams{a.boys, a.boysf, a.kernel, a.omega2, ds{a.omega2_hi, a.omega2_lo}, a.eps_prim};
+}
 
 struct SchwarzArgs {
   const PairRec* pairs;   // all shell pairs
@@ -384,11 +400,10 @@ __device__ __forceinline__ bool ep_blocks_ok(const SysArgs& S, const BuildArgs& 
 #endif
 
 // Horizontal recursion (node tables, shared memory) on the contracted
-// [e0|f0] held in ws[0..NACC-1], then the four exchange contributions
-// (see scatter_K) spread over the lanes.  Whole warp.
+// [e0|f0] held in ws[0..NACC-1]; the outputs land in the slots the class's
+// output table names.  Whole warp.
 template <class C, typename R>
-__device__ __forceinline__ void quartet_epilogue(const BuildArgs& a, const SysArgs& S, const PairRec& bra,
-                                                 const PairRec& ket, int bi, int ki, R* ws, R* pbuf) {
+__device__ __forceinline__ void quartet_hrr(const PairRec& bra, const PairRec& ket, R* ws) {
   using T = typename C::Coop;
   const int lane = threadIdx.x & 31;
   const uint4* __restrict__ hrr = T::hrr();
@@ -406,6 +421,16 @@ __device__ __forceinline__ void quartet_epilogue(const BuildArgs& a, const SysAr
     }
     __syncwarp();
   }
+}
+
+// Horizontal recursion, then the four exchange contributions (see
+// scatter_K) spread over the lanes.  Whole warp.
+template <class C, typename R>
+__device__ __forceinline__ void quartet_epilogue(const BuildArgs& a, const SysArgs& S, const PairRec& bra,
+                                                 const PairRec& ket, int bi, int ki, R* ws, R* pbuf) {
+  using T = typename C::Coop;
+  const int lane = threadIdx.x & 31;
+  quartet_hrr<C, R>(bra, ket, ws);
   // four exchange contributions (see scatter_K), outputs spread over lanes
   constexpr int NA = C::NA, NB = C::NB, NC = C::NC, ND = C::ND;
   const unsigned short* __restrict__ outs = T::out();
@@ -488,18 +513,16 @@ __device__ __forceinline__ void quartet_epilogue(const BuildArgs& a, const SysAr
 
 
 template <class C, typename R>
-__device__ __forceinline__ void coop_quartet(const BuildArgs& a, const SysArgs& S, int bi, int ki, R* ws, R* pbuf,
-                                             R* sg,
-                                             unsigned long long& pdone) {
+__device__ __forceinline__ void coop_accumulate(const EriParams& a, const PairRec& bra,
+                                                const PrimPair* __restrict__ bprims, const PairRec& ket,
+                                                const PrimPair* __restrict__ kprims, R* ws, R* pbuf, R* sg,
+                                                unsigned long long& pdone) {
   using T = typename C::Coop;
   using Lay = CoopLayout<C, R>;
   constexpr bool kMixed = sizeof(R) == 4;
   constexpr int NR = kMixed ? 1 : 2;
   constexpr int NG = C::L + 1;
   const int lane = threadIdx.x & 31;
-  const PairRec bra = S.pairs[a.bra_class][bi], ket = S.pairs[a.ket_class][ki];
-  const PrimPair* __restrict__ bprims = S.prims[a.bra_class];
-  const PrimPair* __restrict__ kprims = S.prims[a.ket_class];
   R acc[Lay::NPL], comp[Lay::NPL];
 #pragma unroll
   for (int k = 0; k < Lay::NPL; ++k) {
@@ -523,7 +546,7 @@ __device__ __forceinline__ void coop_quartet(const BuildArgs& a, const SysArgs& 
         R* rec = pbuf + lane * Lay::PB;
         R G[NG], PQ[3], rinv;
         if constexpr (kMixed) {
-          prologue_ds<C::L>(a.boysf, a.kernel, ds{a.omega2_hi, a.omega2_lo}, pb, pk, G, rinv, PQ);
+          prologue_ds<C::L>(a.boysf, a.kernel, a.w2, pb, pk, G, rinv, PQ);
         } else {
           double inv_s;
           prologue<C::L, NR>(a.boys, a.kernel, a.omega2, pb, pk, G, inv_s, PQ);
@@ -624,6 +647,13 @@ __device__ __forceinline__ void coop_quartet(const BuildArgs& a, const SysArgs& 
     if (tt < C::NACC) ws[tt] = kMixed ? acc[k] - comp[k] : acc[k];
   }
   __syncwarp();
+}
+
+template <class C, typename R>
+__device__ __forceinline__ void coop_quartet(const BuildArgs& a, const SysArgs& S, int bi, int ki, R* ws, R* pbuf,
+                                             R* sg, unsigned long long& pdone) {
+  const PairRec bra = S.pairs[a.bra_class][bi], ket = S.pairs[a.ket_class][ki];
+  coop_accumulate<C, R>(eri_params(a), bra, S.prims[a.bra_class], ket, S.prims[a.ket_class], ws, pbuf, sg, pdone);
   quartet_epilogue<C, R>(a, S, bra, ket, bi, ki, ws, pbuf);
 }
 
@@ -692,30 +722,44 @@ __global__ void __launch_bounds__(kThreadsCoop) k_build_K_coop(const BuildArgs a
 // The recursion of these classes is thousands of straight-line instructions,
 // more than the SM's instruction cache holds, so warps that run it at
 // different places each stream their own instructions from L2 and stall on
-// instruction fetch.  The warps of a block therefore advance in rounds: in
-// each round every warp with work runs one pass (or the epilogue of a finished
-// quartet, or finds its next quartet), then the block meets at a barrier.  The
-// passes of one round start together and run the same code, so one
-// instruction stream serves the whole block.  One block of kSplitWarps warps
-// per SM.
-#ifndef HFX_SPLIT_WARPS
-#define HFX_SPLIT_WARPS 8
+// instruction fetch.  For those classes (SplitShape::LOCKSTEP) the warps of a
+// block advance in rounds: in each round every warp with work runs one pass
+// (or the epilogue of a finished quartet, or finds its next quartet), then the
+// block meets at a barrier.  The passes of one round start together and run
+// the same code, so one instruction stream serves the whole block.  Shapes
+// (measured on GB300, 100-atom HSE build): the longest recursions run one
+// 8-warp block per SM (they need 255 registers anyway); shorter ones run
+// three 4-warp blocks per SM at <= 168 registers, in lockstep from
+// HFX_LOCKSTEP_MIN_FLOPS recursion flops up.
+#ifndef HFX_LOCKSTEP_MIN_FLOPS
+#define HFX_LOCKSTEP_MIN_FLOPS 1400
 #endif
-constexpr int kSplitWarps = HFX_SPLIT_WARPS;
-constexpr int kThreadsSplit = 32 * kSplitWarps;
+#ifndef HFX_WIDE_MIN_FLOPS
+#define HFX_WIDE_MIN_FLOPS 2000
+#endif
+template <class C>
+struct SplitShape {
+  static constexpr bool LOCKSTEP = C::VRR_FLOPS >= HFX_LOCKSTEP_MIN_FLOPS;
+  // a horizontal-recursion workspace this large (doubles or floats per warp)
+  // leaves room for 4-warp blocks only
+  static constexpr bool BIG_HRR = C::Coop::HRR_SLOTS > 4096;
+  static constexpr int WARPS = (C::VRR_FLOPS >= HFX_WIDE_MIN_FLOPS && !BIG_HRR) ? 8 : 4;
+  static constexpr int THREADS = 32 * WARPS;
+  static constexpr int MIN_BLOCKS = (WARPS == 8 || BIG_HRR) ? 1 : 3;
+};
 
 template <class C, typename R>
 struct SplitLayout {
   using T = typename C::Coop;
   static constexpr int PER_WARP = T::HRR_SLOTS + 160;  // HRR workspace + four P blocks
-  static constexpr size_t bytes() { return (size_t)kSplitWarps * PER_WARP * sizeof(R); }
+  static constexpr size_t bytes() { return (size_t)SplitShape<C>::WARPS * PER_WARP * sizeof(R); }
 };
 
 // One pass: prologue and vertical recursion of primitive quartet t of the
 // shell quartet (bra | ket) on every lane (t < 0: idle lane, zero inputs),
 // targets reduced over the warp into acc/comp.
 template <class C, typename R>
-__device__ __forceinline__ void split_pass(const BuildArgs& a, const PrimPair* __restrict__ bprims,
+__device__ __forceinline__ void split_pass(const EriParams& a, const PrimPair* __restrict__ bprims,
                                            const PrimPair* __restrict__ kprims, int bpoff, int kpoff, int nk, int t,
                                            R* acc, R* comp) {
   constexpr bool kMixed = sizeof(R) == 4;
@@ -734,7 +778,7 @@ __device__ __forceinline__ void split_pass(const BuildArgs& a, const PrimPair* _
     const PrimPair& pb = bprims[bpoff + ib];
     const PrimPair& pk = kprims[kpoff + ik];
     if constexpr (kMixed) {
-      prologue_ds<C::L>(a.boysf, a.kernel, ds{a.omega2_hi, a.omega2_lo}, pb, pk, G, rinv, PQ);
+      prologue_ds<C::L>(a.boysf, a.kernel, a.w2, pb, pk, G, rinv, PQ);
     } else {
       double inv_s;
       prologue<C::L, NR>(a.boys, a.kernel, a.omega2, pb, pk, G, inv_s, PQ);
@@ -788,11 +832,12 @@ __device__ __forceinline__ bool split_prims_ok(const BuildArgs& a, const SysArgs
 #endif
 
 template <class C, typename R>
-__global__ void __launch_bounds__(kThreadsSplit, 1) k_build_K_split(const BuildArgs a) {
+__global__ void __launch_bounds__(SplitShape<C>::THREADS, SplitShape<C>::MIN_BLOCKS)
+    k_build_K_split(const BuildArgs a) {
   using Lay = SplitLayout<C, R>;
   constexpr bool kMixed = sizeof(R) == 4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int s_pq[kSplitWarps][64];
+  __shared__ int s_pq[SplitShape<C>::WARPS][64];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   R* ws = reinterpret_cast<R*>(smem_raw) + warp * Lay::PER_WARP;
   R* pbuf = ws + C::Coop::HRR_SLOTS;
@@ -896,11 +941,16 @@ __global__ void __launch_bounds__(kThreadsSplit, 1) k_build_K_split(const BuildA
         __syncwarp();
         qn -= take;
         pdone += take;
-        split_pass<C, R>(a, bprims, kprims, bpoff, kpoff, nk, t, acc, comp);
+        split_pass<C, R>(eri_params(a), bprims, kprims, bpoff, kpoff, nk, t, acc, comp);
       }
     }
-    // C. the round ends for the whole block; stop once no warp has work left
-    if (!__syncthreads_or(have || !exhausted)) break;
+    // C. lockstep classes: the round ends for the whole block, which stops
+    //    once no warp has work left; otherwise each warp runs on by itself
+    if constexpr (SplitShape<C>::LOCKSTEP) {
+      if (!__syncthreads_or(have || !exhausted)) break;
+    } else {
+      if (!have && exhausted) break;
+    }
   }
   if (lane == 0 && done) {
     atomicAdd(a.n_done, done);
@@ -926,6 +976,66 @@ __global__ void __launch_bounds__(64) k_schwarz(const SchwarzArgs a) {
 #pragma unroll
       for (int b = 0; b < C::NB; ++b) mx = fmax(mx, fabs(out[((x * C::NB + b) * C::NA + x) * C::NB + b]));
     a.Q[i] = sqrt(mx);
+  }
+}
+
+// Schwarz bounds of the pairs of a pair class whose quartet class runs on the
+// warp-split or cooperative build kernels: one warp per pair, the same
+// accumulation as the build (FP64, every primitive quartet), the horizontal
+// recursion in shared memory, then the largest diagonal |(ab|ab)|.  A thread
+// per pair would hold hundreds of FP64 accumulators in local memory.
+constexpr int kSchwarzWarps = 4;
+
+template <class C>
+struct SchwarzWarpLayout {
+  static constexpr int PER_WARP = C::COOP ? CoopLayout<C, double>::PER_WARP : C::Coop::HRR_SLOTS;
+  static constexpr size_t bytes() { return (size_t)kSchwarzWarps * PER_WARP * sizeof(double); }
+};
+
+template <class C>
+__global__ void __launch_bounds__(32 * kSchwarzWarps) k_schwarz_warp(const SchwarzArgs a) {
+  if constexpr (C::bra_class == C::ket_class && (C::SPLIT || C::COOP)) {
+    using T = typename C::Coop;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double* ws = reinterpret_cast<double*>(smem_raw) + warp * SchwarzWarpLayout<C>::PER_WARP;
+    const EriParams p{a.boys, nullptr, a.kernel, a.omega2, ds{0.f, 0.f}, -1.f};  // every primitive quartet
+    const unsigned short* __restrict__ outs = T::out();
+    for (int i = blockIdx.x * kSchwarzWarps + warp; i < a.n_pairs; i += gridDim.x * kSchwarzWarps) {
+      if (a.pair_class[i] != a.cls) continue;
+      const PairRec pr = a.pairs[i];
+      if constexpr (C::COOP) {
+        using Lay = CoopLayout<C, double>;
+        unsigned long long pd = 0;
+        coop_accumulate<C, double>(p, pr, a.prims, pr, a.prims, ws, ws + Lay::WS, ws + Lay::WS + Lay::PBUF, pd);
+      } else {
+        double acc[C::NCHUNK], comp[C::NCHUNK];
+#pragma unroll
+        for (int k = 0; k < C::NCHUNK; ++k) acc[k] = comp[k] = 0.0;
+        const int nk = pr.pcnt > 0 ? pr.pcnt : 1, total = pr.pcnt * pr.pcnt;
+        for (int t0 = 0; t0 < total; t0 += 32) {
+          const int t = t0 + lane < total ? t0 + lane : -1;
+          split_pass<C, double>(p, a.prims, a.prims, pr.poff, pr.poff, nk, t, acc, comp);
+        }
+        const unsigned short* __restrict__ perm = C::split_perm();
+#pragma unroll
+        for (int k = 0; k < C::NCHUNK; ++k) {
+          const int tt = lane + 32 * k;
+          if (tt < C::NACC) ws[perm[tt]] = acc[k];
+        }
+        __syncwarp();
+      }
+      quartet_hrr<C, double>(pr, pr, ws);
+      double mx = 0.0;
+      for (int e = lane; e < C::NA * C::NB; e += 32) {
+        const int x = e / C::NB, b = e - x * C::NB;
+        mx = fmax(mx, fabs(ws[outs[((x * C::NB + b) * C::NA + x) * C::NB + b]]));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if (lane == 0) a.Q[i] = sqrt(mx);
+      __syncwarp();
+    }
   }
 }
 
@@ -973,7 +1083,7 @@ void launch_build_K_t(const BuildArgs& a, int grid, cudaStream_t s) {
       cudaFuncSetAttribute(k_build_K_split<C, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
       attr = true;
     }
-    k_build_K_split<C, R><<<grid, kThreadsSplit, sm, s>>>(a);
+    k_build_K_split<C, R><<<grid, SplitShape<C>::THREADS, sm, s>>>(a);
   } else {
     k_build_K<C, R><<<grid, kThreadsK, 0, s>>>(a);
   }
@@ -997,7 +1107,7 @@ int occupancy_build_K_t() {
   } else if constexpr (C::SPLIT) {
     const size_t sm = SplitLayout<C, R>::bytes();
     cudaFuncSetAttribute(k_build_K_split<C, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_build_K_split<C, R>, kThreadsSplit, sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_build_K_split<C, R>, SplitShape<C>::THREADS, sm);
   } else {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_build_K<C, R>, kThreadsK, 0);
   }
@@ -1011,7 +1121,23 @@ int occupancy_build_K(int fp32) {
 
 template <class C>
 void launch_schwarz(const SchwarzArgs& a, cudaStream_t s) {
-  if (a.n_pairs > 0) k_schwarz<C><<<(a.n_pairs + 63) / 64, 64, 0, s>>>(a);
+  if (a.n_pairs <= 0) return;
+  if constexpr (C::SPLIT || C::COOP) {
+    const size_t sm = SchwarzWarpLayout<C>::bytes();
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_schwarz_warp<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      attr = true;
+    }
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const long long need = (a.n_pairs + kSchwarzWarps - 1) / kSchwarzWarps;
+    const int grid = (int)std::min<long long>(need, 8LL * nsm);
+    k_schwarz_warp<C><<<grid, 32 * kSchwarzWarps, sm, s>>>(a);
+  } else {
+    k_schwarz<C><<<(a.n_pairs + 63) / 64, 64, 0, s>>>(a);
+  }
 }
 
 template <class C>

@@ -365,7 +365,7 @@ def _write_if_changed(path, text):
 # kind 2 (bra HRR):  v = s0 + AB_i s1;   kind 3 (ket HRR): v = s0 + CD_i s1
 # VRR slots: 0 = constant zero, 1..L+1 = G_0..G_L, then nodes by level
 # (level = |e| + |f|).  HRR slots: 0..NACC-1 = contracted [e0|f0], then nodes.
-COOP_MIN_ACC = 900
+COOP_MIN_ACC = int(os.environ.get("HFX_COOP_MIN_ACC", "900"))  # (dd|dd): 961 accumulators
 
 
 def coop_tables(la, lb, lc, ld):

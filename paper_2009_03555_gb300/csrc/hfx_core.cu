@@ -154,6 +154,7 @@ struct hfx_quartets_s {
   DBuf<double> pmax;                       // n_shells x n_shells
   DBuf<double> scratch;                    // energy accumulator
   float ms_setup = 0.f;
+  float ms_setup_phase[4] = {0.f, 0.f, 0.f, 0.f};
   SysArgs h_sys{};  // this system's entry of a build table (P, K unset)
   Plan plan;        // single-system build plan
 };
@@ -1014,6 +1015,14 @@ hfx_status hfx_build_quartets(hfx_basis* b, const hfx_opts* opts_in, const hfx_p
   HFX_CK(cudaEventCreate(&t0));
   HFX_CK(cudaEventCreate(&t1));
   HFX_CK(cudaEventRecord(t0, s));
+  struct PhaseEvents {  // ends of setup phases: pairs, Schwarz, sorted lists, work queues
+    cudaEvent_t e[4] = {};
+    ~PhaseEvents() {
+      for (auto x : e)
+        if (x) cudaEventDestroy(x);
+    }
+  } ph;
+  for (auto& x : ph.e) HFX_CK(cudaEventCreate(&x));
   hfx_status st = setup_pattern(q, pattern, s);
   if (st != HFX_OK) return st;
 
@@ -1049,6 +1058,8 @@ hfx_status hfx_build_quartets(hfx_basis* b, const hfx_opts* opts_in, const hfx_p
                                                        all_prims.p, pclass.p);
   HFX_CK(cudaGetLastError());
 
+  HFX_CK(cudaEventRecord(ph.e[0], s));
+
   // 2. Schwarz bounds with the run's kernel (Sec. 2, Eq. schwarz)
   for (int c = 0; c < 6; ++c) {
     SchwarzArgs a;
@@ -1064,6 +1075,7 @@ hfx_status hfx_build_quartets(hfx_basis* b, const hfx_opts* opts_in, const hfx_p
     kClassOps[quartet_class_of(c, c)].launch_schwarz(a, s);
   }
   HFX_CK(cudaGetLastError());
+  HFX_CK(cudaEventRecord(ph.e[1], s));
 
   // 3. sort pairs by (class, descending Q); significant pairs are a prefix of
   //    each class segment (Q_IJ Q_max > tau is lossless)
@@ -1112,6 +1124,8 @@ hfx_status hfx_build_quartets(hfx_basis* b, const hfx_opts* opts_in, const hfx_p
     seg += h_cnt[c];
   }
   HFX_CK(cudaGetLastError());
+
+  HFX_CK(cudaEventRecord(ph.e[2], s));
 
   // 5. work-queue batches per quartet class
   for (int cb = 0; cb < 6; ++cb)
@@ -1163,6 +1177,7 @@ hfx_status hfx_build_quartets(hfx_basis* b, const hfx_opts* opts_in, const hfx_p
     for (auto& r : h) npp += r.pcnt;
   }
   q->n_prim_pairs = npp;
+  HFX_CK(cudaEventRecord(ph.e[3], s));
 
   // 6. per-build buffers and the single-system build plan
   HFX_CK(q->pmax.alloc((size_t)ns * ns));
@@ -1181,6 +1196,8 @@ hfx_status hfx_build_quartets(hfx_basis* b, const hfx_opts* opts_in, const hfx_p
   HFX_CK(cudaEventRecord(t1, s));
   HFX_CK(cudaEventSynchronize(t1));
   cudaEventElapsedTime(&q->ms_setup, t0, t1);
+  cudaEventElapsedTime(&q->ms_setup_phase[0], t0, ph.e[0]);
+  for (int k = 1; k < 4; ++k) cudaEventElapsedTime(&q->ms_setup_phase[k], ph.e[k - 1], ph.e[k]);
   cudaEventDestroy(t0);
   cudaEventDestroy(t1);
   HFX_CK(cudaGetLastError());
@@ -1457,6 +1474,7 @@ hfx_status hfx_get_stats(const hfx_quartets* q, hfx_stats* out) {
   out->n_prim_pairs = q->n_prim_pairs;
   out->n_values = q->n_values;
   out->ms_setup = q->ms_setup;
+  for (int k = 0; k < 4; ++k) out->ms_setup_phase[k] = q->ms_setup_phase[k];
   plan_stats(const_cast<hfx_quartets_s*>(q)->plan, out);
   return HFX_OK;
 }
@@ -1567,6 +1585,7 @@ hfx_status hfx_batch_get_stats(hfx_batch* b, hfx_stats* out) {
     out->n_prim_pairs += q->n_prim_pairs;
     out->n_values += q->n_values;
     out->ms_setup += q->ms_setup;
+    for (int k = 0; k < 4; ++k) out->ms_setup_phase[k] += q->ms_setup_phase[k];
   }
   plan_stats(b->plan, out);
   return HFX_OK;

@@ -61,7 +61,8 @@ class Stats(ctypes.Structure):
                 ("ms_setup", ctypes.c_float), ("ms_last_build", ctypes.c_float),
                 ("n_quartets_pass", (ctypes.c_longlong * N_CLASSES) * 2),
                 ("n_prim_quartets_pass", (ctypes.c_longlong * N_CLASSES) * 2),
-                ("ms_class_pass", (ctypes.c_float * N_CLASSES) * 2)]
+                ("ms_class_pass", (ctypes.c_float * N_CLASSES) * 2),
+                ("ms_setup_phase", ctypes.c_float * 4)]
 
 
 class ClassInfo(ctypes.Structure):
