@@ -31,6 +31,13 @@ sys.path.insert(0, ROOT)
 
 import synth  # noqa: E402
 
+# DRAM bytes per primitive quartet of class kernels, each from one ncu capture
+# (profiles/) of the 50-atom cluster: dram__bytes_read.sum + dram__bytes_write.sum
+# of one launch divided by that launch's primitive quartets.  The roofline's
+# `traffic` scales it to the timed launch; a kernel changed since its capture
+# has no entry (traffic null).
+DRAM_BYTES_PER_PRIM_QUARTET = {}
+
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 80.5: 128 FP32 FMA/clk/SM at the 2070 MHz max clock
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12     # 1.26: 2 FP64 FMA/clk/SM (1/64 of FP32)
 
@@ -225,15 +232,18 @@ def run_ours(args, rank, world):
         a32 = f32 / (t * 1e-3) / 1e12
         u64, u32 = a64 / FP64_PEAK_TFLOPS, a32 / FP32_PEAK_TFLOPS
         pipe = "fp64" if u64 >= u32 else "fp32"
-        roof = {"bound": "alu", "pipe": pipe,
-                "kernel": f"{hfx.KERNEL_KIND_NAMES[ci.kernel_kind]}<Cls{ci.la}{ci.lb}{ci.lc}{ci.ld}, "
-                          f"{'float' if fp32 else 'double'}>",
+        kname = (f"{hfx.KERNEL_KIND_NAMES[ci.kernel_kind]}<Cls{ci.la}{ci.lb}{ci.lc}{ci.ld}, "
+                 f"{'float' if fp32 else 'double'}>")
+        bpq = DRAM_BYTES_PER_PRIM_QUARTET.get(kname)
+        roof = {"bound": "alu", "pipe": pipe, "kernel": kname,
                 "achieved": round(a64 if pipe == "fp64" else a32, 4),
                 "peak": round(FP64_PEAK_TFLOPS if pipe == "fp64" else FP32_PEAK_TFLOPS, 3),
                 "unit": "TFLOP/s", "frac": round(max(u64, u32), 4),
                 "other_pipe_frac": round(min(u64, u32), 4),
                 "peak_source": "derived: 152 SMs x (128 FP32 | 2 FP64) FMA/clk x 2070 MHz",
-                "traffic": None, "launch_ms": round(t, 3), "share_of_build": round(t / st.ms_last_build, 4)}
+                "traffic": (round(bpq * st.n_prim_quartets_pass[p][c]) if bpq is not None else None),
+                "traffic_unit": "bytes per launch",
+                "launch_ms": round(t, 3), "share_of_build": round(t / st.ms_last_build, 4)}
     per_class = []
     for p in range(2):
         for c in range(hfx.N_CLASSES):
@@ -477,6 +487,48 @@ def run_batch(args):
             "max_dE_tuned_vs_default": float(np.abs(E_tuned - E_batch).max())}
 
 
+def run_precision_check(args):
+    """--mixed-vs-fp64: the same build in FP64 and in mixed precision (same
+    screening and primitive cutoff), the mixed one for every FP64-promotion
+    bound of --promote-sweep; |dE_x|, the largest |dK| element, build time and
+    the share of quartets promoted to FP64."""
+    import torch
+    from paper_2009_03555_gb300 import hfx
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dev = torch.device("cuda")
+    s, P, mask = workload(args.atoms)
+
+    def one(prec, promote):
+        opts = hfx.make_opts(kernel=hfx.HFX_KERNEL_ERFC, omega=0.11, screen=True, tau=1e-8, density_screen=True,
+                             eps=1e-8, prim_cutoff=args.prim_cutoff, precision=prec,
+                             fp64_promote_bound=promote, n_block=args.n_block)
+        b = hfx.Basis(s)
+        q = hfx.Quartets(b, opts, mask)
+        Pv = torch.empty(q.n_values, dtype=torch.float64, device=dev)
+        Kv = torch.empty_like(Pv)
+        q.pack(torch.from_numpy(P).to(dev), Pv)
+        q.build_K(Pv, Kv)  # warm-up (first launches)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        q.build_K(Pv, Kv)
+        E = q.exchange_energy(Pv, Kv)
+        dt = time.perf_counter() - t0
+        st = q.stats()
+        n1 = sum(st.n_quartets_pass[1])
+        n = sum(st.n_quartets_computed)
+        return E, Kv.cpu().numpy(), dt, (n1 / n if n else 0.0)
+
+    E64, K64, t64, _ = one(hfx.HFX_PREC_FP64, math.inf)
+    rows = []
+    for b in (float(x) for x in args.promote_sweep.split(",")):
+        E, K, dt, frac = one(hfx.HFX_PREC_MIXED, b)
+        rows.append({"promote": b, "E_x": E, "abs_dE_x": abs(E - E64), "max_abs_dK": float(np.abs(K - K64).max()),
+                     "s": dt, "fp64_quartet_share": frac})
+    return {"check": "mixed_vs_fp64", "atoms": args.atoms, "prim_cutoff": args.prim_cutoff, "E_x_fp64": E64,
+            "s_fp64": t64, "max_abs_K": float(np.abs(K64).max()), "mixed": rows}
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -502,7 +554,12 @@ def main():
     ap.add_argument("--batch", action="store_true", help="many small systems per build (batched vs sequential)")
     ap.add_argument("--batch-systems", type=int, default=64)
     ap.add_argument("--batch-atoms", default="8,24", help="cluster sizes (atoms), min,max")
+    ap.add_argument("--mixed-vs-fp64", action="store_true", help="precision check: one mixed and one FP64 build")
+    ap.add_argument("--promote-sweep", default="inf,1e-2,1e-3,1e-4", help="FP64-promotion bounds for the check")
     args = ap.parse_args()
+    if args.mixed_vs_fp64:
+        print(json.dumps(run_precision_check(args)), flush=True)
+        return 0
     if args.batch:
         print(json.dumps(run_batch(args)), flush=True)
         return 0

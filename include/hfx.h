@@ -261,7 +261,13 @@ long long hfx_setup_bytes_estimate(const hfx_shell_desc* shells, int n_shells, c
  * hfx_server_step() synchronises it. */
 typedef struct hfx_server_s hfx_server;
 
-typedef enum { HFX_REQ_QUEUED = 0, HFX_REQ_ACTIVE = 1, HFX_REQ_DONE = 2, HFX_REQ_FAILED = 3 } hfx_request_state;
+typedef enum {
+  HFX_REQ_QUEUED = 0,
+  HFX_REQ_ACTIVE = 1,
+  HFX_REQ_DONE = 2,
+  HFX_REQ_FAILED = 3,
+  HFX_REQ_CANCELLED = 4
+} hfx_request_state;
 
 typedef struct {
   long long mem_budget; /* device bytes for admitted requests; <= 0: 80% of the free memory at creation */
@@ -309,7 +315,17 @@ hfx_status hfx_server_step(hfx_server* srv, int* n_active);
  * of the builds done so far. */
 hfx_status hfx_server_poll(hfx_server* srv, long long ticket, hfx_request_info* info, double* E_x);
 
-/* Forget a finished (done or failed) request; HFX_ERR_BUSY otherwise. */
+/* Cancel a request: a queued one leaves the queue at once, an active one at
+ * the next step boundary (its device memory is then released); its state
+ * becomes HFX_REQ_CANCELLED.  HFX_ERR_BUSY for a finished request. */
+hfx_status hfx_server_cancel(hfx_server* srv, long long ticket);
+
+/* Test hook (failure injection on the host, no device fault): the setup of a
+ * still-queued request fails with `status` when it is admitted, as a failed
+ * allocation or build would; the other requests are unaffected. */
+hfx_status hfx_server_inject_setup_failure(hfx_server* srv, long long ticket, int status);
+
+/* Forget a finished (done, failed or cancelled) request; HFX_ERR_BUSY otherwise. */
 hfx_status hfx_server_release(hfx_server* srv, long long ticket);
 
 hfx_status hfx_server_get_info(hfx_server* srv, hfx_server_info* out);

@@ -365,7 +365,11 @@ def _write_if_changed(path, text):
 # kind 2 (bra HRR):  v = s0 + AB_i s1;   kind 3 (ket HRR): v = s0 + CD_i s1
 # VRR slots: 0 = constant zero, 1..L+1 = G_0..G_L, then nodes by level
 # (level = |e| + |f|).  HRR slots: 0..NACC-1 = contracted [e0|f0], then nodes.
-COOP_MIN_ACC = int(os.environ.get("HFX_COOP_MIN_ACC", "900"))  # (dd|dd): 961 accumulators
+# Classes with at least this many accumulators use the cooperative
+# (table-interpreter) kernel.  Measured on GB300 (100-atom HSE build): (dd|dd),
+# 961 accumulators, runs 2.1x faster on the lockstep warp-split kernel, so by
+# default no class does; HFX_COOP_MIN_ACC=900 brings it back for (dd|dd).
+COOP_MIN_ACC = int(os.environ.get("HFX_COOP_MIN_ACC", "100000"))
 
 
 def coop_tables(la, lb, lc, ld):

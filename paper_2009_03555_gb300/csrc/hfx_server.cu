@@ -61,6 +61,8 @@ struct Request {
   double* K_out = nullptr;         // n_values, written when the last build is done
   long long n_values = 0;
   long long estimate = 0;
+  bool cancel = false;          // retire at the next step boundary
+  hfx_status inject = HFX_OK;   // test hook: the next setup fails with this status
   std::vector<double> E;
   // device state while active
   hfx_basis* basis = nullptr;
@@ -131,6 +133,11 @@ void finish(hfx_server_s* s, Request* r, int state, hfx_status st) {
 
 // Setup of an admitted request: basis, quartet lists, P and K buffers.
 hfx_status setup_request(hfx_server_s* s, Request* r) {
+  if (r->inject != HFX_OK) {  // failure injected on the host (tests)
+    const hfx_status st = r->inject;
+    r->inject = HFX_OK;
+    return srv_fail(st, "injected setup failure");
+  }
   hfx_status st = hfx_create_basis(r->shells.data(), (int)r->shells.size(), r->xyz.data(), r->n_atoms, s->stream,
                                    &r->basis);
   if (st != HFX_OK) return st;
@@ -271,6 +278,16 @@ hfx_status hfx_server_submit(hfx_server* s, const hfx_shell_desc* shells, int n_
 
 hfx_status hfx_server_step(hfx_server* s, int* n_active) {
   if (!s) return srv_fail(HFX_ERR_INVALID_ARG, "NULL server");
+  // requests cancelled while active leave at this step boundary
+  {
+    std::vector<Request*> keep, gone;
+    for (Request* r : s->active) (r->cancel ? gone : keep).push_back(r);
+    if (!gone.empty()) {
+      s->drop_groups();  // the batches refer to the leaving requests' quartet lists
+      for (Request* r : gone) finish(s, r, HFX_REQ_CANCELLED, HFX_OK);
+      s->active.swap(keep);
+    }
+  }
   hfx_status st = admit(s);
   if (st != HFX_OK) return st;
   if (n_active) *n_active = (int)s->active.size();
@@ -308,22 +325,20 @@ hfx_status hfx_server_step(hfx_server* s, int* n_active) {
   }
   s->stats.steps += 1;
   // retire finished requests
-  std::vector<Request*> still;
-  for (Request* r : s->active) {
-    if (r->info.builds_done < r->info.n_builds) {
-      still.push_back(r);
-      continue;
+  std::vector<Request*> still, gone;
+  for (Request* r : s->active) (r->info.builds_done < r->info.n_builds ? still : gone).push_back(r);
+  if (!gone.empty()) {
+    s->drop_groups();  // the batches refer to the leaving requests' quartet lists
+    for (Request* r : gone) {
+      if (r->K_out) {
+        const cudaError_t e = cudaMemcpyAsync(r->K_out, r->K, (size_t)r->n_values * sizeof(double),
+                                              cudaMemcpyDeviceToHost, s->stream);
+        if (e == cudaSuccess) cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) return srv_fail(HFX_ERR_CUDA, std::string("K download: ") + cudaGetErrorString(e));
+      }
+      finish(s, r, HFX_REQ_DONE, HFX_OK);
     }
-    if (r->K_out) {
-      const cudaError_t e =
-          cudaMemcpyAsync(r->K_out, r->K, (size_t)r->n_values * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
-      if (e == cudaSuccess) cudaStreamSynchronize(s->stream);
-      if (e != cudaSuccess) return srv_fail(HFX_ERR_CUDA, std::string("K download: ") + cudaGetErrorString(e));
-    }
-    finish(s, r, HFX_REQ_DONE, HFX_OK);
-    s->dirty = true;
   }
-  if (s->dirty) s->drop_groups();
   s->active.swap(still);
   if (n_active) *n_active = (int)s->active.size();
   return HFX_OK;
@@ -340,12 +355,40 @@ hfx_status hfx_server_poll(hfx_server* s, long long ticket, hfx_request_info* in
   return HFX_OK;
 }
 
+hfx_status hfx_server_cancel(hfx_server* s, long long ticket) {
+  if (!s) return srv_fail(HFX_ERR_INVALID_ARG, "NULL server");
+  auto it = s->all.find(ticket);
+  if (it == s->all.end()) return srv_fail(HFX_ERR_INVALID_ARG, "unknown ticket");
+  Request* r = it->second.get();
+  if (r->info.state == HFX_REQ_QUEUED) {
+    s->queue.erase(std::find(s->queue.begin(), s->queue.end(), r));
+    finish(s, r, HFX_REQ_CANCELLED, HFX_OK);
+    return HFX_OK;
+  }
+  if (r->info.state == HFX_REQ_ACTIVE) {
+    r->cancel = true;
+    return HFX_OK;
+  }
+  return srv_fail(HFX_ERR_BUSY, "request already finished");
+}
+
+hfx_status hfx_server_inject_setup_failure(hfx_server* s, long long ticket, int status) {
+  if (!s) return srv_fail(HFX_ERR_INVALID_ARG, "NULL server");
+  auto it = s->all.find(ticket);
+  if (it == s->all.end()) return srv_fail(HFX_ERR_INVALID_ARG, "unknown ticket");
+  if (it->second->info.state != HFX_REQ_QUEUED) return srv_fail(HFX_ERR_BUSY, "request already admitted");
+  if (status == HFX_OK) return srv_fail(HFX_ERR_INVALID_ARG, "status must be an error");
+  it->second->inject = (hfx_status)status;
+  return HFX_OK;
+}
+
 hfx_status hfx_server_release(hfx_server* s, long long ticket) {
   if (!s) return srv_fail(HFX_ERR_INVALID_ARG, "NULL server");
   auto it = s->all.find(ticket);
   if (it == s->all.end()) return srv_fail(HFX_ERR_INVALID_ARG, "unknown ticket");
   const int st = it->second->info.state;
-  if (st != HFX_REQ_DONE && st != HFX_REQ_FAILED) return srv_fail(HFX_ERR_BUSY, "request not finished");
+  if (st != HFX_REQ_DONE && st != HFX_REQ_FAILED && st != HFX_REQ_CANCELLED)
+    return srv_fail(HFX_ERR_BUSY, "request not finished");
   s->all.erase(it);
   return HFX_OK;
 }

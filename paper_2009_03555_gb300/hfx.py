@@ -81,6 +81,7 @@ EXPORTED = ["hfx_create_basis", "hfx_build_quartets", "hfx_value_count", "hfx_bu
             "hfx_batch_destroy", "hfx_quartets_device_bytes", "hfx_basis_device_bytes", "hfx_pattern_value_count",
             "hfx_pack_dense_host", "hfx_setup_bytes_estimate", "hfx_server_create", "hfx_server_submit",
             "hfx_server_step", "hfx_server_poll", "hfx_server_release", "hfx_server_get_info", "hfx_server_destroy",
+            "hfx_server_cancel", "hfx_server_inject_setup_failure",
             "hfx_destroy_basis", "hfx_destroy_quartets", "hfx_last_error"]
 
 _lib = None
@@ -104,7 +105,7 @@ class ServerInfo(ctypes.Structure):
                 ("max_active_seen", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
-HFX_REQ_QUEUED, HFX_REQ_ACTIVE, HFX_REQ_DONE, HFX_REQ_FAILED = 0, 1, 2, 3
+HFX_REQ_QUEUED, HFX_REQ_ACTIVE, HFX_REQ_DONE, HFX_REQ_FAILED, HFX_REQ_CANCELLED = 0, 1, 2, 3, 4
 
 
 def load(path: str = LIB_PATH):
@@ -154,6 +155,8 @@ def load(path: str = LIB_PATH):
     lib.hfx_server_step.argtypes = [V, ctypes.POINTER(I)]
     lib.hfx_server_poll.argtypes = [V, LL, ctypes.POINTER(RequestInfo), V]
     lib.hfx_server_release.argtypes = [V, LL]
+    lib.hfx_server_cancel.argtypes = [V, LL]
+    lib.hfx_server_inject_setup_failure.argtypes = [V, LL, I]
     lib.hfx_server_get_info.argtypes = [V, ctypes.POINTER(ServerInfo)]
     lib.hfx_server_destroy.argtypes = [V]
     lib.hfx_server_destroy.restype = None
@@ -505,6 +508,12 @@ class Server:
     def K_values(self, ticket):
         """K values (pattern layout) of the last build of a finished request."""
         return self._req[ticket][2]
+
+    def cancel(self, ticket):
+        _check(load().hfx_server_cancel(self.handle, int(ticket)))
+
+    def inject_setup_failure(self, ticket, status):
+        _check(load().hfx_server_inject_setup_failure(self.handle, int(ticket), int(status)))
 
     def release(self, ticket):
         _check(load().hfx_server_release(self.handle, int(ticket)))

@@ -54,8 +54,9 @@ def test_class_table(lib):
         ne = sum(n(l) for l in range(ci.la, ci.la + ci.lb + 1))
         nf = sum(n(l) for l in range(ci.lc, ci.lc + ci.ld + 1))
         assert ci.n_acc == ne * nf
-        # kernel family by accumulator count: per-thread < 90 <= warp-split < 900 <= cooperative
-        assert ci.kernel_kind == (2 if ci.n_acc >= 900 else (1 if ci.n_acc >= 90 else 0))
+        # kernel family by accumulator count: per-thread below 90, warp-split from 90 up
+        # (the cooperative kernel is opt-in, HFX_COOP_MIN_ACC)
+        assert ci.kernel_kind == (1 if ci.n_acc >= 90 else 0)
         seen.add((ci.la, ci.lb, ci.lc, ci.ld))
     assert len(seen) == 21
     with pytest.raises(hfx.HFXError):

@@ -51,15 +51,16 @@ def test_quartet_integrals_fp64(ch3, kname):
         assert np.abs(g - r).max() <= 1e-12 * max(scale, 1.0), (q, np.abs(g - r).max(), scale)
 
 
-def test_quartet_integrals_mixed(ch3):
+@pytest.mark.parametrize("kname", ["coulomb", "erfc"])
+def test_quartet_integrals_mixed(ch3, kname):
     from paper_2009_03555_gb300 import hfx
     rng = np.random.default_rng(22)
     qs = _all_class_quartets(ch3, rng, per_class=1)
     b = hfx.Basis(ch3)
-    got = b.eval_quartets(qs, kernel=hfx.HFX_KERNEL_ERFC, omega=0.11, precision=hfx.HFX_PREC_MIXED)
+    got = b.eval_quartets(qs, kernel=KMAP[kname], omega=0.11, precision=hfx.HFX_PREC_MIXED)
     ob = oracle.Basis(ch3)
-    ref = oracle.quartets(ob, qs, oracle.KERNEL_ERFC, 0.11)
-    Q = oracle.schwarz(ob, oracle.KERNEL_ERFC, 0.11)
+    ref = oracle.quartets(ob, qs, KMAP[kname], 0.11)
+    Q = oracle.schwarz(ob, KMAP[kname], 0.11)
     for q, g, r in zip(qs, got, ref):
         qq = Q[q[0], q[1]] * Q[q[2], q[3]]
         assert np.abs(g - r).max() <= 2e-4 * qq + 1e-15, (q, np.abs(g - r).max(), qq)

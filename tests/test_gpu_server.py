@@ -153,3 +153,39 @@ def test_graph_replay_equals_launches():
     b = _run(hfx.Server(use_graph=True), reqs, opts)
     for i in range(len(reqs)):
         np.testing.assert_allclose(b[i][1], a[i][1], rtol=1e-12, atol=0)
+
+
+def test_cancel_and_injected_setup_failure():
+    """Host-side failure handling: a cancelled queued request never runs, an
+    active one leaves at the next step with its memory released, and a setup
+    failure injected on the host fails that request only."""
+    from paper_2009_03555_gb300 import hfx
+    reqs = _requests(n_builds=(3, 3, 3))
+    opts = _opts(1)
+    ref = _run(hfx.Server(), reqs, opts)
+    srv = hfx.Server()
+    t = [srv.submit(s, mask, opts, Ps) for s, mask, Ps in reqs]
+    srv.inject_setup_failure(t[2], 2)   # as if its allocation had failed
+    srv.cancel(t[1])                    # still queued
+    assert srv.poll(t[1])[0].state == hfx.HFX_REQ_CANCELLED
+    srv.step()                          # t[0] admitted and built once; t[2] fails at setup
+    assert srv.poll(t[2])[0].state == hfx.HFX_REQ_FAILED and srv.poll(t[2])[0].status == 2
+    assert srv.poll(t[0])[0].state == hfx.HFX_REQ_ACTIVE
+    for _ in range(10):
+        srv.step()
+        if srv.poll(t[0])[0].state == hfx.HFX_REQ_DONE:
+            break
+    info, E = srv.poll(t[0])
+    assert info.state == hfx.HFX_REQ_DONE
+    np.testing.assert_allclose(E, ref[0][1], rtol=1e-9, atol=0)
+    # an active request cancelled between steps leaves at the next one
+    srv2 = hfx.Server()
+    u = srv2.submit(*reqs[0][:2], opts, reqs[0][2])
+    srv2.step()
+    assert srv2.poll(u)[0].state == hfx.HFX_REQ_ACTIVE and srv2.info().used_bytes > 0
+    srv2.cancel(u)
+    srv2.step()
+    ri, E2 = srv2.poll(u)
+    assert ri.state == hfx.HFX_REQ_CANCELLED and ri.builds_done == 1
+    assert srv2.info().used_bytes == 0 and srv2.info().n_active == 0
+    srv2.release(u)
