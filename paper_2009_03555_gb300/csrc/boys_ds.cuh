@@ -148,10 +148,11 @@ __device__ __forceinline__ void boys_ds(const float* __restrict__ tab, ds T, ds*
 // Primitive-quartet prologue of the mixed path, FP64-accurate in
 // double-single: T = rho |PQ|^2 from double-single P, Q, p, q; the Boys
 // function(s); the erfc difference F_m(T) - f^{m+1/2} F_m(f T) taken before
-// rounding; then G_m = pref * D_m rounded to FP32 (w2 = omega^2 as a
-// double-single pair formed once per launch; the prefactor
-// 2 pi^{5/2} K_ab K_cd / (p q sqrt(p+q)) needs no more: K_ab and K_cd were
-// formed in FP64 when the pairs were built).  Also returns FP32 1/(p+q) and PQ.
+// rounding; then G_m = pref * D_m, with the prefactor
+// 2 pi^{5/2} K_ab K_cd / (p q sqrt(p+q)) also in double-single, rounded to
+// FP32 once (w2 = omega^2 as a double-single pair formed once per launch;
+// K_ab c_a c_b / p were formed in FP64 when the pairs were built and are read
+// as FP32).  Also returns FP32 1/(p+q) and PQ.
 template <int L>
 __device__ __forceinline__ void prologue_ds(const float* __restrict__ tab, int kernel, ds w2,
                                             const PrimPair& pb, const PrimPair& pk, float* G, float& inv_s,
@@ -170,13 +171,20 @@ __device__ __forceinline__ void prologue_ds(const float* __restrict__ tab, int k
   }
   const ds T = ds_mul(rho, pq2);
   inv_s = rs.hi;
-  const float pref = 3.498683548e+01f * pb.kpf * pk.kpf * rsqrtf(s.hi);  // 2 pi^{5/2}
+  // prefactor 2 pi^{5/2} K_ab K_cd / sqrt(p+q) in double-single, so that G_m
+  // is the FP32 rounding of an accurate product (an FP32 product with an
+  // approximate reciprocal square root would carry the same small relative
+  // error into every integral)
+  const ds pref = ds_mulf(ds_mulf(ds_mul({3.498683548e+01f, 1.175513376e-06f}, ds_rsqrt(s)), pb.kpf), pk.kpf);
   ds F[L + 1];
   if (kernel != kErf) {
     boys_ds<L>(tab, T, F);
     if (kernel == kCoulomb) {
 #pragma unroll
-      for (int m = 0; m <= L; ++m) G[m] = pref * (F[m].hi + F[m].lo);
+      for (int m = 0; m <= L; ++m) {
+        const ds g = ds_mul(pref, F[m]);
+        G[m] = g.hi + g.lo;
+      }
       return;
     }
   }
@@ -188,7 +196,8 @@ __device__ __forceinline__ void prologue_ds(const float* __restrict__ tab, int k
   for (int m = 0; m <= L; ++m) {
     const ds cw = ds_mul(c, Fw[m]);
     const ds d = (kernel == kErfc) ? ds_sub(F[m], cw) : cw;
-    G[m] = pref * (d.hi + d.lo);
+    const ds g = ds_mul(pref, d);
+    G[m] = g.hi + g.lo;
     c = ds_mul(c, f);
   }
 }
