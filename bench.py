@@ -160,7 +160,7 @@ def run_ours(args, rank, world):
     prec = hfx.HFX_PREC_MIXED if args.precision == "mixed" else hfx.HFX_PREC_FP64
     opts = hfx.make_opts(kernel=hfx.HFX_KERNEL_ERFC, omega=0.11, screen=True, tau=1e-8, density_screen=True,
                          eps=1e-8, prim_cutoff=args.prim_cutoff, precision=prec,
-                         fp64_promote_bound=args.promote, n_block=args.n_block)
+                         fp64_promote_bound=args.promote, n_block=args.n_block, promote_min_l=args.promote_min_l)
     basis = hfx.Basis(s)
     q = hfx.Quartets(basis, opts, mask)
     Pd = torch.from_numpy(P).to(dev)
@@ -268,9 +268,11 @@ def run_ours(args, rank, world):
         "config": {"workload": f"{args.atoms}-atom C/H cluster, HSE erfc w=0.11, Schwarz 1e-8 + density screening, "
                                f"P cut 14 bohr, {args.precision}"
                                + (f" with FP64 promotion above Q_IJ Q_KL P_scr = {args.promote:g}"
+                                  + (f" in classes of total l >= {args.promote_min_l}" if args.promote_min_l else "")
                                   if prec == hfx.HFX_PREC_MIXED and math.isfinite(args.promote) else ""),
                    "atoms": args.atoms, "n_bf": int(s.n_bf), "precision": args.precision,
-                   "fp64_promote_bound": args.promote, "n_block": args.n_block, "prim_cutoff": args.prim_cutoff,
+                   "fp64_promote_bound": args.promote, "promote_min_l": args.promote_min_l,
+                   "n_block": args.n_block, "prim_cutoff": args.prim_cutoff,
                    "l2": "flushed (256 MB write) between timed steps", "parallelism": f"replicas x{world}"},
         "quartets_per_build": n_q, "prim_quartets_per_build": n_pq,
         "eri_quartets_per_s": world * n_q / (ms * 1e-3),
@@ -501,10 +503,10 @@ def run_precision_check(args):
     dev = torch.device("cuda")
     s, P, mask = workload(args.atoms)
 
-    def one(prec, promote):
+    def one(prec, promote, min_l=0):
         opts = hfx.make_opts(kernel=hfx.HFX_KERNEL_ERFC, omega=0.11, screen=True, tau=1e-8, density_screen=True,
                              eps=1e-8, prim_cutoff=args.prim_cutoff, precision=prec,
-                             fp64_promote_bound=promote, n_block=args.n_block)
+                             fp64_promote_bound=promote, n_block=args.n_block, promote_min_l=min_l)
         b = hfx.Basis(s)
         q = hfx.Quartets(b, opts, mask)
         Pv = torch.empty(q.n_values, dtype=torch.float64, device=dev)
@@ -527,9 +529,11 @@ def run_precision_check(args):
     else:  # FP64 energy of an earlier run of the same workload (energies only)
         E64, K64, t64 = args.fp64_energy, None, None
     rows = []
-    for b in (float(x) for x in args.promote_sweep.split(",")):
-        E, K, dt, frac = one(hfx.HFX_PREC_MIXED, b)
-        rows.append({"promote": b, "E_x": E, "abs_dE_x": abs(E - E64),
+    for item in args.promote_sweep.split(","):  # bound, or bound:min_l
+        b, _, ml = item.partition(":")
+        b, ml = float(b), int(ml or 0)
+        E, K, dt, frac = one(hfx.HFX_PREC_MIXED, b, ml)
+        rows.append({"promote": b, "promote_min_l": ml, "E_x": E, "abs_dE_x": abs(E - E64),
                      "max_abs_dK": float(np.abs(K - K64).max()) if K64 is not None else None,
                      "s": dt, "fp64_quartet_share": frac})
     return {"check": "mixed_vs_fp64", "atoms": args.atoms, "prim_cutoff": args.prim_cutoff, "E_x_fp64": E64,
@@ -544,9 +548,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--atoms", type=int, default=400)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    # quartets with Q_IJ Q_KL P_scr above this run in FP64; 2.5e-5 keeps the
-    # 400-atom mixed build within 1e-6 Ha of the FP64 build (measured 6.8e-7)
-    ap.add_argument("--promote", type=float, default=2.5e-5)
+    # (dd|dd) quartets with Q_IJ Q_KL P_scr above 1e-5 run in FP64: the 400-atom
+    # mixed build is then within 1e-6 Ha of the FP64 build (measured 2.9e-7)
+    ap.add_argument("--promote", type=float, default=1e-5)
+    ap.add_argument("--promote-min-l", type=int, default=8, help="promotion only in classes of total l >= this")
     ap.add_argument("--prim-cutoff", type=float, default=1e-13)
     ap.add_argument("--n-block", type=int, default=128)
     ap.add_argument("--no-e2e", action="store_true")

@@ -80,7 +80,8 @@ typedef struct {
   int precision;              /* hfx_precision */
   double fp64_promote_bound;  /* MIXED: quartets with Q_IJ Q_KL P_scr above this run in FP64 */
   int n_block;                /* quartets per work-queue batch (the paper's n_block, Sec. 4); 0 = default */
-  int reserved[3];
+  int promote_min_l;          /* MIXED: promotion only in classes with la+lb+lc+ld >= this (0: every class) */
+  int reserved[2];
 } hfx_opts;
 
 /* Atom-pair block pattern: CSR over atoms (host arrays). */

@@ -762,12 +762,14 @@ static BuildArgs plan_args(Plan& pl, int cls) {
 static hfx_status plan_classes(Plan& pl, cudaStream_t s, bool fork, bool events) {
   const hfx_opts& o = pl.opts;
   const bool mixed = o.precision == HFX_PREC_MIXED;
-  const bool promote = mixed && std::isfinite(o.fp64_promote_bound);
-  const int passes = promote ? 2 : 1;
+  const bool promote_any = mixed && std::isfinite(o.fp64_promote_bound);
   if (fork) HFX_CK(cudaEventRecord(pl.fork_ev, s));
   for (int cls = 0; cls < HFX_NCLASS; ++cls) {
     for (int pass = 0; pass < 2; ++pass) pl.ran[pass][cls] = false;
     if (pl.n_desc[cls] == 0) continue;
+    // promotion applies to classes of total angular momentum >= promote_min_l
+    const bool promote = promote_any && hfx_class_table[cls][6] >= o.promote_min_l;
+    const int passes = promote ? 2 : 1;
     cudaStream_t cs = s;
     if (fork) {
       cs = pl.side[cls];
@@ -1497,7 +1499,7 @@ hfx_status hfx_batch_create(hfx_quartets* const* members, int n, void* stream, h
     if (oi.kernel != o0.kernel || oi.omega != o0.omega || oi.precision != o0.precision ||
         oi.screen != o0.screen || oi.tau != o0.tau || oi.density_screen != o0.density_screen ||
         oi.eps != o0.eps || oi.prim_cutoff != o0.prim_cutoff ||
-        !(oi.fp64_promote_bound == o0.fp64_promote_bound))
+        !(oi.fp64_promote_bound == o0.fp64_promote_bound) || oi.promote_min_l != o0.promote_min_l)
       return fail(HFX_ERR_INVALID_ARG, "batch members must share kernel, precision and screening options");
     b->members.push_back(members[i]);
   }

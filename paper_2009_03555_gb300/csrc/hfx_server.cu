@@ -44,7 +44,8 @@ bool same_options(const hfx_opts& a, const hfx_opts& b) {
   return a.kernel == b.kernel && a.omega == b.omega && a.precision == b.precision && a.screen == b.screen &&
          a.tau == b.tau && a.density_screen == b.density_screen && a.eps == b.eps && a.prim_cutoff == b.prim_cutoff &&
          (a.fp64_promote_bound == b.fp64_promote_bound ||
-          (a.fp64_promote_bound != a.fp64_promote_bound && b.fp64_promote_bound != b.fp64_promote_bound));
+          (a.fp64_promote_bound != a.fp64_promote_bound && b.fp64_promote_bound != b.fp64_promote_bound)) &&
+         a.promote_min_l == b.promote_min_l;
 }
 
 struct Request {
