@@ -586,7 +586,7 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
         if args.ref_quartets_per_build is None:
-            args.ref_quartets_per_build = REF_QUARTETS_PER_BUILD.get(args.atoms, float("nan"))
+            args.ref_quartets_per_build = ref_quartets_per_build(args.atoms)
         res = run_reference(args, rank, world)
         if res is not None:
             print(json.dumps(res), flush=True)
@@ -610,11 +610,17 @@ def main():
     return 0
 
 
-# Canonical quartets evaluated per build of the default workload (the exact
-# count after Schwarz and density screening, read from the build statistics of
-# a GB300 run of this workload); used only to express the oracle's quartets/s
-# in builds/s for --impl reference, which runs no GPU code.
-REF_QUARTETS_PER_BUILD = {400: 3444705497}
+def ref_quartets_per_build(atoms):
+    """Canonical quartets per build of the cluster workload, counted by the
+    oracle (oracle/count_quartets.py writes tests/golden/); used only to express
+    the oracle's quartets/s in builds/s for --impl reference, which runs no GPU
+    code."""
+    path = os.path.join(ROOT, "tests", "golden", f"quartet_count_hse_c{atoms}.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["canonical_quartets"])
+    except (OSError, KeyError, ValueError):
+        return float("nan")
 
 if __name__ == "__main__":
     sys.exit(main())

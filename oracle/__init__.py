@@ -65,6 +65,8 @@ def _load():
         lib.oracle_build_K.restype = ctypes.c_longlong
         lib.oracle_K_shell_pairs.argtypes = [I, P, P, P, P, P, P, P, I, D, I, D, I, D, I, P, P, I, P, P, P]
         lib.oracle_K_shell_pairs.restype = ctypes.c_longlong
+        lib.oracle_count_quartets.argtypes = [I, P, P, P, P, P, P, P, I, D, D, I, D, I, P]
+        lib.oracle_count_quartets.restype = ctypes.c_longlong
         lib.oracle_max_threads.restype = I
         _lib = lib
     return _lib
@@ -181,6 +183,21 @@ def K_shell_pairs(basis, P, pairs, kernel: int = KERNEL_COULOMB, omega: float = 
     shp = [(int(nf[i]), int(nf[j])) for i, j in pr]
     cut = lambda a: [a[off[q]:off[q + 1]].reshape(shp[q]) for q in range(pr.shape[0])]
     return cut(K), cut(W1), cut(W0), int(n)
+
+
+def count_quartets(basis, P, kernel: int = KERNEL_COULOMB, omega: float = 0.11, tau: float = 1e-8,
+                   density_screen: bool = False, eps: float = 1e-8, nthreads: int | None = None):
+    """Number of canonical shell quartets surviving Schwarz (and density)
+    screening, counted without evaluating them; also returns the Schwarz
+    bounds (ns x ns)."""
+    b = _basis(basis)
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    assert P.shape == (b.nbf, b.nbf)
+    Q = np.zeros((b.n_shells, b.n_shells))
+    nt = max_threads() if nthreads is None else int(nthreads)
+    n = _load().oracle_count_quartets(*b.args(), _p(P), int(kernel), float(omega), float(tau),
+                                      int(bool(density_screen)), float(eps), nt, _p(Q))
+    return int(n), Q
 
 
 def exchange_energy(P, K) -> float:

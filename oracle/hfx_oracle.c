@@ -568,6 +568,65 @@ long long oracle_K_shell_pairs(int n_shells, const double *xyz, const int *l, co
   return count;
 }
 
+/* Number of canonical shell quartets (each unordered pair of shell pairs
+ * once) that survive the screening of Sec. 2 (the predicate of survives()),
+ * counted without evaluating any quartet: Schwarz bounds of every shell pair
+ * with the run's kernel, pairs ranked by descending Q, and for each pair a the
+ * pairs b ranked at or before a with Q_a Q_b > tau (a prefix of the ranking)
+ * tested one by one.  Q_out (ns x ns, may be NULL) receives the bounds. */
+typedef struct { double q; int i, j; } qpair_t;
+
+static int qpair_desc(const void *x, const void *y) {
+  const qpair_t *a = (const qpair_t *)x, *b = (const qpair_t *)y;
+  if (a->q != b->q) return a->q > b->q ? -1 : 1;
+  if (a->i != b->i) return a->i < b->i ? -1 : 1;
+  return a->j < b->j ? -1 : (a->j > b->j);
+}
+
+long long oracle_count_quartets(int n_shells, const double *xyz, const int *l, const int *prim_off,
+                                const double *alpha, const double *coef, const long long *func_off,
+                                const double *P, int kernel, double omega, double tau, int dscreen, double eps,
+                                int nthreads, double *Q_out) {
+  basis_t B;
+  fill_basis(&B, n_shells, xyz, l, prim_off, alpha, coef, func_off);
+  int ns = n_shells;
+  double *Q = (double *)calloc((size_t)ns * ns, sizeof(double));
+  double *Pm = (double *)calloc((size_t)ns * ns, sizeof(double));
+  oracle_schwarz(ns, xyz, l, prim_off, alpha, coef, func_off, kernel, omega, Q);
+  shell_pmax(&B, P, Pm);
+  long long npair = (long long)ns * (ns + 1) / 2;
+  qpair_t *pr = (qpair_t *)malloc(sizeof(qpair_t) * (size_t)npair);
+  long long k = 0;
+  for (int I = 0; I < ns; ++I)
+    for (int J = 0; J <= I; ++J) {
+      pr[k].q = Q[I * ns + J];
+      pr[k].i = I;
+      pr[k].j = J;
+      ++k;
+    }
+  qsort(pr, (size_t)npair, sizeof(qpair_t), qpair_desc);
+  if (nthreads <= 0) nthreads = 1;
+  long long count = 0;
+#pragma omp parallel for num_threads(nthreads) schedule(dynamic, 256) reduction(+ : count)
+  for (long long a = 0; a < npair; ++a) {
+    const double qa = pr[a].q;
+    /* last b with qa q_b > tau (q descending) */
+    long long lo = 0, hi = a + 1;  /* search in [0, a] */
+    while (lo < hi) {
+      long long mid = (lo + hi) / 2;
+      if (qa * pr[mid].q > tau) lo = mid + 1;
+      else hi = mid;
+    }
+    for (long long b = 0; b < lo; ++b)
+      if (survives(ns, Q, Pm, 1, tau, dscreen, eps, pr[a].i, pr[a].j, pr[b].i, pr[b].j)) ++count;
+  }
+  if (Q_out) memcpy(Q_out, Q, sizeof(double) * (size_t)ns * ns);
+  free(pr);
+  free(Q);
+  free(Pm);
+  return count;
+}
+
 int oracle_max_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();

@@ -5,7 +5,9 @@ precision, primitive cutoff 1e-13, work-queue batches of 128 quartets.
 
 The oracle cannot build the whole K at this size, so it computes sampled
 exchange blocks K_IJ one shell pair at a time straight from the definition
-(every ordered (K, L) whose quartet (I K | J L) survives the same screening).
+(every ordered (K, L) whose quartet (I K | J L) survives the same screening),
+and the number of surviving canonical quartets (stored by
+oracle/count_quartets.py), which the build must match exactly.
 
 Tolerance, derived from the per-integral bounds of the mixed path: each
 integral of a surviving quartet is within 2e-4 Q_IK Q_JL of the exact value
@@ -86,6 +88,13 @@ def test_sampled_blocks_400_atoms_mixed():
     del Kd, Pd
     assert np.isfinite(E) and E < 0.0
     np.testing.assert_array_equal(K, K.T)
+    # every surviving canonical quartet computed once: the oracle's count of the
+    # same screening (oracle/count_quartets.py, tests/golden/)
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", f"quartet_count_hse_c{N_ATOMS}.json")) as fh:
+        n_oracle = json.load(fh)["canonical_quartets"]
+    assert sum(q.stats().n_quartets_computed) == n_oracle
 
     pairs = _sample_pairs(s, np.random.default_rng(2009_03555 + 400))
     blocks, W1, W0, n = oracle.K_shell_pairs(oracle.Basis(s), P, pairs, kernel=oracle.KERNEL_ERFC,

@@ -175,3 +175,16 @@ def test_K_shell_pairs_screened_equals_brute(tiny):
         # Schwarz: |K_ij| <= sum over surviving (K,L) of Q_IK Q_JL sum |P_kl| = W1
         assert np.all(np.abs(k) <= w1 * (1 + 1e-12) + 1e-300)
         assert np.all(w1 <= Q.max() ** 2 * w0 * (1 + 1e-12))
+
+
+@pytest.mark.parametrize("dscreen", [False, True])
+def test_count_quartets_equals_canonical_loop(tiny, dscreen):
+    """The ranked-prefix count of surviving canonical quartets equals the
+    count of the canonical quartet loop with the same screening, and its
+    Schwarz bounds are the oracle's."""
+    s, P, b = tiny
+    kw = dict(kernel=oracle.KERNEL_ERFC, tau=1e-6, density_screen=dscreen, eps=1e-6)
+    _, n_loop = oracle.build_K(b, P, screen=True, **kw)
+    n, Q = oracle.count_quartets(b, P, **kw)
+    assert n == n_loop > 0
+    np.testing.assert_array_equal(Q, oracle.schwarz(b, oracle.KERNEL_ERFC))
