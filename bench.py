@@ -36,7 +36,10 @@ import synth  # noqa: E402
 # of one launch divided by that launch's primitive quartets.  The roofline's
 # `traffic` scales it to the timed launch; a kernel changed since its capture
 # has no entry (traffic null).
-DRAM_BYTES_PER_PRIM_QUARTET = {}
+DRAM_BYTES_PER_PRIM_QUARTET = {
+    # profiles/k_build_K_split_Cls2221_float_ch50.md: 42.0 MB for 132 623 015 primitive quartets
+    "k_build_K_split<Cls2221, float>": 42.009856e6 / 132623015,
+}
 
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 80.5: 128 FP32 FMA/clk/SM at the 2070 MHz max clock
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12     # 1.26: 2 FP64 FMA/clk/SM (1/64 of FP32)
