@@ -1,11 +1,19 @@
 // eri_kernels.cuh -- per-class kernel templates of the HFX library:
-//   * k_build_K   persistent exchange-build kernel: warps pull quartet batches
-//                 from a device work queue (atomic counter), screen the
-//                 quartets, compact the survivors so every lane works, evaluate
-//                 the contracted ERIs and scatter the four exchange
-//                 contributions into atom-pair-blocked K;
-//   * k_schwarz   Schwarz bounds Q_AB = sqrt(max |(ab|ab)|) of shell pairs;
-//   * k_eval      raw shell-quartet integrals (diagnostics and tests).
+//   * k_build_K        persistent exchange-build kernel, one thread per shell
+//                      quartet (classes with fewer than 90 accumulators): warps
+//                      pull quartet batches from a device work queue (atomic
+//                      counter), screen the quartets, compact the survivors so
+//                      every lane works, evaluate the contracted ERIs and
+//                      scatter the four exchange contributions into
+//                      atom-pair-blocked K;
+//   * k_build_K_split  the same with one warp per shell quartet and the lanes
+//                      on its primitive quartets (the d-shell classes), warps
+//                      of a block in lockstep rounds for the long recursions;
+//   * k_build_K_coop   a table-interpreter variant of the warp-per-quartet
+//                      kernel, used only when the build selects it;
+//   * k_schwarz, k_schwarz_warp  Schwarz bounds Q_AB = sqrt(max |(ab|ab)|) of
+//                      shell pairs (a thread or a warp per pair);
+//   * k_eval           raw shell-quartet integrals (diagnostics and tests).
 // Included once per angular-momentum class by the generated tu_*.cu files.
 #pragma once
 #include <cuda_runtime.h>
@@ -364,8 +372,10 @@ __global__ void __launch_bounds__(kThreadsK) k_build_K(const BuildArgs a) {
 
 
 // ------------------------------------------------------------ cooperative
-// Classes with many contracted accumulators (d-shell quartets) run one warp
-// per shell quartet.  The 32 lanes compute the FP64 prologue of 32 primitive
+// Table-interpreter variant for classes with many contracted accumulators
+// (selected at build time by the generator's accumulator threshold; by
+// default no class uses it, the warp-split kernel being faster): one warp per
+// shell quartet.  The 32 lanes compute the FP64 prologue of 32 primitive
 // quartets at once into a per-warp buffer; the warp then walks the vertical
 // recursion of each primitive quartet level by level (node tables emitted by
 // the generator, intermediates in shared memory), every lane owning a slice of
