@@ -1,9 +1,9 @@
 """Node tables of the generated ERI code (CPU, no GPU needed).
 
-The warp kernels interpret two generated tables per angular-momentum class:
-the horizontal-recursion nodes and the output slots.  The warp-split kernels
-also use the permutation that maps their reduce-scatter order to accumulator
-slots.  These tests check, for all 21 classes:
+The warp kernels interpret generated tables per angular-momentum class: the
+horizontal-recursion nodes and the output slots, the permutation that maps the
+split kernels' reduce-scatter order to accumulator slots, and (table kernel)
+the vertical-recursion nodes.  These tests check, for all 21 classes:
   * every slot index is inside the shared-memory workspace the kernels
     allocate, and nodes of one level (run by different lanes at once) never
     read a slot that another node of the same level writes;
@@ -12,7 +12,9 @@ slots.  These tests check, for all 21 classes:
     recursively (along the other Cartesian axis where there is a choice) on
     random contracted [e0|f0] values and random AB, CD;
   * the split permutation is a permutation of the accumulators, and the four
-    P blocks of the exchange contraction fit the 160-value staging buffer.
+    P blocks of the exchange contraction fit the 160-value staging buffer;
+  * the vertical-recursion tables equal the Obara-Saika recursion written out
+    recursively, likewise on random G_m and geometry.
 """
 import functools
 import importlib.util
@@ -113,3 +115,64 @@ def test_split_permutation_and_p_blocks(cls):
     assert sorted(perm) == list(range(nacc)) and nchunk == (nacc + 31) // 32
     na, nb, nc, nd = (len(g.comps(l)) for l in cls)
     assert na * nc + nb * nd + na * nd + nb * nc <= 160
+
+
+@pytest.mark.parametrize("cls", _classes(), ids=lambda c: "".join(map(str, c)))
+def test_vrr_tables(cls):
+    """The vertical-recursion node tables (interpreted as the table kernel
+    does: slot 0 = 0, slots 1..L+1 = G_0..G_L, bra nodes then ket nodes level
+    by level) equal the Obara-Saika recursion written out recursively along
+    the other axis where there is a choice, on random G_m and geometry."""
+    g = _gen()
+    la, lb, lc, ld = cls
+    L = la + lb + lc + ld
+    t = g.coop_tables(la, lb, lc, ld)
+    rng = np.random.default_rng(7 + sum(10 ** k * l for k, l in enumerate(cls)))
+    G = rng.uniform(0.1, 1.0, L + 1)
+    PA, QC, WP, WQ = (rng.uniform(-1, 1, 3) for _ in range(4))
+    oo2p, oo2q, oo2pq, rop, roq = rng.uniform(0.1, 1.0, 5)
+    ws = np.zeros(t["vrr_slots"])
+    ws[1:L + 2] = G
+    for node in t["nodes"]:
+        x, y, z, w = node
+        dst, kind, axis = x & 0xFFFF, (x >> 16) & 3, (x >> 18) & 3
+        k1, k2 = (x >> 20) & 15, (x >> 24) & 15
+        s0, s1, s2, s3 = y & 0xFFFF, y >> 16, z & 0xFFFF, z >> 16
+        assert max(dst, s0, s1, s2, s3, w) < t["vrr_slots"]
+        if kind == 0:
+            ws[dst] = PA[axis] * ws[s0] + WP[axis] * ws[s1] + k1 * oo2p * (ws[s2] - rop * ws[s3])
+        else:
+            ws[dst] = (QC[axis] * ws[s0] + WQ[axis] * ws[s1] + k1 * oo2q * (ws[s2] - roq * ws[s3])
+                       + k2 * oo2pq * ws[w])
+    got = ws[t["targets"]]
+
+    def sub(u, i):
+        v = list(u)
+        v[i] -= 1
+        return tuple(v)
+
+    @functools.lru_cache(maxsize=None)
+    def r(e, f, m):  # [e0|f0]^(m)
+        if sum(e) < 0 or min(e) < 0 or min(f) < 0:
+            return 0.0
+        if sum(f) > 0:
+            i = max(k for k in range(3) if f[k] > 0)
+            f1 = sub(f, i)
+            out = QC[i] * r(e, f1, m) + WQ[i] * r(e, f1, m + 1)
+            if f1[i] > 0:
+                out += f1[i] * oo2q * (r(e, sub(f1, i), m) - roq * r(e, sub(f1, i), m + 1))
+            if e[i] > 0:
+                out += e[i] * oo2pq * r(sub(e, i), f1, m + 1)
+            return out
+        if sum(e) > 0:
+            i = max(k for k in range(3) if e[k] > 0)
+            e1 = sub(e, i)
+            out = PA[i] * r(e1, f, m) + WP[i] * r(e1, f, m + 1)
+            if e1[i] > 0:
+                out += e1[i] * oo2p * (r(sub(e1, i), f, m) - rop * r(sub(e1, i), f, m + 1))
+            return out
+        return G[m]
+
+    v = g.VRR(la, lb, lc, ld)
+    ref = np.array([r(e, f, 0) for e in v.E for f in v.F])
+    np.testing.assert_allclose(got, ref, rtol=1e-10, atol=1e-12 * np.abs(ref).max())
