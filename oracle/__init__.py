@@ -16,6 +16,11 @@ Functions (each cites the passage it follows):
                      Schwarz and density screening (Eq. dmscreening), either by
                      the 8-fold permutation symmetry or by brute force
   exchange_energy -- E_x = -1/2 sum_ij P_ij K_ij
+  periodic_images -- the image atoms of a periodic cell's extended set
+                     (Sec. 2: the cells N, G, H of Eq. H-HFX)
+  K_periodic      -- exchange rows K^G_{mu lambda} of a periodic system,
+                     Eq. H-HFX with the Gamma-point real-space density of
+                     Eq. dm, by brute force over the extended set
 
 Parity status: every function is pinned by tests in ``tests/test_oracle_*.py``
 (closed forms, special functions from scipy/mpmath, brute-force numerical
@@ -67,6 +72,10 @@ def _load():
         lib.oracle_K_shell_pairs.restype = ctypes.c_longlong
         lib.oracle_count_quartets.argtypes = [I, P, P, P, P, P, P, P, I, D, D, I, D, I, P]
         lib.oracle_count_quartets.restype = ctypes.c_longlong
+        lib.oracle_periodic_images.argtypes = [I, P, P, D, ctypes.c_longlong, P]
+        lib.oracle_periodic_images.restype = ctypes.c_longlong
+        lib.oracle_K_periodic.argtypes = [I, P, P, P, P, P, P, I, P, P, D, D, P, I, D, I, D, I, D, I, P, P]
+        lib.oracle_K_periodic.restype = ctypes.c_longlong
         lib.oracle_max_threads.restype = I
         _lib = lib
     return _lib
@@ -203,3 +212,52 @@ def count_quartets(basis, P, kernel: int = KERNEL_COULOMB, omega: float = 0.11, 
 def exchange_energy(P, K) -> float:
     """E_x = -1/2 sum_ij P_ij K_ij."""
     return float(-0.5 * np.sum(np.asarray(P) * np.asarray(K)))
+
+
+def periodic_images(atom_xyz, lattice, r_ext: float) -> np.ndarray:
+    """(n_images, 4) rows (home atom, n1, n2, n3): every translate of a home
+    atom by n1 a1 + n2 a2 + n3 a3 (n != 0; lattice rows a_i) within ``r_ext``
+    of some home atom, atom by atom, shifts in lexicographic order."""
+    x = np.ascontiguousarray(atom_xyz, dtype=np.float64).reshape(-1, 3)
+    A = np.ascontiguousarray(lattice, dtype=np.float64).reshape(3, 3)
+    lib = _load()
+    n = lib.oracle_periodic_images(int(x.shape[0]), _p(x), _p(A), float(r_ext), 0, None)
+    if n < 0:
+        raise ValueError("singular lattice or negative radius")
+    out = np.zeros((max(int(n), 1), 4), dtype=np.int32)
+    lib.oracle_periodic_images(int(x.shape[0]), _p(x), _p(A), float(r_ext), int(n), _p(out))
+    return out[:int(n)]
+
+
+def K_periodic(sysobj, P_home, lattice, r_ext: float, r_P: float, kernel: int = KERNEL_COULOMB,
+               omega: float = 0.11, screen: bool = False, tau: float = 1e-8, density_screen: bool = False,
+               eps: float = 1e-8, nthreads: int | None = None):
+    """Exchange rows of a periodic system (Eq. H-HFX without the -1/2).
+
+    Returns (K_rows, ext, n): K_rows (home nbf x extended nbf) with
+    K_rows[mu, lambda^G] = sum_{N,H,nu,sigma} P^{H-N}_{nu sigma} (mu^0 nu^N | lambda^G sigma^H);
+    ext (n_ext x 4) the extended atoms (home atom, n1, n2, n3), home atoms
+    first, each carrying its home atom's functions in home order; n the
+    number of surviving ordered shell quartets.  P^L_{nu sigma} is the home
+    density P_home where the atoms of nu^0 and sigma^L are at most ``r_P``
+    apart, else 0."""
+    b = Basis(sysobj)
+    P = np.ascontiguousarray(P_home, dtype=np.float64)
+    assert P.shape == (b.nbf, b.nbf)
+    x = np.ascontiguousarray(sysobj.atom_xyz, dtype=np.float64)
+    A = np.ascontiguousarray(lattice, dtype=np.float64).reshape(3, 3)
+    sa = np.ascontiguousarray(sysobj.shell_atom, dtype=np.int32)
+    img = periodic_images(x, A, r_ext)
+    ext = np.zeros((sysobj.n_atoms + img.shape[0], 4), dtype=np.int32)
+    # every extended atom carries its home atom's functions
+    nf_atom = np.diff(sysobj.atom_func_off)
+    nbf_ext = int(nf_atom.sum() + nf_atom[img[:, 0]].sum())
+    K = np.zeros((b.nbf, nbf_ext))
+    nt = max_threads() if nthreads is None else int(nthreads)
+    n = _load().oracle_K_periodic(b.n_shells, _p(sa), _p(b.l), _p(b.prim_off), _p(b.alpha), _p(b.coef),
+                                  _p(b.func_off), int(sysobj.n_atoms), _p(x), _p(A), float(r_ext), float(r_P),
+                                  _p(P), int(kernel), float(omega), int(bool(screen)), float(tau),
+                                  int(bool(density_screen)), float(eps), nt, _p(ext), _p(K))
+    if n < 0:
+        raise ValueError("bad input (shells not grouped by atom, singular lattice or negative radius)")
+    return K, ext, int(n)

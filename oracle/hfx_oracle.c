@@ -627,6 +627,208 @@ long long oracle_count_quartets(int n_shells, const double *xyz, const int *l, c
   return count;
 }
 
+/* ------------------------------------------------------------------------
+ * Periodic systems (Sec. 2, Eq. H-HFX): mu runs over the home cell, nu, lambda
+ * and sigma over the cells N, G, H of the auxiliary supercell.
+ * ------------------------------------------------------------------------ */
+
+/* Rows b_i of (A^T)^{-1} for the lattice A (rows a_i): n_i = b_i . L for the
+ * lattice vector L = sum n_i a_i.  Returns 0 for a singular lattice. */
+static int reciprocal_rows(const double *A, double *b) {
+  const double det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+                     A[2] * (A[3] * A[7] - A[4] * A[6]);
+  if (!(fabs(det) > 0.0)) return 0;
+  /* b_i = (a_j x a_k) / det, (i, j, k) cyclic */
+  for (int i = 0; i < 3; ++i) {
+    const double *aj = A + 3 * ((i + 1) % 3), *ak = A + 3 * ((i + 2) % 3);
+    b[3 * i + 0] = (aj[1] * ak[2] - aj[2] * ak[1]) / det;
+    b[3 * i + 1] = (aj[2] * ak[0] - aj[0] * ak[2]) / det;
+    b[3 * i + 2] = (aj[0] * ak[1] - aj[1] * ak[0]) / det;
+  }
+  return 1;
+}
+
+/* The images kept in the extended set: every translate R_a + n1 a1 + n2 a2 +
+ * n3 a3 (n != 0) of a home atom a that lies within r_ext of at least one home
+ * atom.  Rows (a, n1, n2, n3), atom by atom, shifts in lexicographic order;
+ * at most max_out rows are written.  Returns the number of images, -1 for a
+ * singular lattice or a negative radius. */
+long long oracle_periodic_images(int n_atoms, const double *atom_xyz, const double *lattice, double r_ext,
+                                 long long max_out, int *out) {
+  double b[9];
+  if (!reciprocal_rows(lattice, b) || r_ext < 0.0) return -1;
+  double diam = 0.0;
+  for (int a = 0; a < n_atoms; ++a)
+    for (int c = 0; c < n_atoms; ++c) {
+      double d2 = 0.0;
+      for (int k = 0; k < 3; ++k) d2 += (atom_xyz[3 * a + k] - atom_xyz[3 * c + k]) * (atom_xyz[3 * a + k] - atom_xyz[3 * c + k]);
+      if (sqrt(d2) > diam) diam = sqrt(d2);
+    }
+  /* a kept image has |L| <= r_ext + diam, hence |n_i| <= |b_i| (r_ext + diam) */
+  double bmax = 0.0;
+  for (int i = 0; i < 3; ++i) {
+    double nb = sqrt(b[3 * i] * b[3 * i] + b[3 * i + 1] * b[3 * i + 1] + b[3 * i + 2] * b[3 * i + 2]);
+    if (nb > bmax) bmax = nb;
+  }
+  const int m = (int)ceil(bmax * (r_ext + diam)) + 1;
+  long long count = 0;
+  for (int a = 0; a < n_atoms; ++a)
+    for (int n1 = -m; n1 <= m; ++n1)
+      for (int n2 = -m; n2 <= m; ++n2)
+        for (int n3 = -m; n3 <= m; ++n3) {
+          if (n1 == 0 && n2 == 0 && n3 == 0) continue;
+          double x[3];
+          for (int k = 0; k < 3; ++k)
+            x[k] = atom_xyz[3 * a + k] + n1 * lattice[k] + n2 * lattice[3 + k] + n3 * lattice[6 + k];
+          int near = 0;
+          for (int c = 0; c < n_atoms && !near; ++c) {
+            double d2 = 0.0;
+            for (int k = 0; k < 3; ++k) d2 += (x[k] - atom_xyz[3 * c + k]) * (x[k] - atom_xyz[3 * c + k]);
+            near = sqrt(d2) <= r_ext;
+          }
+          if (!near) continue;
+          if (count < max_out) {
+            out[4 * count + 0] = a;
+            out[4 * count + 1] = n1;
+            out[4 * count + 2] = n2;
+            out[4 * count + 3] = n3;
+          }
+          ++count;
+        }
+  return count;
+}
+
+/* Exchange rows of a periodic system (Eq. H-HFX without the -1/2):
+ *   K^G_{mu lambda} = sum_{N,H} sum_{nu,sigma} P^{H-N}_{nu sigma} (mu^0 nu^N | lambda^G sigma^H)
+ * for mu in the home cell and lambda^G in the extended set (home atoms first,
+ * in home order, then the images of oracle_periodic_images in its order);
+ * nu^N and sigma^H run over the extended set.
+ * Real-space density at the Gamma point (Eq. dm with a single k-point):
+ * P^L_{nu sigma} = P_{nu sigma} (the home-cell density) when the atoms of
+ * nu^0 and sigma^L are at most r_P apart, and 0 otherwise.
+ * Screening as in survives(), with the Schwarz bounds and shell maxima of P
+ * over the extended set.  Home shells: grouped by atom in atom order
+ * (shell_atom), coefficients normalised.  ext_out: (n_ext x 4) rows
+ * (home atom, n1, n2, n3), n_ext = n_atoms + the image count; K_rows:
+ * home nbf x extended nbf, row-major.  The sum is taken by brute force over
+ * all ordered shell triples (K, J, L) for every home shell I.
+ * Returns the number of surviving ordered shell quartets, -1 on bad input. */
+long long oracle_K_periodic(int n_shells, const int *shell_atom, const int *l, const int *prim_off,
+                            const double *alpha, const double *coef, const long long *func_off, int n_atoms,
+                            const double *atom_xyz, const double *lattice, double r_ext, double r_P,
+                            const double *P_home, int kernel, double omega, int screen, double tau, int dscreen,
+                            double eps, int nthreads, int *ext_out, double *K_rows) {
+  for (int s = 1; s < n_shells; ++s)
+    if (shell_atom[s] < shell_atom[s - 1]) return -1;
+  const long long n_img = oracle_periodic_images(n_atoms, atom_xyz, lattice, r_ext, 0, NULL);
+  if (n_img < 0) return -1;
+  const int n_ext = n_atoms + (int)n_img;
+  int *img = (int *)malloc(sizeof(int) * 4 * (size_t)(n_img + 1));
+  oracle_periodic_images(n_atoms, atom_xyz, lattice, r_ext, n_img, img);
+  for (int a = 0; a < n_atoms; ++a) {
+    ext_out[4 * a] = a;
+    ext_out[4 * a + 1] = ext_out[4 * a + 2] = ext_out[4 * a + 3] = 0;
+  }
+  memcpy(ext_out + 4 * (size_t)n_atoms, img, sizeof(int) * 4 * (size_t)n_img);
+  free(img);
+
+  /* home atom -> its shells [s0, s1) and functions [f0, f1) */
+  int *as0 = (int *)calloc((size_t)n_atoms + 1, sizeof(int));
+  for (int s = 0; s < n_shells; ++s) as0[shell_atom[s] + 1]++;
+  for (int a = 0; a < n_atoms; ++a) as0[a + 1] += as0[a];
+  const int nbf_home = (int)func_off[n_shells];
+
+  /* extended shells: each extended atom carries its home atom's shells */
+  int ens = 0, enp = 0;
+  for (int X = 0; X < n_ext; ++X) {
+    const int h = ext_out[4 * X];
+    ens += as0[h + 1] - as0[h];
+    enp += prim_off[as0[h + 1]] - prim_off[as0[h]];
+  }
+  double *exyz = (double *)malloc(sizeof(double) * 3 * (size_t)ens);
+  double *axyz = (double *)malloc(sizeof(double) * 3 * (size_t)n_ext);
+  int *el = (int *)malloc(sizeof(int) * (size_t)ens);
+  int *epo = (int *)malloc(sizeof(int) * ((size_t)ens + 1));
+  double *eal = (double *)malloc(sizeof(double) * (size_t)enp);
+  double *eco = (double *)malloc(sizeof(double) * (size_t)enp);
+  long long *efo = (long long *)malloc(sizeof(long long) * ((size_t)ens + 1));
+  int *eatom_f0 = (int *)malloc(sizeof(int) * ((size_t)n_ext + 1));
+  int es = 0;
+  epo[0] = 0;
+  efo[0] = 0;
+  for (int X = 0; X < n_ext; ++X) {
+    const int *e = ext_out + 4 * X;
+    for (int k = 0; k < 3; ++k)
+      axyz[3 * X + k] = atom_xyz[3 * e[0] + k] + e[1] * lattice[k] + e[2] * lattice[3 + k] + e[3] * lattice[6 + k];
+    eatom_f0[X] = (int)efo[es];
+    for (int s = as0[e[0]]; s < as0[e[0] + 1]; ++s, ++es) {
+      for (int k = 0; k < 3; ++k) exyz[3 * es + k] = axyz[3 * X + k];
+      el[es] = l[s];
+      const int np = prim_off[s + 1] - prim_off[s];
+      memcpy(eal + epo[es], alpha + prim_off[s], sizeof(double) * np);
+      memcpy(eco + epo[es], coef + prim_off[s], sizeof(double) * np);
+      epo[es + 1] = epo[es] + np;
+      efo[es + 1] = efo[es] + ncart(l[s]);
+    }
+  }
+  eatom_f0[n_ext] = (int)efo[ens];
+  const long long nbf = efo[ens];
+
+  /* P over the extended set, block by block of atom pairs */
+  double *Pe = (double *)calloc((size_t)(nbf * nbf), sizeof(double));
+  for (int X = 0; X < n_ext; ++X)
+    for (int Y = 0; Y < n_ext; ++Y) {
+      double d2 = 0.0;
+      for (int k = 0; k < 3; ++k) d2 += (axyz[3 * X + k] - axyz[3 * Y + k]) * (axyz[3 * X + k] - axyz[3 * Y + k]);
+      if (sqrt(d2) > r_P) continue;
+      const int hx = ext_out[4 * X], hy = ext_out[4 * Y];
+      const long long fx = func_off[as0[hx]], fy = func_off[as0[hy]];
+      const int nx = eatom_f0[X + 1] - eatom_f0[X], ny = eatom_f0[Y + 1] - eatom_f0[Y];
+      for (int i = 0; i < nx; ++i)
+        for (int j = 0; j < ny; ++j)
+          Pe[(eatom_f0[X] + i) * nbf + eatom_f0[Y] + j] = P_home[(fx + i) * nbf_home + fy + j];
+    }
+
+  basis_t B;
+  fill_basis(&B, ens, exyz, el, epo, eal, eco, efo);
+  double *Q = (double *)calloc((size_t)ens * ens, sizeof(double));
+  double *Pm = (double *)calloc((size_t)ens * ens, sizeof(double));
+  if (screen) oracle_schwarz(ens, exyz, el, epo, eal, eco, efo, kernel, omega, Q);
+  shell_pmax(&B, Pe, Pm);
+  memset(K_rows, 0, sizeof(double) * (size_t)nbf_home * (size_t)nbf);
+  if (nthreads <= 0) nthreads = 1;
+  long long count = 0;
+#pragma omp parallel num_threads(nthreads) reduction(+ : count)
+  {
+    double *Kt = (double *)calloc((size_t)nbf_home * (size_t)nbf, sizeof(double));
+    double g[MAXC * MAXC * MAXC * MAXC];
+#pragma omp for schedule(dynamic, 1) collapse(2)
+    for (int I = 0; I < n_shells; ++I) /* the home shells are the first n_shells extended shells */
+      for (int Ks = 0; Ks < ens; ++Ks)
+        for (int J = 0; J < ens; ++J)
+          for (int Ls = 0; Ls < ens; ++Ls) {
+            if (!survives(ens, Q, Pm, screen, tau, dscreen, eps, I, Ks, J, Ls)) continue;
+            ++count;
+            shell_quartet(&B, I, Ks, J, Ls, kernel, omega, g);
+            const int nI = ncart(el[I]), nK = ncart(el[Ks]), nJ = ncart(el[J]), nL = ncart(el[Ls]);
+            for (int a = 0; a < nI; ++a)
+              for (int k = 0; k < nK; ++k)
+                for (int c = 0; c < nJ; ++c)
+                  for (int d = 0; d < nL; ++d)
+                    Kt[(efo[I] + a) * nbf + efo[J] + c] +=
+                        g[((a * nK + k) * nJ + c) * nL + d] * Pe[(efo[Ks] + k) * nbf + efo[Ls] + d];
+          }
+#pragma omp critical
+    {
+      for (long long x = 0; x < (long long)nbf_home * nbf; ++x) K_rows[x] += Kt[x];
+    }
+    free(Kt);
+  }
+  free(Q); free(Pm); free(Pe); free(as0); free(exyz); free(axyz); free(el); free(epo); free(eal); free(eco);
+  free(efo); free(eatom_f0);
+  return count;
+}
+
 int oracle_max_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();

@@ -52,6 +52,7 @@ class System:
     prim_off: np.ndarray  # (n_shells + 1,) int32 into alpha/coef
     alpha: np.ndarray  # (n_prims,) float64, bohr^-2
     coef: np.ndarray  # (n_prims,) float64, raw
+    lattice: np.ndarray | None = None  # (3, 3) lattice vectors as rows (bohr); None = molecule
 
     @property
     def n_atoms(self) -> int:
@@ -121,8 +122,8 @@ def _draw_shells(rng, elements, recipe, nprim, alpha_lo=0.1, alpha_hi=50.0):
             np.array(coef, dtype=np.float64))
 
 
-def _make(name, elements, xyz, recipe, nprim, rng) -> System:
-    sa, sl, off, a, c = _draw_shells(rng, elements, recipe, nprim)
+def _make(name, elements, xyz, recipe, nprim, rng, alpha_range=(0.1, 50.0)) -> System:
+    sa, sl, off, a, c = _draw_shells(rng, elements, recipe, nprim, *alpha_range)
     return System(name=name, atom_Z=np.array([ZNUC[e] for e in elements], dtype=np.int32),
                   atom_xyz=np.ascontiguousarray(xyz, dtype=np.float64), shell_atom=sa,
                   shell_l=sl, prim_off=off, alpha=a, coef=c)
@@ -190,6 +191,87 @@ def ch_slab(n_atoms: int, config_idx: int = 4, sub: int = 0, spacing: float = 4.
     xyz += rng.uniform(-0.1, 0.1, size=xyz.shape)
     el = ["C" if i % 2 == 0 else "H" for i in range(n_atoms)]
     return _make(f"ch_slab_{n_atoms}", el, xyz, CH_RECIPE, 4, rng)
+
+
+def si_supercell(ncell: int = 3, config_idx: int = 4, sub: int = 0, a: float = 10.26, nprim: int = 4) -> System:
+    """Silicon in the diamond structure: ncell^3 conventional cubic cells of side
+    ``a`` bohr (8 atoms each; 3x3x3 = 216 atoms), atoms on the exact lattice
+    sites (no jitter), 3s+3p+1d shells with ``nprim`` primitives drawn per atom
+    like the other recipes.  ``lattice`` is the supercell (ncell a on each axis)."""
+    rng = _rng(config_idx, 4000 + sub)
+    fcc = np.array([[0, 0, 0], [0, 0.5, 0.5], [0.5, 0, 0.5], [0.5, 0.5, 0]])
+    basis = np.vstack([fcc, fcc + 0.25])
+    cells = np.array([[i, j, k] for i in range(ncell) for j in range(ncell) for k in range(ncell)], dtype=np.float64)
+    xyz = a * (cells[:, None, :] + basis[None, :, :]).reshape(-1, 3)
+    s = _make(f"si_{len(xyz)}", ["Si"] * len(xyz), xyz, SI_RECIPE, nprim, rng)
+    s.lattice = np.eye(3) * (ncell * a)
+    return s
+
+
+#: a light shell recipe (one s and one p shell per atom) for small periodic cells
+LIGHT_RECIPE = {"C": [0, 1], "H": [0, 1], "Si": [0, 1, 2]}
+
+
+def periodic_cell(n_atoms: int, lattice, config_idx: int = 4, sub: int = 0, min_dist: float = 2.0,
+                  recipe: dict | None = None, nprim: int = 2, alpha_range=(0.1, 50.0)) -> System:
+    """A small periodic cell for tests: ``n_atoms`` atoms (C, H alternating)
+    at uniform random fractional coordinates, at least ``min_dist`` bohr from
+    each other and from each other's images; shells from ``recipe``
+    (default LIGHT_RECIPE), exponents log-uniform in ``alpha_range``."""
+    rng = _rng(config_idx, 6000 + sub)
+    A = np.asarray(lattice, dtype=np.float64).reshape(3, 3)
+    shifts = np.array([[i, j, k] for i in (-1, 0, 1) for j in (-1, 0, 1) for k in (-1, 0, 1)], dtype=np.float64) @ A
+    if np.linalg.norm(shifts[np.any(shifts != 0, axis=1)], axis=1).min() < min_dist:
+        raise ValueError("lattice vectors shorter than min_dist")
+    pts = np.zeros((0, 3))
+    tries = 0
+    while pts.shape[0] < n_atoms:
+        tries += 1
+        if tries > 100_000:
+            raise RuntimeError("cell too small for the requested atoms")
+        cand = rng.uniform(0.0, 1.0, size=3) @ A
+        if pts.shape[0]:
+            d = np.linalg.norm(pts[:, None, :] + shifts[None, :, :] - cand[None, None, :], axis=-1)
+            if d.min() < min_dist:
+                continue
+        pts = np.vstack([pts, cand])
+    el = ["C" if i % 2 == 0 else "H" for i in range(n_atoms)]
+    s = _make(f"cell_{n_atoms}", el, pts, recipe or LIGHT_RECIPE, nprim, rng, alpha_range)
+    s.lattice = A.copy()
+    return s
+
+
+def min_image_distances(sys: System) -> np.ndarray:
+    """(n_atoms, n_atoms) distance from atom a to the nearest periodic image of
+    atom b (plain distances for a molecule)."""
+    if sys.lattice is None:
+        return atom_distances(sys)
+    A = np.asarray(sys.lattice, dtype=np.float64)
+    x = sys.atom_xyz
+    diam = atom_distances(sys).max()
+    # a minimum image is no farther than the direct distance, so its lattice
+    # vector L has |L| <= 2 * diam and |n_i| <= 2 * diam / h_i (h_i: cell heights)
+    h = abs(np.linalg.det(A)) / np.linalg.norm(np.cross(A[[1, 2, 0]], A[[2, 0, 1]]), axis=1)
+    m = np.ceil(2.0 * diam / h).astype(int)
+    best = np.full((sys.n_atoms, sys.n_atoms), np.inf)
+    for n1 in range(-m[0], m[0] + 1):
+        for n2 in range(-m[1], m[1] + 1):
+            for n3 in range(-m[2], m[2] + 1):
+                L = np.array([n1, n2, n3], dtype=np.float64) @ A
+                d = np.linalg.norm(x[:, None, :] - x[None, :, :] - L[None, None, :], axis=-1)
+                np.minimum(best, d, out=best)
+    return best
+
+
+def periodic_density_matrix(sys: System, config_idx: int = 4, cutoff: float | None = 14.0, sub: int = 0,
+                            n_occ: int | None = None) -> np.ndarray:
+    """Home-cell density matrix of a periodic system: P = C C^T as in
+    ``density_matrix``, with every atom-pair block whose minimum-image
+    distance exceeds ``cutoff`` set to zero."""
+    P = density_matrix(sys, config_idx, n_occ=n_occ, sub=sub)
+    if cutoff is not None:
+        P = P * expand_atom_mask(sys, min_image_distances(sys) <= cutoff)
+    return np.ascontiguousarray(P)
 
 
 def atom_distances(sys: System) -> np.ndarray:
