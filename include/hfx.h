@@ -246,6 +246,43 @@ hfx_status hfx_pack_dense_host(const hfx_shell_desc* shells, int n_shells, const
  * primitive pairs during setup, plus what stays resident); -1 on bad input. */
 long long hfx_setup_bytes_estimate(const hfx_shell_desc* shells, int n_shells, const hfx_pattern* pattern);
 
+/* ---- Periodic systems (Sec. 2, Eq. H-HFX) ------------------------------
+ * The periodic exchange K^G_{mu lambda} = sum_{N,H} sum_{nu sigma}
+ * P^{H-N}_{nu sigma} (mu^0 nu^N | lambda^G sigma^H) (mu in the home cell; N, G,
+ * H cells of the auxiliary supercell) is the molecular exchange of an
+ * extended atom set: the home atoms (extended atoms 0..n_home-1, in home
+ * order) followed by the images, each image carrying its home atom's shells
+ * at the translated centre.  Build it with hfx_create_basis /
+ * hfx_build_quartets / hfx_build_K on the extended shells and pattern; the
+ * rows of the home atoms are K^G.  The exchange energy per cell is
+ * -1/2 sum over the home atoms' rows of P K: with the home atoms first, those
+ * rows are a prefix of the value arrays (hfx_exchange_energy_noalloc with
+ * that prefix length). */
+
+/* Image table: every translate R_a + n1 a1 + n2 a2 + n3 a3 (n != 0) of a home
+ * atom a lying within r_ext (bohr) of at least one home atom.
+ * atom_xyz: host, n_atoms x 3; lattice: host, 3 x 3, lattice vectors a_i as
+ * rows (bohr).  Images are ordered by shift (n1, n2, n3 lexicographic) and
+ * then by atom.  The first min(count, max_images) are written to image_atom
+ * (home atom) and image_shift (n1, n2, n3 per image); call with
+ * max_images = 0 to size the arrays.  Returns the number of images, or -1
+ * (message in hfx_last_error) for NULL input, a singular lattice, a negative
+ * r_ext or a search beyond 1000 cells per direction. */
+long long hfx_periodic_images(const double* atom_xyz, int n_atoms, const double* lattice, double r_ext,
+                              long long max_images, int* image_atom, int* image_shift);
+
+/* Real-space density of the extended set (Eq. dm at the Gamma point): for
+ * every block (X, Y) of ext_pattern (CSR over the extended atoms, normally
+ * the pairs within the density cutoff), the home-cell block
+ * P_home(ext_home[X], ext_home[Y]) is written to val in the pattern's value
+ * layout (blocks in CSR order, row-major inside a block).
+ * shells: the n_shells home shells (atom < n_home_atoms, grouped by atom);
+ * ext_home: host, ext_pattern->n_atoms home-atom indices; P_home: host, dense
+ * home nbf x nbf row-major; val: host, hfx_pattern_value_count of the
+ * extended shells and ext_pattern. */
+hfx_status hfx_periodic_pack_host(const hfx_shell_desc* shells, int n_shells, int n_home_atoms, const int* ext_home,
+                                  const hfx_pattern* ext_pattern, const double* P_home, double* val);
+
 /* ---- Serving: continuous batching of independent requests -------------
  * No counterpart in the paper, whose runs build one system's K once per SCF
  * iteration; a server interleaves many such SCF-like runs on one GPU.

@@ -33,7 +33,7 @@ def _sources():
     spec.loader.exec_module(gen)
     gen.generate(GEN)
     tus = sorted(os.path.join(GEN, f) for f in os.listdir(GEN) if f.endswith(".cu"))
-    return [os.path.join(CSRC, f) for f in ("hfx_core.cu", "hfx_noalloc.cu", "hfx_server.cu")] + tus
+    return [os.path.join(CSRC, f) for f in ("hfx_core.cu", "hfx_noalloc.cu", "hfx_server.cu", "hfx_periodic.cu")] + tus
 
 
 def _digest(src, extra):

@@ -1,0 +1,145 @@
+// hfx_periodic.cu -- periodic systems as an extended atom set (host code).
+//
+// Sec. 2, Eq. H-HFX: for a periodic system the exchange matrix is
+//   K^G_{mu lambda} = sum_{N,H} sum_{nu sigma} P^{H-N}_{nu sigma} (mu^0 nu^N | lambda^G sigma^H),
+// mu in the home cell and nu, lambda, sigma in the cells N, G, H of the
+// auxiliary supercell.  Here the supercell is an extended atom set: the home
+// atoms followed by the images (translates of home atoms by lattice vectors)
+// that lie within r_ext of some home atom.  Each image carries its home atom's
+// shells.  The sum above is then the molecular exchange of the extended set
+// (the row of mu^0 and the column of lambda^G), so the molecular path builds
+// it unchanged; these functions produce the image table and lay the
+// real-space density P^{H-N} onto the extended pattern.
+//
+// Real-space density at the Gamma point (Eq. dm with one k-point): the
+// caller's pattern over the extended atoms decides where P^{H-N} is nonzero
+// (normally the atom pairs within a distance cutoff).  Every block (X, Y) of
+// that pattern receives the home-cell density block of the home atoms of X
+// and Y.
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "hfx.h"
+
+void hfx_set_last_error(const std::string& m);
+
+namespace {
+
+long long periodic_fail(const std::string& m) {
+  hfx_set_last_error(m);
+  return -1;
+}
+
+hfx_status status_fail(hfx_status s, const std::string& m) {
+  hfx_set_last_error(m);
+  return s;
+}
+
+int n_cart(int l) { return (l + 1) * (l + 2) / 2; }
+
+}  // namespace
+
+extern "C" {
+
+long long hfx_periodic_images(const double* atom_xyz, int n_atoms, const double* lattice, double r_ext,
+                              long long max_images, int* image_atom, int* image_shift) {
+  if (!atom_xyz || !lattice || n_atoms <= 0) return periodic_fail("hfx_periodic_images: NULL argument or no atoms");
+  if (!(r_ext >= 0.0) || !std::isfinite(r_ext)) return periodic_fail("hfx_periodic_images: r_ext must be >= 0");
+  if (max_images > 0 && (!image_atom || !image_shift))
+    return periodic_fail("hfx_periodic_images: NULL output arrays");
+  const double* a = lattice;
+  const double det = a[0] * (a[4] * a[8] - a[5] * a[7]) - a[1] * (a[3] * a[8] - a[5] * a[6]) +
+                     a[2] * (a[3] * a[7] - a[4] * a[6]);
+  if (!(std::fabs(det) > 0.0) || !std::isfinite(det)) return periodic_fail("hfx_periodic_images: singular lattice");
+  // |n_i| = |L . b_i| <= |L| |b_i| with b_i = (a_j x a_k) / det; a kept image
+  // has |L| <= r_ext + (largest distance between home atoms)
+  double diam2 = 0.0;
+  for (int p = 0; p < n_atoms; ++p)
+    for (int q = p + 1; q < n_atoms; ++q) {
+      double d2 = 0.0;
+      for (int k = 0; k < 3; ++k) d2 += (atom_xyz[3 * p + k] - atom_xyz[3 * q + k]) * (atom_xyz[3 * p + k] - atom_xyz[3 * q + k]);
+      diam2 = std::max(diam2, d2);
+    }
+  const double reach = r_ext + std::sqrt(diam2);
+  int m[3];
+  long long n_shift = 1;
+  for (int i = 0; i < 3; ++i) {
+    const double* aj = a + 3 * ((i + 1) % 3);
+    const double* ak = a + 3 * ((i + 2) % 3);
+    const double c0 = aj[1] * ak[2] - aj[2] * ak[1], c1 = aj[2] * ak[0] - aj[0] * ak[2],
+                 c2 = aj[0] * ak[1] - aj[1] * ak[0];
+    const double bnorm = std::sqrt(c0 * c0 + c1 * c1 + c2 * c2) / std::fabs(det);
+    const double mi = std::floor(reach * bnorm) + 1.0;
+    if (mi > 1000.0) return periodic_fail("hfx_periodic_images: r_ext too large for this lattice");
+    m[i] = (int)mi;
+    n_shift *= 2LL * m[i] + 1;
+  }
+  if (n_shift * n_atoms * (long long)n_atoms > 4000000000LL)
+    return periodic_fail("hfx_periodic_images: search too large (r_ext or atom count)");
+  // shift-major order: (n1, n2, n3) lexicographic, then atoms ascending
+  long long count = 0;
+  for (int n1 = -m[0]; n1 <= m[0]; ++n1)
+    for (int n2 = -m[1]; n2 <= m[1]; ++n2)
+      for (int n3 = -m[2]; n3 <= m[2]; ++n3) {
+        if (n1 == 0 && n2 == 0 && n3 == 0) continue;
+        for (int p = 0; p < n_atoms; ++p) {
+          double x[3];
+          for (int k = 0; k < 3; ++k)
+            x[k] = atom_xyz[3 * p + k] + n1 * lattice[k] + n2 * lattice[3 + k] + n3 * lattice[6 + k];
+          bool near = false;
+          for (int q = 0; q < n_atoms && !near; ++q) {
+            double d2 = 0.0;
+            for (int k = 0; k < 3; ++k) d2 += (x[k] - atom_xyz[3 * q + k]) * (x[k] - atom_xyz[3 * q + k]);
+            near = std::sqrt(d2) <= r_ext;
+          }
+          if (!near) continue;
+          if (count < max_images) {
+            image_atom[count] = p;
+            image_shift[3 * count + 0] = n1;
+            image_shift[3 * count + 1] = n2;
+            image_shift[3 * count + 2] = n3;
+          }
+          ++count;
+        }
+      }
+  return count;
+}
+
+hfx_status hfx_periodic_pack_host(const hfx_shell_desc* shells, int n_shells, int n_home_atoms, const int* ext_home,
+                                  const hfx_pattern* ext_pattern, const double* P_home, double* val) {
+  if (!shells || n_shells <= 0 || n_home_atoms <= 0 || !ext_home || !ext_pattern || !ext_pattern->row_ptr ||
+      !ext_pattern->col || ext_pattern->n_atoms <= 0 || !P_home || !val)
+    return status_fail(HFX_ERR_INVALID_ARG, "hfx_periodic_pack_host: NULL or empty argument");
+  // home atom -> first function and function count (shells grouped by atom)
+  std::vector<long long> nf((size_t)n_home_atoms, 0), f0((size_t)n_home_atoms + 1, 0);
+  for (int s = 0; s < n_shells; ++s) {
+    const int at = shells[s].atom, l = shells[s].l;
+    if (at < 0 || at >= n_home_atoms || l < 0 || l > 2 || (s > 0 && at < shells[s - 1].atom))
+      return status_fail(HFX_ERR_INVALID_ARG, "hfx_periodic_pack_host: shells not grouped by home atom");
+    nf[(size_t)at] += n_cart(l);
+  }
+  for (int at = 0; at < n_home_atoms; ++at) f0[(size_t)at + 1] = f0[(size_t)at] + nf[(size_t)at];
+  const long long nbf = f0[(size_t)n_home_atoms];
+  const int n_ext = ext_pattern->n_atoms;
+  for (int X = 0; X < n_ext; ++X)
+    if (ext_home[X] < 0 || ext_home[X] >= n_home_atoms)
+      return status_fail(HFX_ERR_INVALID_ARG, "hfx_periodic_pack_host: ext_home out of range");
+  long long v = 0;
+  for (int X = 0; X < n_ext; ++X) {
+    if (ext_pattern->row_ptr[X] > ext_pattern->row_ptr[X + 1])
+      return status_fail(HFX_ERR_INVALID_ARG, "hfx_periodic_pack_host: row_ptr not ascending");
+    const int hx = ext_home[X];
+    for (int k = ext_pattern->row_ptr[X]; k < ext_pattern->row_ptr[X + 1]; ++k) {
+      const int Y = ext_pattern->col[k];
+      if (Y < 0 || Y >= n_ext) return status_fail(HFX_ERR_INVALID_ARG, "hfx_periodic_pack_host: column out of range");
+      const int hy = ext_home[Y];
+      for (long long i = 0; i < nf[(size_t)hx]; ++i)
+        for (long long j = 0; j < nf[(size_t)hy]; ++j) val[v++] = P_home[(f0[(size_t)hx] + i) * nbf + f0[(size_t)hy] + j];
+    }
+  }
+  return HFX_OK;
+}
+
+}  // extern "C"

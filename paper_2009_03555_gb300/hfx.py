@@ -81,7 +81,7 @@ EXPORTED = ["hfx_create_basis", "hfx_build_quartets", "hfx_value_count", "hfx_bu
             "hfx_batch_destroy", "hfx_quartets_device_bytes", "hfx_basis_device_bytes", "hfx_pattern_value_count",
             "hfx_pack_dense_host", "hfx_setup_bytes_estimate", "hfx_server_create", "hfx_server_submit",
             "hfx_server_step", "hfx_server_poll", "hfx_server_release", "hfx_server_get_info", "hfx_server_destroy",
-            "hfx_server_cancel", "hfx_server_inject_setup_failure",
+            "hfx_server_cancel", "hfx_server_inject_setup_failure", "hfx_periodic_images", "hfx_periodic_pack_host",
             "hfx_destroy_basis", "hfx_destroy_quartets", "hfx_last_error"]
 
 _lib = None
@@ -160,9 +160,11 @@ def load(path: str = LIB_PATH):
     lib.hfx_server_get_info.argtypes = [V, ctypes.POINTER(ServerInfo)]
     lib.hfx_server_destroy.argtypes = [V]
     lib.hfx_server_destroy.restype = None
+    lib.hfx_periodic_images.argtypes = [V, I, V, D, LL, V, V]
+    lib.hfx_periodic_pack_host.argtypes = [ctypes.POINTER(ShellDesc), I, I, V, ctypes.POINTER(Pattern), V, V]
     for name in EXPORTED:
         if name in ("hfx_quartets_device_bytes", "hfx_basis_device_bytes", "hfx_pattern_value_count",
-                    "hfx_setup_bytes_estimate"):
+                    "hfx_setup_bytes_estimate", "hfx_periodic_images"):
             getattr(lib, name).restype = LL
         elif name not in ("hfx_value_count", "hfx_destroy_basis", "hfx_destroy_quartets", "hfx_last_error",
                           "hfx_batch_destroy", "hfx_server_destroy"):
@@ -467,6 +469,91 @@ class _SystemInput:
 
     def setup_bytes_estimate(self) -> int:
         return int(load().hfx_setup_bytes_estimate(self.descs, self.n_shells, ctypes.byref(self.pattern)))
+
+
+def hfx_periodic_images(atom_xyz, lattice, r_ext):
+    """Image table of a periodic cell: (image_atom, image_shift), the home atom
+    and the lattice shift (n1, n2, n3) of every image within ``r_ext`` of a
+    home atom, ordered by shift and then atom (see hfx.h)."""
+    lib = load()
+    xyz = np.ascontiguousarray(atom_xyz, dtype=np.float64).reshape(-1, 3)
+    A = np.ascontiguousarray(lattice, dtype=np.float64).reshape(3, 3)
+    n = lib.hfx_periodic_images(_ptr(xyz), int(xyz.shape[0]), _ptr(A), float(r_ext), 0, None, None)
+    if n < 0:
+        raise HFXError(1, lib.hfx_last_error().decode(errors="replace"))
+    atom = np.zeros(max(n, 1), dtype=np.int32)
+    shift = np.zeros((max(n, 1), 3), dtype=np.int32)
+    m = lib.hfx_periodic_images(_ptr(xyz), int(xyz.shape[0]), _ptr(A), float(r_ext), int(n), _ptr(atom),
+                                _ptr(shift))
+    assert m == n
+    return atom[:n], shift[:n]
+
+
+class ExtendedSystem:
+    """Flat shell arrays of a periodic cell's extended atom set: the home atoms,
+    then the images, each with its home atom's shells at the translated centre."""
+
+    def __init__(self, home, ext_home, ext_xyz):
+        sa = np.asarray(home.shell_atom)
+        s0 = np.searchsorted(sa, np.arange(home.n_atoms + 1))  # home atom -> its shell range
+        src = np.concatenate([np.arange(s0[h], s0[h + 1]) for h in ext_home])
+        self.atom_xyz = np.ascontiguousarray(ext_xyz, dtype=np.float64)
+        self.atom_Z = np.asarray(home.atom_Z)[ext_home]
+        self.shell_atom = np.repeat(np.arange(len(ext_home), dtype=np.int32), np.diff(s0)[ext_home])
+        self.shell_l = np.asarray(home.shell_l, dtype=np.int32)[src]
+        po = np.asarray(home.prim_off)
+        n_p = (po[1:] - po[:-1])[src]
+        self.prim_off = np.concatenate([[0], np.cumsum(n_p)]).astype(np.int32)
+        take = np.concatenate([np.arange(po[S], po[S + 1]) for S in src])
+        self.alpha = np.asarray(home.alpha, dtype=np.float64)[take]
+        self.coef = np.asarray(home.coef, dtype=np.float64)[take]
+        nf = (self.shell_l + 1) * (self.shell_l + 2) // 2
+        self.func_off = np.concatenate([[0], np.cumsum(nf)]).astype(np.int64)
+        af = np.zeros(len(ext_home) + 1, dtype=np.int64)
+        np.add.at(af, self.shell_atom + 1, nf)
+        self.atom_func_off = np.cumsum(af)
+        self.n_atoms, self.n_shells, self.n_bf = len(ext_home), len(self.shell_l), int(self.func_off[-1])
+
+
+class Periodic:
+    """A periodic system handed to the molecular path as its extended atom set
+    (Sec. 2, Eq. H-HFX; see the periodic section of hfx.h).
+
+    ``system``: the home cell (flat shell arrays, shells grouped by atom);
+    ``lattice``: 3 x 3 lattice vectors as rows (bohr).  Images within ``r_ext``
+    of a home atom join the set; the density pattern is every pair of extended
+    atoms at most ``r_P`` apart.  ``system`` (extended), ``mask`` and
+    ``pack`` feed ``Basis``/``Quartets``; the first ``n_home_bf`` rows of the
+    extended K are K^G, and the first ``n_home_values`` values are the home
+    rows (the per-cell exchange energy)."""
+
+    def __init__(self, system, lattice, r_ext=10.0, r_P=14.0):
+        self.home = system
+        self.lattice = np.ascontiguousarray(lattice, dtype=np.float64).reshape(3, 3)
+        n_home = int(system.n_atoms)
+        atom, shift = hfx_periodic_images(system.atom_xyz, self.lattice, r_ext)
+        self.ext_home = np.concatenate([np.arange(n_home), atom]).astype(np.int32)
+        self.ext_shift = np.vstack([np.zeros((n_home, 3), dtype=np.int32), shift]).astype(np.int32)
+        ext_xyz = np.asarray(system.atom_xyz, dtype=np.float64)[self.ext_home] + self.ext_shift @ self.lattice
+        self.system = ExtendedSystem(system, self.ext_home, ext_xyz)
+        d = np.linalg.norm(ext_xyz[:, None, :] - ext_xyz[None, :, :], axis=-1)
+        self.mask = d <= r_P
+        self._inp = _SystemInput(self.system, self.mask)
+        self._home_descs, self._home_keep = shell_descs(system.shell_l, system.shell_atom, system.prim_off,
+                                                        system.alpha, system.coef)
+        self.n_values = self._inp.value_count()
+        nfa = np.diff(self.system.atom_func_off)
+        self.n_home_bf = int(nfa[:n_home].sum())
+        self.n_home_values = int(sum(nfa[X] * nfa[self.mask[X]].sum() for X in range(n_home)))
+
+    def pack(self, P_home) -> np.ndarray:
+        """Values of the real-space density on the extended pattern (host)."""
+        P = np.ascontiguousarray(P_home, dtype=np.float64)
+        out = np.empty(self.n_values)
+        _check(load().hfx_periodic_pack_host(self._home_descs, len(self.home.shell_l), int(self.home.n_atoms),
+                                             _ptr(self.ext_home), ctypes.byref(self._inp.pattern), _ptr(P),
+                                             _ptr(out)))
+        return out
 
 
 class Server:
