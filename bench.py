@@ -137,6 +137,11 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def _json_num(x):
+    """A float for the JSON line; null for an infinite bound (no FP64 promotion)."""
+    return None if x is None or math.isinf(x) else x
+
+
 def max_over_ranks(ms, world, device):
     """The slowest rank's step time (every rank gets it); world 1: unchanged."""
     if world <= 1:
@@ -276,7 +281,7 @@ def run_ours(args, rank, world):
                                   + (f" in classes of total l >= {args.promote_min_l}" if args.promote_min_l else "")
                                   if prec == hfx.HFX_PREC_MIXED and math.isfinite(args.promote) else ""),
                    "atoms": args.atoms, "n_bf": int(s.n_bf), "precision": args.precision,
-                   "fp64_promote_bound": args.promote, "promote_min_l": args.promote_min_l,
+                   "fp64_promote_bound": _json_num(args.promote), "promote_min_l": args.promote_min_l,
                    "n_block": args.n_block, "prim_cutoff": args.prim_cutoff,
                    "l2": "flushed (256 MB write) between timed steps", "parallelism": f"replicas x{world}"},
         "quartets_per_build": n_q, "prim_quartets_per_build": n_pq,
@@ -496,6 +501,64 @@ def run_batch(args):
             "max_dE_tuned_vs_default": float(np.abs(E_tuned - E_batch).max())}
 
 
+def run_periodic(args):
+    """--periodic: the periodic Si workload (diamond supercell of
+    --periodic-cells^3 conventional cells, 216 home atoms by default; images
+    within --periodic-rext bohr of a home atom; density pairs within 14 bohr)
+    built as its extended atom set; builds/s of the extended build and the
+    exchange energy per cell (the home rows)."""
+    import torch
+    from paper_2009_03555_gb300 import hfx
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dev = torch.device("cuda")
+    s = synth.si_supercell(args.periodic_cells)
+    P = synth.periodic_density_matrix(s, cutoff=14.0)
+    per = hfx.Periodic(s, s.lattice, r_ext=args.periodic_rext, r_P=14.0)
+    prec = hfx.HFX_PREC_MIXED if args.precision == "mixed" else hfx.HFX_PREC_FP64
+    promote = args.promote if prec == hfx.HFX_PREC_MIXED else math.inf
+    opts = hfx.make_opts(kernel=hfx.HFX_KERNEL_ERFC, omega=0.11, screen=True, tau=1e-8, density_screen=True,
+                         eps=1e-8, prim_cutoff=args.prim_cutoff, precision=prec, fp64_promote_bound=promote,
+                         n_block=args.n_block, promote_min_l=args.promote_min_l)
+    t0 = time.perf_counter()
+    q = hfx.Quartets(hfx.Basis(per.system), opts, per.mask)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    Pv = torch.from_numpy(per.pack(P)).to(dev)
+    Kv = torch.empty_like(Pv)
+    E = torch.zeros(1, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        q.build_K(Pv, Kv)
+    torch.cuda.synchronize()
+    clk = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        q.build_K(Pv, Kv)
+    e1.record(stream)
+    e1.synchronize()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    hfx.hfx_exchange_energy_noalloc(Pv, Kv, per.n_home_values, E)  # home rows: the value prefix
+    st = q.stats()
+    n_q = sum(st.n_quartets_computed)
+    return {"metric": "hfx_periodic_builds_per_s", "value": 1000.0 / ms, "unit": "builds/s", "n_gpus": 1,
+            "higher_is_better": True, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "dtype": "f32+f64" if prec == hfx.HFX_PREC_MIXED else "f64", "data": "synthetic",
+            "config": {"workload": f"periodic Si, diamond {args.periodic_cells}^3 supercell ({s.n_atoms} atoms, "
+                                   f"3s3p1d, 4 primitives), images within {args.periodic_rext} bohr, P pairs within "
+                                   f"14 bohr, HSE erfc w=0.11, Schwarz 1e-8 + density screening, {args.precision}",
+                       "home_atoms": s.n_atoms, "extended_atoms": int(per.system.n_atoms),
+                       "extended_shells": int(per.system.n_shells), "extended_functions": int(per.system.n_bf),
+                       "values": int(per.n_values), "precision": args.precision,
+                       "fp64_promote_bound": _json_num(promote), "promote_min_l": args.promote_min_l},
+            "E_x_per_cell": float(E.item()), "quartets_per_build": int(n_q),
+            "prim_quartets_per_build": int(sum(st.n_prim_quartets_pass[0]) + sum(st.n_prim_quartets_pass[1])),
+            "setup_s": setup_s, "clocks": clocks}
+
+
 def run_precision_check(args):
     """--mixed-vs-fp64: the same build in FP64 and in mixed precision (same
     screening and primitive cutoff), the mixed one for every FP64-promotion
@@ -538,7 +601,7 @@ def run_precision_check(args):
         b, _, ml = item.partition(":")
         b, ml = float(b), int(ml or 0)
         E, K, dt, frac = one(hfx.HFX_PREC_MIXED, b, ml)
-        rows.append({"promote": b, "promote_min_l": ml, "E_x": E, "abs_dE_x": abs(E - E64),
+        rows.append({"promote": _json_num(b), "promote_min_l": ml, "E_x": E, "abs_dE_x": abs(E - E64),
                      "max_abs_dK": float(np.abs(K - K64).max()) if K64 is not None else None,
                      "s": dt, "fp64_quartet_share": frac})
     return {"check": "mixed_vs_fp64", "atoms": args.atoms, "prim_cutoff": args.prim_cutoff, "E_x_fp64": E64,
@@ -573,11 +636,17 @@ def main():
     ap.add_argument("--batch", action="store_true", help="many small systems per build (batched vs sequential)")
     ap.add_argument("--batch-systems", type=int, default=64)
     ap.add_argument("--batch-atoms", default="8,24", help="cluster sizes (atoms), min,max")
+    ap.add_argument("--periodic", action="store_true", help="periodic Si supercell built as its extended atom set")
+    ap.add_argument("--periodic-cells", type=int, default=3, help="conventional cells per axis of the Si supercell")
+    ap.add_argument("--periodic-rext", type=float, default=10.0, help="image radius (bohr)")
     ap.add_argument("--mixed-vs-fp64", action="store_true", help="precision check: one mixed and one FP64 build")
     ap.add_argument("--promote-sweep", default="inf,1e-2,1e-3,1e-4", help="FP64-promotion bounds for the check")
     ap.add_argument("--fp64-energy", type=float, default=None,
                     help="precision check: FP64 E_x of an earlier run of the same workload instead of a new FP64 build")
     args = ap.parse_args()
+    if args.periodic:
+        print(json.dumps(run_periodic(args)), flush=True)
+        return 0
     if args.mixed_vs_fp64:
         print(json.dumps(run_precision_check(args)), flush=True)
         return 0
