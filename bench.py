@@ -37,10 +37,10 @@ import synth  # noqa: E402
 # `traffic` scales it to the timed launch; a kernel changed since its capture
 # has no entry (traffic null).
 DRAM_BYTES_PER_PRIM_QUARTET = {
-    # profiles/k_build_K_split_Cls2221_float_ch50.md: 42.0 MB for 132 623 015 primitive quartets
-    "k_build_K_split<Cls2221, float>": 42.009856e6 / 132623015,
-    # profiles/k_build_K_split_Cls2222_double_ch50.md: 119.5 GB for 9 450 274 primitive quartets
-    "k_build_K_split<Cls2222, double>": (3.622961e9 + 115.877184e9) / 9450274,
+    # The captures in profiles/ (k_build_K_split<Cls2221, float>: 0.317 B,
+    # k_build_K_split<Cls2222, double>: 12.6 KB per primitive quartet) predate
+    # the grouped target order of the split recursion, so no kernel has a
+    # current entry.
 }
 
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 80.5: 128 FP32 FMA/clk/SM at the 2070 MHz max clock

@@ -39,7 +39,8 @@ def _sources():
 def _digest(src, extra):
     h = hashlib.sha256()
     h.update(" ".join(FLAGS + extra).encode())
-    h.update(os.environ.get("HFX_COOP_MIN_ACC", "").encode())  # generator switch
+    h.update(os.environ.get("HFX_COOP_MIN_ACC", "").encode())  # generator switches
+    h.update(os.environ.get("HFX_VRR_ORDER", "").encode())
     own = [os.path.join(GEN, os.path.basename(src).replace("tu_", "cls_").replace(".cu", ".cuh"))]
     own = [p for p in own if os.path.exists(p)]
     if os.path.basename(src) == "hfx_core.cu":

@@ -5,7 +5,7 @@ The per-class headers the generator writes hold the code the kernels run:
 `vrr_split` (the same targets in 32-target chunks, each handed to the warp
 reduce-scatter, with the permutation back to accumulator order) and `hrr`
 (horizontal recursion to the Cartesian integrals).  Here every class is
-generated with split code, compiled with g++ behind a small host shim (the
+generated with split code (in both target orders of the split recursion), compiled with g++ behind a small host shim (the
 warp reduce-scatter replaced by a recorder of each chunk's 32 values) and run
 on random G_m and geometry; the results must equal the Obara-Saika and
 Head-Gordon-Pople recursions written out in Python (along the other axis where
@@ -53,13 +53,14 @@ def _gen_module():
     return g
 
 
-@pytest.fixture(scope="module")
-def built(tmp_path_factory):
+@pytest.fixture(scope="module", params=["grouped", "greedy"])
+def built(request, tmp_path_factory):
     if shutil.which("g++") is None:
         pytest.skip("g++ not available")
     g = _gen_module()
     g.SPLIT_MIN_ACC = 1        # emit split code for every class
     g.COOP_MIN_ACC = 10 ** 9
+    g.VRR_ORDER = request.param  # both target orders of the split recursion
     d = tmp_path_factory.mktemp("gen_host")
     g.generate(str(d))
     (d / "eri_common.cuh").write_text(SHIM)
