@@ -761,7 +761,21 @@ struct SplitShape {
 template <class C, typename R>
 struct SplitLayout {
   using T = typename C::Coop;
+#ifdef HFX_SPLIT_SMEM_ACC
+  // Opt-in build (-DHFX_SPLIT_SMEM_ACC): the chunk accumulators and their
+  // compensations live in shared memory instead of registers, lane-major with
+  // an odd stride (no bank conflicts).  They sit at the top of the HRR
+  // workspace when they fit above its NACC accumulator slots (the workspace is
+  // idle until the epilogue, which copies them down before the recursion
+  // writes there), otherwise after the P blocks.
+  static constexpr int ACC_STRIDE = C::NCHUNK | 1;
+  static constexpr int ACC_WORDS = 2 * 32 * ACC_STRIDE;
+  static constexpr bool ACC_IN_WS = ACC_WORDS <= T::HRR_SLOTS - C::NACC;
+  static constexpr int PER_WARP = T::HRR_SLOTS + 160 + (ACC_IN_WS ? 0 : ACC_WORDS);
+  __device__ static R* acc_base(R* ws) { return ACC_IN_WS ? ws + (T::HRR_SLOTS - ACC_WORDS) : ws + T::HRR_SLOTS + 160; }
+#else
   static constexpr int PER_WARP = T::HRR_SLOTS + 160;  // HRR workspace + four P blocks
+#endif
   static constexpr size_t bytes() { return (size_t)SplitShape<C>::WARPS * PER_WARP * sizeof(R); }
 };
 
@@ -861,7 +875,12 @@ __global__ void __launch_bounds__(SplitShape<C>::THREADS, SplitShape<C>::MIN_BLO
   // current shell quartet
   bool have = false;
   int bi = 0, ki = 0, bpoff = 0, kpoff = 0, nk = 1, total = 0, t0 = 0, qn = 0;
+#ifdef HFX_SPLIT_SMEM_ACC
+  R* const acc = Lay::acc_base(ws) + lane * Lay::ACC_STRIDE;
+  R* const comp = acc + 32 * Lay::ACC_STRIDE;
+#else
   R acc[C::NCHUNK], comp[C::NCHUNK];
+#endif
   for (;;) {
     // A. the next shell quartet: next kept ket of the window, next window of
     //    the batch, or the next batch from the queue (Algorithms 1-3)
