@@ -147,6 +147,17 @@ long long hfx_value_count(const hfx_quartets* q);
  * device arrays of hfx_value_count() doubles.  Asynchronous on `stream`. */
 hfx_status hfx_build_K(hfx_quartets* q, const double* P_val, double* K_val, void* stream);
 
+/* Incremental build: K_val += K(dP_val).  K is linear in the density
+ * (Eq. H-HFX), so an SCF step n can form K(P_n) = K(P_{n-1}) + K(P_n - P_{n-1}).
+ * The density screening (Eq. dmscreening) then uses the shell maxima of the
+ * difference, which is small near convergence, so fewer quartets survive.
+ * dP_val, K_val: device arrays of hfx_value_count() doubles; K_val holds the
+ * previous exchange matrix (symmetric, as hfx_build_K leaves it).  The change
+ * is built into a scratch array the quartet list keeps (hfx_value_count()
+ * doubles, allocated on first use) and added to K_val.  Asynchronous on
+ * `stream`; hfx_get_stats reports the quartets of the difference build. */
+hfx_status hfx_build_K_delta(hfx_quartets* q, const double* dP_val, double* K_val, void* stream);
+
 /* E_x = -1/2 sum_ij P_ij K_ij over the pattern (device reduction, FP64).
  * Synchronises the stream; *E_x is a host double. */
 hfx_status hfx_exchange_energy(hfx_quartets* q, const double* P_val, const double* K_val, double* E_x,

@@ -153,6 +153,7 @@ struct hfx_quartets_s {
   // per-build buffers
   DBuf<double> pmax;                       // n_shells x n_shells
   DBuf<double> scratch;                    // energy accumulator
+  DBuf<double> delta_K;                    // K of a density difference (hfx_build_K_delta)
   float ms_setup = 0.f;
   float ms_setup_phase[4] = {0.f, 0.f, 0.f, 0.f};
   SysArgs h_sys{};  // this system's entry of a build table (P, K unset)
@@ -479,6 +480,12 @@ __global__ void k_dot(long long n, const double* __restrict__ P, const double* _
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     if (threadIdx.x == 0) atomicAdd(out, s);
   }
+}
+
+// y += x over n values (incremental exchange builds)
+__global__ void k_axpy(long long n, const double* __restrict__ x, double* __restrict__ y) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) y[i] += x[i];
 }
 
 __global__ void k_pack(int n_blocks, const int* bx, const int* by, const long long* boff, const long long* afoff,
@@ -1234,7 +1241,7 @@ extern "C" {
 long long hfx_quartets_device_bytes(const hfx_quartets* q) {
   if (!q) return -1;
   long long n = dbytes(q->blk_off) + dbytes(q->blk_x) + dbytes(q->blk_y) + dbytes(q->blk_val_off) +
-                dbytes(q->pmax) + dbytes(q->scratch);
+                dbytes(q->pmax) + dbytes(q->scratch) + dbytes(q->delta_K);
   for (int c = 0; c < 6; ++c) n += dbytes(q->pairs[c]) + dbytes(q->prims[c]);
   for (int c = 0; c < HFX_NCLASS; ++c) n += dbytes(q->desc[c]) + dbytes(q->plan.desc_own[c]);
   const Plan& pl = q->plan;
@@ -1320,6 +1327,20 @@ hfx_status hfx_build_K(hfx_quartets* q, const double* P, double* K, void* stream
   pl.h_sys[0].P = P;
   pl.h_sys[0].K = K;
   return plan_build(pl, (cudaStream_t)stream, false, true);
+}
+
+hfx_status hfx_build_K_delta(hfx_quartets* q, const double* dP, double* K, void* stream) {
+  if (!q || !dP || !K) return fail(HFX_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (q->delta_K.p == nullptr || q->delta_K.n < (size_t)q->n_values) HFX_CK(q->delta_K.alloc((size_t)q->n_values));
+  const hfx_status st = hfx_build_K(q, dP, q->delta_K.p, stream);
+  if (st != HFX_OK) return st;
+  if (q->n_values > 0) {
+    const int blocks = (int)std::max<long long>(1, std::min<long long>(4LL * q->n_sm, (q->n_values + 255) / 256));
+    k_axpy<<<blocks, 256, 0, s>>>(q->n_values, q->delta_K.p, K);
+    HFX_CK(cudaGetLastError());
+  }
+  return HFX_OK;
 }
 
 hfx_status hfx_exchange_energy(hfx_quartets* q, const double* P, const double* K, double* E_x, void* stream) {

@@ -74,7 +74,8 @@ class ClassInfo(ctypes.Structure):
 KERNEL_KIND_NAMES = ("k_build_K", "k_build_K_split", "k_build_K_coop")
 
 
-EXPORTED = ["hfx_create_basis", "hfx_build_quartets", "hfx_value_count", "hfx_build_K", "hfx_exchange_energy",
+EXPORTED = ["hfx_create_basis", "hfx_build_quartets", "hfx_value_count", "hfx_build_K", "hfx_build_K_delta",
+            "hfx_exchange_energy",
             "hfx_pack_dense", "hfx_unpack_dense", "hfx_eval_quartets", "hfx_boys_eval", "hfx_get_stats",
             "hfx_get_class_info", "hfx_exchange_energy_noalloc", "hfx_batch_create", "hfx_batch_build_K",
             "hfx_batch_energies", "hfx_batch_autotune", "hfx_batch_get_tuning", "hfx_batch_get_stats",
@@ -123,6 +124,7 @@ def load(path: str = LIB_PATH):
     lib.hfx_value_count.argtypes = [V]
     lib.hfx_value_count.restype = LL
     lib.hfx_build_K.argtypes = [V, V, V, V]
+    lib.hfx_build_K_delta.argtypes = [V, V, V, V]
     lib.hfx_exchange_energy.argtypes = [V, V, V, ctypes.POINTER(D), V]
     lib.hfx_pack_dense.argtypes = [V, V, V, V]
     lib.hfx_unpack_dense.argtypes = [V, V, V, V]
@@ -272,6 +274,11 @@ def hfx_build_K(q, P_val, K_val, stream=None):
     _check(load().hfx_build_K(q, _ptr(P_val), _ptr(K_val), _stream(stream)))
 
 
+def hfx_build_K_delta(q, dP_val, K_val, stream=None):
+    """K_val += K(dP_val) (incremental build; see hfx.h)."""
+    _check(load().hfx_build_K_delta(q, _ptr(dP_val), _ptr(K_val), _stream(stream)))
+
+
 def hfx_exchange_energy(q, P_val, K_val, stream=None) -> float:
     e = ctypes.c_double()
     _check(load().hfx_exchange_energy(q, _ptr(P_val), _ptr(K_val), ctypes.byref(e), _stream(stream)))
@@ -374,6 +381,9 @@ class Quartets:
 
     def build_K(self, P_val, K_val, stream=None):
         hfx_build_K(self.handle, P_val, K_val, stream)
+
+    def build_K_delta(self, dP_val, K_val, stream=None):
+        hfx_build_K_delta(self.handle, dP_val, K_val, stream)
 
     def exchange_energy(self, P_val, K_val, stream=None) -> float:
         return hfx_exchange_energy(self.handle, P_val, K_val, stream)
