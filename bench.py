@@ -58,24 +58,45 @@ def _peaks():
 
 def fp64_prologue_flops(L, kernel):
     """FP64 flops (FMA = 2) of the per-primitive-quartet prologue of the FP64
-    path as written in eri_common.cuh: argument T, prefactor, Boys function(s),
-    erfc difference."""
-    boys = 17 + (16 + 3 * L if L > 0 else 0)
-    base = 31
+    path as written in eri_common.cuh (two Newton steps per reciprocal and
+    reciprocal square root).  Argument and prefactor: p+q 1, 1/(p+q) 8, rho 2,
+    PQ 3, T 6, prefactor 3 + rsqrt 12 = 35.  Boys (T below the table end): grid
+    offset 3, Taylor series of F_L 12; for L > 0 exp(-T) 16 and 3 per
+    downward step.  Coulomb: 1 per G_m.  erfc: attenuation factor 10, f T 1,
+    f^{1/2} 13, a second Boys evaluation, 4 per G_m."""
+    boys = 15 + (16 + 3 * L if L > 0 else 0)
     if kernel == 0:
-        return base + boys + (L + 1)
-    return base + 2 * boys + 1 + 8 + 12 + 4 * (L + 1)
+        return 35 + boys + (L + 1)
+    if kernel == 2:
+        return 35 + 24 + boys + 3 * (L + 1)
+    return 35 + 24 + 2 * boys + 4 * (L + 1)
+
+
+# FP32 flops of the double-single operations of boys_ds.cuh (FMA = 2;
+# TwoSum 6, Fast-TwoSum 3)
+DS_ADD, DS_MUL, DS_MULF, DS_ADDF = 11, 10, 8, 10
+DS_RCP = 1 + 2 * DS_MULF + 2 * DS_ADDF            # seed, one Newton step: 37
+DS_RSQRT = 1 + 3 * DS_MULF + 2 * DS_ADDF + 1      # seed, one Newton step: 46
 
 
 def ds_prologue_flops(L, kernel):
     """FP32 flops of the same prologue in double-single arithmetic
-    (boys_ds.cuh): argument and prefactor ~160, Boys 88 (+67+27L for L > 0),
-    erfc: second Boys, attenuation factor and the per-m difference."""
-    base = 160
-    boys = 88 + (67 + 27 * L if L > 0 else 0)
+    (prologue_ds and boys_ds in boys_ds.cuh).  Argument and prefactor: p+q,
+    1/(p+q), rho, three PQ components with their squares, T, prefactor
+    (reciprocal square root and three products) = 246.  Boys: grid offset 12,
+    Taylor series of F_L 86; for L > 0 exp(-T) 78 and 31 per downward step.
+    Coulomb: 11 per G_m.  erfc: attenuation factor 58, f T 10, f^{1/2} 56, a
+    second Boys evaluation, 42 per G_m."""
+    base = DS_ADD + DS_RCP + 2 * DS_MUL + 3 * (6 + 2 + 3 + DS_MUL + DS_ADD) + DS_MUL + DS_RSQRT + DS_MUL + 2 * DS_MULF
+    boys = 12 + 4 + DS_MULF + DS_ADD + 3 * (DS_MUL + DS_ADD)
+    if L > 0:
+        boys += 8 + DS_MULF + DS_ADDF + 2 * (DS_MUL + DS_ADDF) + DS_MUL + 2 + L * (2 * DS_MUL + DS_ADD)
     if kernel == 0:
-        return base + boys + 2 * (L + 1)
-    return base + 2 * boys + 101 + 29 * (L + 1)
+        return base + boys + (L + 1) * (DS_MUL + 1)
+    atten = (DS_ADD + DS_RCP + DS_MUL) + DS_MUL + (DS_RSQRT + DS_MUL)
+    if kernel == 2:
+        return base + atten + boys + (L + 1) * (3 * DS_MUL + 1)
+    return base + atten + 2 * boys + (L + 1) * (3 * DS_MUL + DS_ADD + 1)
 
 
 def class_flops(ci, n_q, n_pq, kernel, fp32):
