@@ -747,12 +747,13 @@ __global__ void __launch_bounds__(kThreadsCoop) k_build_K_coop(const BuildArgs a
 #ifndef HFX_WIDE_MIN_FLOPS
 #define HFX_WIDE_MIN_FLOPS 2000
 #endif
-template <class C>
+template <class C, typename R>
 struct SplitShape {
   static constexpr bool LOCKSTEP = C::VRR_FLOPS >= HFX_LOCKSTEP_MIN_FLOPS;
-  // a horizontal-recursion workspace this large (doubles or floats per warp)
-  // leaves room for 4-warp blocks only
-  static constexpr bool BIG_HRR = C::Coop::HRR_SLOTS > 4096;
+  // a horizontal-recursion workspace above 32 KB per warp leaves room for
+  // 4-warp blocks only: (dd|dd) in FP64 (6254 slots x 8 B); in FP32 its eight
+  // warps take 205 KB of shared memory, like the FP64 four
+  static constexpr bool BIG_HRR = C::Coop::HRR_SLOTS * sizeof(R) > 4096 * sizeof(double);
   static constexpr int WARPS = (C::VRR_FLOPS >= HFX_WIDE_MIN_FLOPS && !BIG_HRR) ? 8 : 4;
   static constexpr int THREADS = 32 * WARPS;
   static constexpr int MIN_BLOCKS = (WARPS == 8 || BIG_HRR) ? 1 : 3;
@@ -776,7 +777,7 @@ struct SplitLayout {
 #else
   static constexpr int PER_WARP = T::HRR_SLOTS + 160;  // HRR workspace + four P blocks
 #endif
-  static constexpr size_t bytes() { return (size_t)SplitShape<C>::WARPS * PER_WARP * sizeof(R); }
+  static constexpr size_t bytes() { return (size_t)SplitShape<C, R>::WARPS * PER_WARP * sizeof(R); }
 };
 
 // One pass: prologue and vertical recursion of primitive quartet t of the
@@ -856,12 +857,12 @@ __device__ __forceinline__ bool split_prims_ok(const BuildArgs& a, const SysArgs
 #endif
 
 template <class C, typename R>
-__global__ void __launch_bounds__(SplitShape<C>::THREADS, SplitShape<C>::MIN_BLOCKS)
+__global__ void __launch_bounds__(SplitShape<C, R>::THREADS, SplitShape<C, R>::MIN_BLOCKS)
     k_build_K_split(const BuildArgs a) {
   using Lay = SplitLayout<C, R>;
   constexpr bool kMixed = sizeof(R) == 4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int s_pq[SplitShape<C>::WARPS][64];
+  __shared__ int s_pq[SplitShape<C, R>::WARPS][64];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   R* ws = reinterpret_cast<R*>(smem_raw) + warp * Lay::PER_WARP;
   R* pbuf = ws + C::Coop::HRR_SLOTS;
@@ -975,7 +976,7 @@ __global__ void __launch_bounds__(SplitShape<C>::THREADS, SplitShape<C>::MIN_BLO
     }
     // C. lockstep classes: the round ends for the whole block, which stops
     //    once no warp has work left; otherwise each warp runs on by itself
-    if constexpr (SplitShape<C>::LOCKSTEP) {
+    if constexpr (SplitShape<C, R>::LOCKSTEP) {
       if (!__syncthreads_or(have || !exhausted)) break;
     } else {
       if (!have && exhausted) break;
@@ -1112,7 +1113,7 @@ void launch_build_K_t(const BuildArgs& a, int grid, cudaStream_t s) {
       cudaFuncSetAttribute(k_build_K_split<C, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
       attr = true;
     }
-    k_build_K_split<C, R><<<grid, SplitShape<C>::THREADS, sm, s>>>(a);
+    k_build_K_split<C, R><<<grid, SplitShape<C, R>::THREADS, sm, s>>>(a);
   } else {
     k_build_K<C, R><<<grid, kThreadsK, 0, s>>>(a);
   }
@@ -1136,7 +1137,7 @@ int occupancy_build_K_t() {
   } else if constexpr (C::SPLIT) {
     const size_t sm = SplitLayout<C, R>::bytes();
     cudaFuncSetAttribute(k_build_K_split<C, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_build_K_split<C, R>, SplitShape<C>::THREADS, sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_build_K_split<C, R>, SplitShape<C, R>::THREADS, sm);
   } else {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_build_K<C, R>, kThreadsK, 0);
   }
