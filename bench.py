@@ -580,6 +580,62 @@ def run_periodic(args):
             "setup_s": setup_s, "clocks": clocks}
 
 
+def run_incremental(args):
+    """--incremental: one SCF-like step of the cluster workload, P2 = P1
+    perturbed by --incremental-rel (pattern kept).  K(P2) from a full build
+    against K(P1) + K(P2 - P1) from hfx_build_K_delta (density screening on
+    the difference): build times, quartets evaluated, and the energy
+    difference of the two results."""
+    import torch
+    from paper_2009_03555_gb300 import hfx
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dev = torch.device("cuda")
+    s, P1, mask = workload(args.atoms)
+    P2 = synth.perturb_density(P1, np.random.default_rng(2009_03555 + 5), rel=args.incremental_rel)
+    prec = hfx.HFX_PREC_MIXED if args.precision == "mixed" else hfx.HFX_PREC_FP64
+    promote = args.promote if prec == hfx.HFX_PREC_MIXED else math.inf
+    opts = hfx.make_opts(kernel=hfx.HFX_KERNEL_ERFC, omega=0.11, screen=True, tau=1e-8, density_screen=True,
+                         eps=1e-8, prim_cutoff=args.prim_cutoff, precision=prec, fp64_promote_bound=promote,
+                         n_block=args.n_block, promote_min_l=args.promote_min_l)
+    q = hfx.Quartets(hfx.Basis(s), opts, mask)
+
+    def values(P):
+        v = torch.empty(q.n_values, dtype=torch.float64, device=dev)
+        q.pack(torch.from_numpy(np.ascontiguousarray(P)).to(dev), v)
+        return v
+
+    P1v, P2v, dPv = values(P1), values(P2), values(P2 - P1)
+    K1, K2, K = torch.empty_like(P1v), torch.empty_like(P1v), torch.empty_like(P1v)
+    stream = torch.cuda.current_stream()
+    q.build_K(P1v, K1)  # the previous step's K (also the warm-up)
+    torch.cuda.synchronize()
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    ms_full = timed(lambda: q.build_K(P2v, K2))
+    n_full = sum(q.stats().n_quartets_computed)
+    K.copy_(K1)
+    ms_delta = timed(lambda: q.build_K_delta(dPv, K))
+    n_delta = sum(q.stats().n_quartets_computed)
+    E_full = q.exchange_energy(P2v, K2)
+    E_inc = q.exchange_energy(P2v, K)
+    return {"metric": "hfx_incremental_speedup", "value": ms_full / ms_delta, "unit": "x", "n_gpus": 1,
+            "higher_is_better": True, "dtype": "f32+f64" if prec == hfx.HFX_PREC_MIXED else "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{args.atoms}-atom C/H cluster, HSE erfc w=0.11, Schwarz 1e-8 + density "
+                                   f"screening, P2 = P1 o (1 + {args.incremental_rel} xi), {args.precision}",
+                       "atoms": args.atoms, "precision": args.precision, "rel": args.incremental_rel},
+            "ms_full": ms_full, "ms_delta": ms_delta, "quartets_full": int(n_full), "quartets_delta": int(n_delta),
+            "E_x_full": E_full, "E_x_incremental": E_inc, "abs_dE_x": abs(E_inc - E_full)}
+
+
 def run_precision_check(args):
     """--mixed-vs-fp64: the same build in FP64 and in mixed precision (same
     screening and primitive cutoff), the mixed one for every FP64-promotion
@@ -657,6 +713,8 @@ def main():
     ap.add_argument("--batch", action="store_true", help="many small systems per build (batched vs sequential)")
     ap.add_argument("--batch-systems", type=int, default=64)
     ap.add_argument("--batch-atoms", default="8,24", help="cluster sizes (atoms), min,max")
+    ap.add_argument("--incremental", action="store_true", help="full build vs incremental build of one SCF-like step")
+    ap.add_argument("--incremental-rel", type=float, default=1e-3, help="relative change of P between the steps")
     ap.add_argument("--periodic", action="store_true", help="periodic Si supercell built as its extended atom set")
     ap.add_argument("--periodic-cells", type=int, default=3, help="conventional cells per axis of the Si supercell")
     ap.add_argument("--periodic-rext", type=float, default=10.0, help="image radius (bohr)")
@@ -665,6 +723,9 @@ def main():
     ap.add_argument("--fp64-energy", type=float, default=None,
                     help="precision check: FP64 E_x of an earlier run of the same workload instead of a new FP64 build")
     args = ap.parse_args()
+    if args.incremental:
+        print(json.dumps(run_incremental(args)), flush=True)
+        return 0
     if args.periodic:
         print(json.dumps(run_periodic(args)), flush=True)
         return 0
