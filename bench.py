@@ -355,8 +355,8 @@ def run_reference(args, rank, world):
     if rank != 0:
         return None
     qpb = args.ref_quartets_per_build
-    for _ in range(args.warmup if args.warmup < 1 else 1):
-        pass
+    for _ in range(args.warmup):  # untimed warm-up steps, the same sample
+        run_cpu_oracle(args)
     vals = []
     for _ in range(args.steps):
         qps, nt, dt, n = run_cpu_oracle(args)
