@@ -845,7 +845,8 @@ __device__ __forceinline__ bool split_desc_ok(const BuildArgs& a, const Desc& ds
 __device__ __forceinline__ bool split_prims_ok(const BuildArgs& a, const SysArgs& S, const PairRec& bra,
                                                const PairRec& ket) {
   const int cc = a.bra_class * 10 + a.ket_class;
-  if (bra.pcnt < 0 || ket.pcnt < 0 || bra.pcnt > 64 || ket.pcnt > 64) return hfx_oob("pcnt", bra.pcnt, 64, cc);
+  // at most 16 x 16 primitive pairs per shell pair (16 primitives per shell)
+  if (bra.pcnt < 0 || ket.pcnt < 0 || bra.pcnt > 256 || ket.pcnt > 256) return hfx_oob("pcnt", bra.pcnt, 256, cc);
   if (bra.pcnt > 0 && (!HFX_IN(bra.poff, S.n_prims[a.bra_class], "bra.poff", cc) ||
                        !HFX_IN(bra.poff + bra.pcnt - 1, S.n_prims[a.bra_class], "bra.poff+pcnt", cc)))
     return false;
