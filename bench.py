@@ -394,8 +394,10 @@ def run_serve(args):
     kinds = rng.integers(0, 2, size=n)
     sizes = [int(rng.integers(c0, c1 + 1)) if k == 0 else int(rng.integers(s0, s1 + 1)) for k in kinds]
     prec = hfx.HFX_PREC_MIXED if args.precision == "mixed" else hfx.HFX_PREC_FP64
+    promote = args.promote if prec == hfx.HFX_PREC_MIXED else math.inf
     opts = hfx.make_opts(kernel=hfx.HFX_KERNEL_ERFC, omega=0.11, screen=True, tau=1e-8, density_screen=True,
-                         eps=1e-8, prim_cutoff=args.prim_cutoff, precision=prec, n_block=args.n_block)
+                         eps=1e-8, prim_cutoff=args.prim_cutoff, precision=prec, n_block=args.n_block,
+                         fp64_promote_bound=promote, promote_min_l=args.promote_min_l)
     reqs = []
     for i, (k, na) in enumerate(zip(kinds, sizes)):
         s = synth.ch_chain(na, sub=i) if k == 0 else synth.ch_slab(na, sub=i)
@@ -446,7 +448,8 @@ def run_serve(args):
             "config": {"workload": f"{n} requests, Poisson {args.serve_rate}/s, {args.serve_builds} builds each "
                                    f"(P perturbed 1e-3), C/H chains {c0}-{c1} atoms and slabs {s0}-{s1} atoms, "
                                    f"HSE erfc w=0.11, Schwarz 1e-8 + density screening, {args.precision}",
-                       "use_graph": bool(args.serve_graph), "precision": args.precision},
+                       "use_graph": bool(args.serve_graph), "precision": args.precision,
+                       "fp64_promote_bound": _json_num(promote), "promote_min_l": args.promote_min_l},
             "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3),
                            "max": float(lat.max() * 1e3), "mean": float(lat.mean() * 1e3)},
             "makespan_s": makespan, "builds": builds, "max_active": info.max_active_seen,
@@ -467,8 +470,10 @@ def run_batch(args):
     lo, hi = (int(x) for x in args.batch_atoms.split(","))
     sizes = rng.integers(lo, hi + 1, size=args.batch_systems)
     prec = hfx.HFX_PREC_MIXED if args.precision == "mixed" else hfx.HFX_PREC_FP64
+    promote = args.promote if prec == hfx.HFX_PREC_MIXED else math.inf
     opts = hfx.make_opts(kernel=hfx.HFX_KERNEL_ERFC, omega=0.11, screen=True, tau=1e-8, density_screen=True,
-                         eps=1e-8, prim_cutoff=args.prim_cutoff, precision=prec, n_block=args.n_block)
+                         eps=1e-8, prim_cutoff=args.prim_cutoff, precision=prec, n_block=args.n_block,
+                         fp64_promote_bound=promote, promote_min_l=args.promote_min_l)
     mem = []
     for i, na in enumerate(sizes):
         s = synth.ch_cluster(int(na), 3, sub=i)
@@ -514,7 +519,8 @@ def run_batch(args):
             "dtype": "f32+f64" if prec == hfx.HFX_PREC_MIXED else "f64", "data": "synthetic",
             "config": {"workload": f"{n} C/H clusters of {lo}-{hi} atoms (sum {int(sizes.sum())} atoms), HSE erfc "
                                    f"w=0.11, Schwarz 1e-8 + density screening, P cut 14 bohr, {args.precision}",
-                       "systems": n, "atoms_total": int(sizes.sum()), "precision": args.precision},
+                       "systems": n, "atoms_total": int(sizes.sum()), "precision": args.precision,
+                       "fp64_promote_bound": _json_num(promote), "promote_min_l": args.promote_min_l},
             "ms_batched_graph": ms_batch, "ms_sequential": ms_seq, "ms_autotuned_graph": ms_tuned,
             "speedup_vs_sequential": ms_seq / ms_batch, "autotune_s": tune_s,
             "autotuned_vs_default": ms_batch / ms_tuned,

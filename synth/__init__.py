@@ -274,6 +274,26 @@ def periodic_density_matrix(sys: System, config_idx: int = 4, cutoff: float | No
     return np.ascontiguousarray(P)
 
 
+def shell_subset(sys: System, P: np.ndarray, keep_l) -> tuple[System, np.ndarray]:
+    """The shells of ``sys`` whose angular momentum is in ``keep_l`` (same atoms
+    and centres, shells in the original order) and the matching rows and
+    columns of the density matrix ``P``.  Used to isolate one angular-momentum
+    class of quartets (e.g. only d shells: every quartet is (dd|dd))."""
+    keep = [S for S in range(sys.n_shells) if int(sys.shell_l[S]) in set(keep_l)]
+    po = sys.prim_off
+    take = np.concatenate([np.arange(po[S], po[S + 1]) for S in keep])
+    n_p = np.array([po[S + 1] - po[S] for S in keep])
+    sub = System(name=sys.name + "_l" + "".join(str(l) for l in sorted(set(keep_l))), atom_Z=sys.atom_Z.copy(),
+                 atom_xyz=sys.atom_xyz.copy(), shell_atom=sys.shell_atom[keep].astype(np.int32),
+                 shell_l=sys.shell_l[keep].astype(np.int32),
+                 prim_off=np.concatenate([[0], np.cumsum(n_p)]).astype(np.int32),
+                 alpha=sys.alpha[take].copy(), coef=sys.coef[take].copy(),
+                 lattice=None if sys.lattice is None else sys.lattice.copy())
+    fo = sys.func_off
+    f = np.concatenate([np.arange(fo[S], fo[S + 1]) for S in keep])
+    return sub, np.ascontiguousarray(P[np.ix_(f, f)])
+
+
 def atom_distances(sys: System) -> np.ndarray:
     d = sys.atom_xyz[:, None, :] - sys.atom_xyz[None, :, :]
     return np.sqrt(np.sum(d * d, axis=-1))

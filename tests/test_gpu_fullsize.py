@@ -1,13 +1,16 @@
 """Parity at the full benchmark size, in the launch configuration the benchmark
 times: the 400-atom C/H cluster (5600 Cartesian functions), HSE erfc kernel
 (w = 0.11), Schwarz 1e-8 with density screening, P cut at 14 bohr, mixed
-precision, primitive cutoff 1e-13, work-queue batches of 128 quartets.
+precision with the (dd|dd) quartets above Q_IJ Q_KL P_scr = 1e-5 promoted to
+FP64 (promotion bound 1e-5, classes of total l >= 8), primitive cutoff 1e-13,
+work-queue batches of 128 quartets: the options bench.py times.
 
 The oracle cannot build the whole K at this size, so it computes sampled
 exchange blocks K_IJ one shell pair at a time straight from the definition
 (every ordered (K, L) whose quartet (I K | J L) survives the same screening),
-and the number of surviving canonical quartets (stored by
-oracle/count_quartets.py), which the build must match exactly.
+and two quartet counts stored by oracle/count_quartets.py, which the build
+must match exactly: the surviving canonical quartets (both precision passes
+together) and the (dd|dd) quartets above the promotion bound (the FP64 pass).
 
 Tolerance, derived from the per-integral bounds of the mixed path: each
 integral of a surviving quartet is within 2e-4 Q_IK Q_JL of the exact value
@@ -71,7 +74,8 @@ def test_sampled_blocks_400_atoms_mixed():
 
     s, P, mask = _workload()
     opts = hfx.make_opts(kernel=hfx.HFX_KERNEL_ERFC, omega=0.11, screen=True, tau=1e-8, density_screen=True,
-                         eps=1e-8, prim_cutoff=1e-13, precision=hfx.HFX_PREC_MIXED, n_block=128)
+                         eps=1e-8, prim_cutoff=1e-13, precision=hfx.HFX_PREC_MIXED, n_block=128,
+                         fp64_promote_bound=1e-5, promote_min_l=8)
     basis = hfx.Basis(s)
     q = hfx.Quartets(basis, opts, mask)
     dev = torch.device("cuda")
@@ -92,9 +96,19 @@ def test_sampled_blocks_400_atoms_mixed():
     # same screening (oracle/count_quartets.py, tests/golden/)
     import json
     import os
-    with open(os.path.join(os.path.dirname(__file__), "golden", f"quartet_count_hse_c{N_ATOMS}.json")) as fh:
+    gold = os.path.join(os.path.dirname(__file__), "golden")
+    with open(os.path.join(gold, f"quartet_count_hse_c{N_ATOMS}.json")) as fh:
         n_oracle = json.load(fh)["canonical_quartets"]
-    assert sum(q.stats().n_quartets_computed) == n_oracle
+    with open(os.path.join(gold, f"quartet_count_hse_c{N_ATOMS}_dddd_above1e-05.json")) as fh:
+        n_promoted = json.load(fh)["canonical_quartets"]
+    st = q.stats()
+    assert sum(st.n_quartets_computed) == n_oracle
+    assert sum(st.n_quartets_pass[0]) + sum(st.n_quartets_pass[1]) == n_oracle
+    dddd = [c for c in range(hfx.N_CLASSES) if hfx.hfx_get_class_info(c).la + hfx.hfx_get_class_info(c).lb
+            + hfx.hfx_get_class_info(c).lc + hfx.hfx_get_class_info(c).ld == 8]
+    assert len(dddd) == 1
+    assert st.n_quartets_pass[1][dddd[0]] == n_promoted > 0
+    assert sum(st.n_quartets_pass[1]) == n_promoted  # no other class promoted
 
     pairs = _sample_pairs(s, np.random.default_rng(2009_03555 + 400))
     blocks, W1, W0, n = oracle.K_shell_pairs(oracle.Basis(s), P, pairs, kernel=oracle.KERNEL_ERFC,

@@ -159,3 +159,92 @@ def test_errors_are_reported():
     with pytest.raises(hfx.HFXError) as ei:
         hfx.Quartets(b, hfx.make_opts(), asym)
     assert ei.value.status == 1
+
+
+@pytest.mark.parametrize("min_l,d_only", [(0, False), (8, True)], ids=["every-class", "dddd-only"])
+def test_promoted_pass_elementwise_fp64(min_l, d_only):
+    """The FP64-promoted pass of the mixed path (the launch the benchmark's
+    (dd|dd) promotion runs) element by element against the oracle at the FP64
+    tolerance: promotion bound 0 sends every surviving quartet of the promoted
+    classes to FP64.  With classes of total l >= 8 only, a system of d shells
+    alone makes every quartet (dd|dd), so the whole K comes from that pass."""
+    from paper_2009_03555_gb300 import hfx
+    s = synth.ch_cluster(4, 13)
+    mask = pattern_mask(s, 6.0)
+    P = synth.density_matrix(s, 13) * mask_dense(s, mask)
+    if d_only:
+        s, P = synth.shell_subset(s, P, [2])
+    kw = dict(kernel=oracle.KERNEL_ERFC, omega=0.11, screen=True, tau=1e-8, density_screen=True, eps=1e-8)
+    Kref, n = oracle.build_K(oracle.Basis(s), P, **kw)
+    K, E, q = run_gpu_K(s, P, mask=mask, prim_cutoff=1e-14, precision=hfx.HFX_PREC_MIXED,
+                        fp64_promote_bound=0.0, promote_min_l=min_l, **kw)
+    st = q.stats()
+    assert sum(st.n_quartets_pass[0]) == 0 and sum(st.n_quartets_pass[1]) == n
+    md = mask_dense(s, mask)
+    assert np.abs((K - Kref) * md).max() <= 1e-10
+    Eref = oracle.exchange_energy(P, Kref)
+    assert abs(E - Eref) <= 1e-9 * abs(Eref)
+
+
+def test_promotion_routing_matches_oracle_count():
+    """Mixed build with (dd|dd) promotion above Q_IJ Q_KL P_scr = 1e-3 (classes
+    of total l >= 8): the FP64 pass evaluates exactly the (dd|dd) quartets the
+    oracle counts with eps = 1e-3 on the d shells alone, the FP32 pass the rest
+    of the surviving quartets, and the energy stays within 1e-6 Ha."""
+    from paper_2009_03555_gb300 import hfx
+    s = synth.ch_cluster(6, 14)
+    mask = pattern_mask(s, 8.0)
+    P = synth.density_matrix(s, 14) * mask_dense(s, mask)
+    kw = dict(kernel=oracle.KERNEL_ERFC, omega=0.11, tau=1e-8, density_screen=True, eps=1e-8)
+    Kref, n = oracle.build_K(oracle.Basis(s), P, screen=True, **kw)
+    sd, Pd = synth.shell_subset(s, P, [2])
+    n_dd, _ = oracle.count_quartets(oracle.Basis(sd), Pd, kernel=oracle.KERNEL_ERFC, omega=0.11, tau=1e-8,
+                                    density_screen=True, eps=1e-3)
+    assert 0 < n_dd
+    K, E, q = run_gpu_K(s, P, mask=mask, screen=True, precision=hfx.HFX_PREC_MIXED, fp64_promote_bound=1e-3,
+                        promote_min_l=8, **kw)
+    st = q.stats()
+    dd = [c for c in range(hfx.N_CLASSES) if hfx.hfx_get_class_info(c).bra_class == 5
+          and hfx.hfx_get_class_info(c).ket_class == 5]
+    assert st.n_quartets_pass[1][dd[0]] == n_dd == sum(st.n_quartets_pass[1])
+    assert sum(st.n_quartets_pass[0]) + n_dd == n
+    Eref = oracle.exchange_energy(P, Kref)
+    assert abs(E - Eref) <= 1e-6
+
+
+def _sixteen_primitive_d_system():
+    """Two atoms: a d shell of 16 primitives (the library's primitive limit,
+    256 primitive pairs per shell pair) plus an s shell on atom 0, an s and a
+    p shell of 2 primitives on atom 1; exponents log-uniform in [0.1, 50]."""
+    rng = np.random.default_rng(2009_03555 + 16)
+    shells = [(0, 2, 16), (0, 0, 2), (1, 0, 2), (1, 1, 2)]  # (atom, l, nprim)
+    alpha, coef, off = [], [], [0]
+    for _, _, k in shells:
+        alpha.extend(sorted(np.exp(rng.uniform(np.log(0.1), np.log(50.0), size=k)), reverse=True))
+        coef.extend(rng.uniform(0.1, 1.0, size=k))
+        off.append(off[-1] + k)
+    return synth.System(name="d16", atom_Z=np.array([6, 1], dtype=np.int32),
+                        atom_xyz=np.array([[0.0, 0.0, 0.0], [1.2, 0.9, -0.7]]),
+                        shell_atom=np.array([a for a, _, _ in shells], dtype=np.int32),
+                        shell_l=np.array([l for _, l, _ in shells], dtype=np.int32),
+                        prim_off=np.array(off, dtype=np.int32), alpha=np.array(alpha), coef=np.array(coef))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_sixteen_primitive_d_shell(prec):
+    """A d shell at the 16-primitive limit through the warp-split (d-shell
+    class) path: FP64 at |dK|max <= 1e-10, mixed at |dE_x| <= 1e-6 Ha."""
+    from paper_2009_03555_gb300 import hfx
+    s = _sixteen_primitive_d_system()
+    P = synth.density_matrix(s, 16, n_occ=3)
+    kw = dict(kernel=oracle.KERNEL_ERFC, omega=0.11, screen=False, density_screen=False)
+    Kref, n = oracle.build_K(oracle.Basis(s), P, **kw)
+    p = hfx.HFX_PREC_FP64 if prec == "fp64" else hfx.HFX_PREC_MIXED
+    K, E, q = run_gpu_K(s, P, prim_cutoff=0.0, precision=p, **kw)
+    assert sum(q.stats().n_quartets_computed) == n
+    Eref = oracle.exchange_energy(P, Kref)
+    if prec == "fp64":
+        assert np.abs(K - Kref).max() <= 1e-10
+        assert abs(E - Eref) <= 1e-9 * abs(Eref)
+    else:
+        assert abs(E - Eref) <= 1e-6

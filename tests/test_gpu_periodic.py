@@ -3,14 +3,18 @@ home cell (Sec. 2, Eq. H-HFX) built by the CUDA path on the extended atom set
 (hfx_periodic_images, hfx_periodic_pack_host, then hfx_build_K), against the
 oracle's brute-force lattice sum over its own image set.
 
-Tolerances as for molecules: FP64 |dK|max <= 1e-10 and per-cell
-|dE_x| <= 1e-9 |E_x|; mixed precision |dE_x| <= 1e-6 Ha.
+The library forms K on the pattern of P only (the pairs of extended atoms at
+most r_P apart), so the rows are compared on those blocks and must be zero on
+the others (periodic_helpers.formed_blocks_error).  Tolerances as for
+molecules: FP64 |dK|max <= 1e-10 and per-cell |dE_x| <= 1e-9 |E_x|; mixed
+precision |dE_x| <= 1e-6 Ha.
 """
 import numpy as np
 import pytest
 
 import oracle
 import synth
+from periodic_helpers import formed_blocks_error
 
 pytestmark = pytest.mark.gpu
 
@@ -75,11 +79,12 @@ def test_periodic_rows_fp64(kname, A, n_atoms, r_ext, r_P, sub):
               density_screen=kw["density_screen"], precision=hfx.HFX_PREC_FP64)
     K, E, per = gpu_periodic(s, P, A, r_ext, r_P, **hk)
     ref, E_ref = oracle_rows_by_key(s, P, A, r_ext, r_P, **kw)
-    ef = per.system.atom_func_off
     keys = [(int(h), tuple(int(x) for x in n)) for h, n in zip(per.ext_home, per.ext_shift)]
     assert set(keys) == set(ref)
-    err = max(float(np.abs(K[:, ef[X]:ef[X + 1]] - ref[k]).max()) for X, k in enumerate(keys))
+    err, outside, n_formed = formed_blocks_error(K, per, ref, s.atom_func_off)
+    assert n_formed > s.n_atoms  # blocks beyond the home cell's own
     assert err <= 1e-10, err
+    assert outside == 0.0
     assert abs(E - E_ref) <= 1e-9 * abs(E_ref), (E, E_ref)
 
 

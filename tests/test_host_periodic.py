@@ -13,6 +13,7 @@ import pytest
 
 import oracle
 import synth
+from periodic_helpers import formed_blocks_error
 
 SKEW = np.array([[6.0, 0.0, 0.0], [1.0, 6.0, 0.0], [0.0, 1.0, 6.0]])
 FCC = 7.0 * np.array([[0.0, 0.5, 0.5], [0.5, 0.0, 0.5], [0.5, 0.5, 0.0]])
@@ -114,8 +115,15 @@ def test_extended_set_and_density_reproduce_oracle_rows(hfx, opts, A, n_atoms, r
     for X, k in enumerate(keys):
         c0, c1 = col[k]
         np.testing.assert_allclose(Km[:s.n_bf, ef[X]:ef[X + 1]], Kref[:, c0:c1], rtol=0, atol=1e-12 * scale)
-    # per-cell exchange energy from the value prefix of the home rows
+    # what the GPU test sees: K kept on the pattern only (the library forms no
+    # other block), compared on the formed blocks with zeros required elsewhere
     Kv = hfx._SystemInput(e, per.mask).pack(Km)
+    Kpat = unpack(e, per.mask, Kv)[:s.n_bf]
+    ref = {k: Kref[:, col[k][0]:col[k][1]] for k in keys}
+    err, outside, n_formed = formed_blocks_error(Kpat, per, ref, s.atom_func_off)
+    assert n_formed > s.n_atoms
+    assert err <= 1e-12 * scale and outside == 0.0
+    # per-cell exchange energy from the value prefix of the home rows
     E_prefix = -0.5 * float(np.dot(Pv[:per.n_home_values], Kv[:per.n_home_values]))
     E_rows = -0.5 * float(np.sum(Pe[:s.n_bf] * Km[:s.n_bf]))
     assert abs(E_prefix - E_rows) <= 1e-13 * abs(E_rows)

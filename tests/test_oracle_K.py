@@ -188,3 +188,59 @@ def test_count_quartets_equals_canonical_loop(tiny, dscreen):
     n, Q = oracle.count_quartets(b, P, **kw)
     assert n == n_loop > 0
     np.testing.assert_array_equal(Q, oracle.schwarz(b, oracle.KERNEL_ERFC))
+
+
+def _canonical_survivors(s, Pmax_nonzero, pairing):
+    """Brute-force count of canonical shell quartets (I>=J, K>=L, IJ>=KL) whose
+    P_scr is nonzero, with P_scr built from the shell-pair blocks ``pairing``
+    names: 'exchange' = the four blocks (IK, IL, JK, JL) of Eq. dmscreening,
+    'coulomb' = (IJ, KL), a plausible wrong reading."""
+    ns = s.n_shells
+    pairs = [(i, j) for i in range(ns) for j in range(i + 1)]
+    n = 0
+    for a in range(len(pairs)):
+        I, J = pairs[a]
+        for c in range(a + 1):
+            K, L = pairs[c]
+            if pairing == "exchange":
+                nz = Pmax_nonzero[I, K] or Pmax_nonzero[I, L] or Pmax_nonzero[J, K] or Pmax_nonzero[J, L]
+            else:
+                nz = Pmax_nonzero[I, J] or Pmax_nonzero[K, L]
+            n += bool(nz)
+    return n
+
+
+def test_exact_pscr_skip_uses_the_four_exchange_blocks():
+    """The exact P_scr = 0 skip alone (Schwarz threshold 0, no density
+    screening) with P nonzero in one off-diagonal atom-pair block only: every
+    skipped quartet has all four exchange blocks P_IK, P_IL, P_JK, P_JL zero
+    (Eq. dmscreening), so it contributes nothing and the screened K equals the
+    unscreened K; the number of survivors equals a brute-force count over the
+    canonical quartets with those four blocks.  Pairing the blocks as
+    (P_IJ, P_KL) instead changes both for this P."""
+    s = synth.ch_cluster(4, 97, nprim=2)
+    b = oracle.Basis(s)
+    rng = np.random.default_rng(97)
+    fo = s.atom_func_off
+    X, Y = 0, 2
+    P = np.zeros((s.n_bf, s.n_bf))
+    blk = rng.standard_normal((fo[X + 1] - fo[X], fo[Y + 1] - fo[Y]))
+    P[fo[X]:fo[X + 1], fo[Y]:fo[Y + 1]] = blk
+    P[fo[Y]:fo[Y + 1], fo[X]:fo[X + 1]] = blk.T
+    k = oracle.KERNEL_ERFC
+    Kf, nf = oracle.build_K(b, P, kernel=k)
+    Ks, ns_ = oracle.build_K(b, P, kernel=k, screen=True, tau=0.0, density_screen=False)
+    assert 0 < ns_ < nf
+    assert np.abs(Kf).max() > 0
+    np.testing.assert_allclose(Ks, Kf, rtol=0, atol=1e-14 * np.abs(Kf).max())
+    # shell-pair |P| maxima, then the brute-force survivor counts
+    sf = s.func_off
+    nz = np.zeros((s.n_shells, s.n_shells), dtype=bool)
+    for I in range(s.n_shells):
+        for J in range(s.n_shells):
+            nz[I, J] = np.abs(P[sf[I]:sf[I + 1], sf[J]:sf[J + 1]]).max() > 0
+    n_exch = _canonical_survivors(s, nz, "exchange")
+    assert ns_ == n_exch
+    n_count, _ = oracle.count_quartets(b, P, kernel=k, tau=0.0, density_screen=False)
+    assert n_count == n_exch
+    assert _canonical_survivors(s, nz, "coulomb") != n_exch
