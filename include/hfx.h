@@ -260,15 +260,53 @@ long long hfx_setup_bytes_estimate(const hfx_shell_desc* shells, int n_shells, c
 /* ---- Periodic systems (Sec. 2, Eq. H-HFX) ------------------------------
  * The periodic exchange K^G_{mu lambda} = sum_{N,H} sum_{nu sigma}
  * P^{H-N}_{nu sigma} (mu^0 nu^N | lambda^G sigma^H) (mu in the home cell; N, G,
- * H cells of the auxiliary supercell) is the molecular exchange of an
- * extended atom set: the home atoms (extended atoms 0..n_home-1, in home
- * order) followed by the images, each image carrying its home atom's shells
- * at the translated centre.  Build it with hfx_create_basis /
- * hfx_build_quartets / hfx_build_K on the extended shells and pattern; the
- * rows of the home atoms are K^G.  The exchange energy per cell is
- * -1/2 sum over the home atoms' rows of P K: with the home atoms first, those
- * rows are a prefix of the value arrays (hfx_exchange_energy_noalloc with
- * that prefix length). */
+ * H cells of the auxiliary supercell) is built on an extended atom set: the
+ * home atoms (extended atoms 0..n_home-1, in home order) followed by the
+ * images, each image carrying its home atom's shells at the translated
+ * centre.  hfx_create_basis_periodic builds that set inside the library;
+ * hfx_build_quartets on such a basis evaluates only the quartets with at least
+ * one home-cell shell (the paper's list-IJ with I in the unit cell: every
+ * integral (mu^0 nu | lambda sigma) of a home row is one of them), and
+ * hfx_build_K returns the home rows K^G (the leading rows of the value
+ * layout) with every row of an image atom set to zero.  hfx_exchange_energy
+ * then gives the exchange energy per cell, -1/2 sum over the home rows of P K. */
+
+/* Periodic basis.  shells, atom_xyz: the home cell as for hfx_create_basis;
+ * lattice: host, 3 x 3, lattice vectors a_i as rows (bohr); r_ext (bohr): the
+ * images are the translates R_a + n1 a1 + n2 a2 + n3 a3 (n != 0) of home atoms
+ * that lie within r_ext of at least one home atom, in the order of
+ * hfx_periodic_images.  Errors as hfx_create_basis and hfx_periodic_images
+ * (HFX_ERR_INVALID_ARG for a singular lattice or a negative r_ext).
+ * Synchronises the stream; release with hfx_destroy_basis. */
+hfx_status hfx_create_basis_periodic(const hfx_shell_desc* shells, int n_shells, const double* atom_xyz, int n_atoms,
+                                     const double* lattice, double r_ext, void* stream, hfx_basis** out);
+
+/* Atoms of a basis: returns their number (the extended set for a periodic
+ * basis), -1 for NULL.  n_home_atoms (may be NULL): home atoms (all atoms of
+ * a molecular basis); ext_home (may be NULL): per atom its home atom;
+ * ext_shift (may be NULL): per atom its lattice shift (n1, n2, n3), zero for
+ * home atoms.  Host arrays sized by the return value. */
+int hfx_basis_atoms(const hfx_basis* basis, int* n_home_atoms, int* ext_home, int* ext_shift);
+
+/* Extended atom set of a periodic cell (host only; the set
+ * hfx_create_basis_periodic builds): the n_atoms home atoms, then the images of
+ * hfx_periodic_images in its order.  Returns the number of extended atoms, -1
+ * on bad input (message in hfx_last_error).  The first min(count, max_atoms)
+ * are written: ext_home (home atom), ext_shift (n1, n2, n3; zero for home
+ * atoms), ext_xyz (R_home + n1 a1 + n2 a2 + n3 a3, bohr); call with
+ * max_atoms = 0 to size the arrays. */
+long long hfx_periodic_extend(const double* atom_xyz, int n_atoms, const double* lattice, double r_ext,
+                              long long max_atoms, int* ext_home, int* ext_shift, double* ext_xyz);
+
+/* Distance pattern (host only): every pair of the n_atoms atoms at most r_cut
+ * bohr apart, and every diagonal pair, as CSR with columns ascending.
+ * Returns the number of pairs, -1 on bad input.  row_ptr (n_atoms + 1 ints)
+ * and col (first max_nnz pairs) may be NULL: call once to size col.  On a
+ * periodic cell's extended atoms with r_cut the density cutoff this is the
+ * pattern of the real-space density P^{H-N} (Eq. dm at the Gamma point) and of
+ * the exchange rows. */
+long long hfx_distance_pattern(const double* atom_xyz, int n_atoms, double r_cut, int* row_ptr, int* col,
+                               long long max_nnz);
 
 /* Image table: every translate R_a + n1 a1 + n2 a2 + n3 a3 (n != 0) of a home
  * atom a lying within r_ext (bohr) of at least one home atom.

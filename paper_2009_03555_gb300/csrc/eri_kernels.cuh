@@ -52,6 +52,12 @@ struct SysArgs {
   int n_atoms;
   int n_pairs[6];           // entries of pairs[c]
   long long n_prims[6];     // entries of prims[c]
+  // Periodic cell as an extended atom set: its home atoms and their shells
+  // come first (equal to n_atoms and ns for a molecule).  Only quartets with a
+  // home-cell shell are evaluated: they are the ones that reach the home rows
+  // K^G_{mu lambda} (mu in the home cell, Sec. 2, Eq. H-HFX).
+  int n_home_atoms;
+  int n_home_shells;
 };
 
 struct BuildArgs {
@@ -278,6 +284,8 @@ __device__ __forceinline__ void scatter_K(const SysArgs& a, int sA, int sB, int 
 // exact skip when every P block it touches is zero) and precision routing.
 __device__ __forceinline__ bool keep_quartet(const BuildArgs& a, const SysArgs& S, const PairRec& bra,
                                              const PairRec& ket) {
+  const int nh = S.n_home_shells;
+  if (min(min(bra.A, bra.B), min(ket.A, ket.B)) >= nh) return false;  // no home-cell shell
   const double qq = bra.Q * ket.Q;
   double pscr = 0.0;
   if (a.screen || a.route) {

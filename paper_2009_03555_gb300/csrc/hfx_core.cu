@@ -74,6 +74,11 @@ static inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t
 struct hfx_basis_s {
   int device = 0;
   int n_shells = 0, n_atoms = 0, nbf = 0, max_nprim = 0;
+  // Home cell of a periodic basis (the first n_home_atoms atoms and their
+  // n_home_shells shells; the images follow); a molecule is all home.
+  int n_home_atoms = 0, n_home_shells = 0;
+  std::vector<int> h_ext_home, h_ext_shift;  // per atom: home atom and lattice shift (n1, n2, n3)
+  std::vector<double> h_atom_xyz;            // atom positions (bohr)
   std::vector<int> h_l, h_atom, h_np, h_poff, h_loc, h_atom_nf;
   std::vector<long long> h_sh_foff, h_atom_foff;
   DBuf<double> sh_xyz, alpha, coef, boys;
@@ -400,56 +405,6 @@ __global__ void k_desc_fill(int nb, int nk, const PairRec* bra, const PairRec* k
   }
 }
 
-// Pmax per shell pair, max |P_ij| over i in I, j in J (Sec. 2, density
-// screening; computed every build from the current P).
-__global__ void k_pmax(int ns, int na, const int* sh_atom, const int* sh_loc, const int* l, const int* atom_nf,
-                       const long long* blk_off, const double* P, double* pmax) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (long long)ns * ns) return;
-  const int I = (int)(t / ns), J = (int)(t % ns);
-  const long long o = blk_off[sh_atom[I] * na + sh_atom[J]];
-  double mx = 0.0;
-  if (o >= 0) {
-    const int nI = (l[I] + 1) * (l[I] + 2) / 2, nJ = (l[J] + 1) * (l[J] + 2) / 2;
-    const int nfJ = atom_nf[sh_atom[J]];
-    for (int a = 0; a < nI; ++a)
-      for (int b = 0; b < nJ; ++b) mx = fmax(mx, fabs(P[o + (long long)(sh_loc[I] + a) * nfJ + sh_loc[J] + b]));
-  }
-  pmax[t] = mx;
-}
-
-// K = K' + K'^T over the pattern: the scatter adds four of the eight
-// permutations of each canonical quartet; the other four are the transposes.
-__global__ void k_symmetrize(int n_blocks, const int* bx, const int* by, const long long* boff, int na,
-                             const long long* blk_off, const int* atom_nf, double* K) {
-  const int b = blockIdx.x;
-  if (b >= n_blocks) return;
-  const int X = bx[b], Y = by[b];
-  if (X > Y) return;
-  const int nX = atom_nf[X], nY = atom_nf[Y];
-  const long long oXY = boff[b];
-  if (X == Y) {
-    for (int e = threadIdx.x; e < nX * nX; e += blockDim.x) {
-      const int r = e / nX, c = e % nX;
-      if (r < c) {
-        const double s = K[oXY + r * nX + c] + K[oXY + c * nX + r];
-        K[oXY + r * nX + c] = s;
-        K[oXY + c * nX + r] = s;
-      } else if (r == c) {
-        K[oXY + r * nX + r] *= 2.0;
-      }
-    }
-  } else {
-    const long long oYX = blk_off[Y * na + X];
-    for (int e = threadIdx.x; e < nX * nY; e += blockDim.x) {
-      const int r = e / nY, c = e % nY;
-      const double s = K[oXY + r * nY + c] + K[oYX + c * nX + r];
-      K[oXY + r * nY + c] = s;
-      K[oYX + c * nX + r] = s;
-    }
-  }
-}
-
 // sum_i P_i K_i (FP64), block reduction then one atomicAdd per block.  `vec`:
 // both arrays 16-byte aligned, read as double2.
 __global__ void k_dot(long long n, const double* __restrict__ P, const double* __restrict__ K, int vec,
@@ -537,6 +492,8 @@ __global__ void k_pmax_b(const SysArgs* sys, double* const* pmax) {
 
 // K = K' + K'^T over each system's pattern (the scatter adds four of the
 // eight permutations of a canonical quartet; the other four are transposes).
+// Rows of image atoms of a periodic cell (atoms from n_home_atoms on) are set
+// to zero: they only received the partial sums of the home-cell quartets.
 __global__ void k_sym_b(const SysArgs* sys) {
   const SysArgs& S = sys[blockIdx.y];
   const int b = blockIdx.x;
@@ -546,15 +503,16 @@ __global__ void k_sym_b(const SysArgs* sys) {
   const int nX = S.atom_nf[X], nY = S.atom_nf[Y];
   const long long oXY = S.blk_val_off[b];
   double* K = S.K;
+  const double keepX = X < S.n_home_atoms ? 1.0 : 0.0, keepY = Y < S.n_home_atoms ? 1.0 : 0.0;
   if (X == Y) {
     for (int e = threadIdx.x; e < nX * nX; e += blockDim.x) {
       const int r = e / nX, c = e % nX;
       if (r < c) {
-        const double v = K[oXY + r * nX + c] + K[oXY + c * nX + r];
+        const double v = keepX * (K[oXY + r * nX + c] + K[oXY + c * nX + r]);
         K[oXY + r * nX + c] = v;
         K[oXY + c * nX + r] = v;
       } else if (r == c) {
-        K[oXY + r * nX + r] *= 2.0;
+        K[oXY + r * nX + r] *= 2.0 * keepX;
       }
     }
   } else {
@@ -562,8 +520,8 @@ __global__ void k_sym_b(const SysArgs* sys) {
     for (int e = threadIdx.x; e < nX * nY; e += blockDim.x) {
       const int r = e / nY, c = e % nY;
       const double v = K[oXY + r * nY + c] + K[oYX + c * nX + r];
-      K[oXY + r * nY + c] = v;
-      K[oYX + c * nX + r] = v;
+      K[oXY + r * nY + c] = keepX * v;
+      K[oYX + c * nX + r] = keepY * v;
     }
   }
 }
@@ -629,6 +587,8 @@ static void fill_sys(hfx_quartets_s* q) {
   S.n_blocks = q->n_blocks;
   S.ns = b->n_shells;
   S.n_atoms = q->n_atoms;
+  S.n_home_atoms = b->n_home_atoms;
+  S.n_home_shells = b->n_home_shells;
 }
 
 static hfx_status plan_alloc(Plan& pl, const std::vector<hfx_quartets_s*>& m, int n_sm) {
@@ -937,6 +897,12 @@ hfx_status hfx_create_basis(const hfx_shell_desc* shells, int n_shells, const do
   b->h_sh_foff.resize(n_shells + 1);
   for (int i = 0; i < n_shells; ++i) b->h_sh_foff[i] = b->h_atom_foff[b->h_atom[i]] + b->h_loc[i];
   b->h_sh_foff[n_shells] = b->nbf;
+  b->n_home_atoms = n_atoms;
+  b->n_home_shells = n_shells;
+  b->h_atom_xyz.assign(atom_xyz, atom_xyz + 3 * (size_t)n_atoms);
+  b->h_ext_home.resize(n_atoms);
+  for (int a = 0; a < n_atoms; ++a) b->h_ext_home[a] = a;
+  b->h_ext_shift.assign(3 * (size_t)n_atoms, 0);
   cudaError_t e = cudaSuccess;
   if ((e = upload(b->sh_xyz, xyz, s)) != cudaSuccess || (e = upload(b->alpha, alpha, s)) != cudaSuccess ||
       (e = upload(b->coef, coef, s)) != cudaSuccess || (e = upload(b->sh_l, b->h_l, s)) != cudaSuccess ||
@@ -963,6 +929,61 @@ hfx_status hfx_create_basis(const hfx_shell_desc* shells, int n_shells, const do
 }
 
 void hfx_destroy_basis(hfx_basis* b) { delete b; }
+
+hfx_status hfx_create_basis_periodic(const hfx_shell_desc* shells, int n_shells, const double* atom_xyz, int n_atoms,
+                                     const double* lattice, double r_ext, void* stream, hfx_basis** out) {
+  if (!out) return fail(HFX_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (n_shells <= 0 || n_atoms <= 0 || !shells || !atom_xyz || !lattice)
+    return fail(HFX_ERR_INVALID_ARG, "need at least one shell, one atom and the lattice");
+  for (int i = 0; i < n_shells; ++i)
+    if (shells[i].atom < 0 || shells[i].atom >= n_atoms || (i > 0 && shells[i].atom < shells[i - 1].atom))
+      return fail(HFX_ERR_INVALID_ARG, "shells must be grouped by atom in increasing atom order");
+  // extended set: home atoms, then the images (hfx_periodic_extend)
+  const long long n_ext = hfx_periodic_extend(atom_xyz, n_atoms, lattice, r_ext, 0, nullptr, nullptr, nullptr);
+  if (n_ext < 0) return HFX_ERR_INVALID_ARG;  // message set by hfx_periodic_extend
+  if (n_ext > (1LL << 24)) return fail(HFX_ERR_UNSUPPORTED, "too many images");
+  std::vector<int> ext_home((size_t)n_ext), ext_shift(3 * (size_t)n_ext);
+  std::vector<double> xyz(3 * (size_t)n_ext);
+  if (hfx_periodic_extend(atom_xyz, n_atoms, lattice, r_ext, n_ext, ext_home.data(), ext_shift.data(), xyz.data()) !=
+      n_ext)
+    return fail(HFX_ERR_INVALID_ARG, "extended set changed between calls");
+  // every image carries its home atom's shells
+  std::vector<int> first((size_t)n_atoms + 1, n_shells);
+  for (int i = n_shells - 1; i >= 0; --i) first[(size_t)shells[i].atom] = i;
+  for (int a = n_atoms - 1; a >= 0; --a)
+    if (first[(size_t)a] > first[(size_t)a + 1]) first[(size_t)a] = first[(size_t)a + 1];
+  std::vector<hfx_shell_desc> ext(shells, shells + n_shells);
+  for (long long X = n_atoms; X < n_ext; ++X) {
+    const int h = ext_home[(size_t)X];
+    for (int S = first[(size_t)h]; S < first[(size_t)h + 1]; ++S) {
+      hfx_shell_desc d = shells[S];
+      d.atom = (int)X;
+      ext.push_back(d);
+    }
+  }
+  hfx_basis* b = nullptr;
+  const hfx_status st = hfx_create_basis(ext.data(), (int)ext.size(), xyz.data(), (int)n_ext, stream, &b);
+  if (st != HFX_OK) return st;
+  b->n_home_atoms = n_atoms;
+  b->n_home_shells = n_shells;
+  b->h_ext_home = ext_home;
+  b->h_ext_shift = ext_shift;
+  *out = b;
+  return HFX_OK;
+}
+
+int hfx_basis_atoms(const hfx_basis* b, int* n_home_atoms, int* ext_home, int* ext_shift) {
+  if (!b) {
+    fail(HFX_ERR_INVALID_ARG, "NULL basis");
+    return -1;
+  }
+  if (n_home_atoms) *n_home_atoms = b->n_home_atoms;
+  if (ext_home) std::copy(b->h_ext_home.begin(), b->h_ext_home.end(), ext_home);
+  if (ext_shift) std::copy(b->h_ext_shift.begin(), b->h_ext_shift.end(), ext_shift);
+  return b->n_atoms;
+}
+
 
 static hfx_status setup_pattern(hfx_quartets_s* q, const hfx_pattern* pat, cudaStream_t s) {
   hfx_basis* b = q->basis;

@@ -6,16 +6,18 @@
 // auxiliary supercell.  Here the supercell is an extended atom set: the home
 // atoms followed by the images (translates of home atoms by lattice vectors)
 // that lie within r_ext of some home atom.  Each image carries its home atom's
-// shells.  The sum above is then the molecular exchange of the extended set
-// (the row of mu^0 and the column of lambda^G), so the molecular path builds
-// it unchanged; these functions produce the image table and lay the
+// shells.  The sum above is then the row of mu^0 (column lambda^G) of the
+// molecular exchange of the extended set; a periodic basis
+// (hfx_create_basis_periodic, hfx_core.cu) evaluates only the quartets with a
+// home-cell shell, which are the ones that reach those rows.  These functions
+// produce the image table, the extended set, the distance pattern and lay the
 // real-space density P^{H-N} onto the extended pattern.
 //
 // Real-space density at the Gamma point (Eq. dm with one k-point): the
 // caller's pattern over the extended atoms decides where P^{H-N} is nonzero
-// (normally the atom pairs within a distance cutoff).  Every block (X, Y) of
-// that pattern receives the home-cell density block of the home atoms of X
-// and Y.
+// (normally the atom pairs within a distance cutoff, hfx_distance_pattern).
+// Every block (X, Y) of that pattern receives the home-cell density block of
+// the home atoms of X and Y.
 #include <algorithm>
 #include <cmath>
 #include <string>
@@ -105,6 +107,54 @@ long long hfx_periodic_images(const double* atom_xyz, int n_atoms, const double*
         }
       }
   return count;
+}
+
+long long hfx_periodic_extend(const double* atom_xyz, int n_atoms, const double* lattice, double r_ext,
+                              long long max_atoms, int* ext_home, int* ext_shift, double* ext_xyz) {
+  if (max_atoms > 0 && (!ext_home || !ext_shift || !ext_xyz))
+    return periodic_fail("hfx_periodic_extend: NULL output arrays");
+  const long long n_img = hfx_periodic_images(atom_xyz, n_atoms, lattice, r_ext, 0, nullptr, nullptr);
+  if (n_img < 0) return -1;  // message set by hfx_periodic_images
+  const long long n_ext = n_atoms + n_img;
+  if (max_atoms <= 0) return n_ext;
+  std::vector<int> atom((size_t)std::max<long long>(n_img, 1)), shift(3 * (size_t)std::max<long long>(n_img, 1));
+  if (n_img > 0 && hfx_periodic_images(atom_xyz, n_atoms, lattice, r_ext, n_img, atom.data(), shift.data()) != n_img)
+    return periodic_fail("hfx_periodic_extend: image table changed between calls");
+  for (long long X = 0; X < n_ext && X < max_atoms; ++X) {
+    const bool home = X < n_atoms;
+    const int h = home ? (int)X : atom[(size_t)(X - n_atoms)];
+    const int* n = home ? nullptr : &shift[3 * (size_t)(X - n_atoms)];
+    ext_home[X] = h;
+    for (int k = 0; k < 3; ++k) {
+      ext_shift[3 * X + k] = home ? 0 : n[k];
+      // R_X = R_h + n1 a1 + n2 a2 + n3 a3 (lattice vectors as rows)
+      ext_xyz[3 * X + k] = atom_xyz[3 * h + k] +
+                           (home ? 0.0 : n[0] * lattice[k] + n[1] * lattice[3 + k] + n[2] * lattice[6 + k]);
+    }
+  }
+  return n_ext;
+}
+
+long long hfx_distance_pattern(const double* atom_xyz, int n_atoms, double r_cut, int* row_ptr, int* col,
+                               long long max_nnz) {
+  if (!atom_xyz || n_atoms <= 0 || !(r_cut >= 0.0) || !std::isfinite(r_cut))
+    return periodic_fail("hfx_distance_pattern: NULL coordinates, no atoms or a bad cutoff");
+  const double r2 = r_cut * r_cut;
+  long long nnz = 0;
+  if (row_ptr) row_ptr[0] = 0;
+  for (int X = 0; X < n_atoms; ++X) {
+    for (int Y = 0; Y < n_atoms; ++Y) {
+      double d2 = 0.0;
+      for (int k = 0; k < 3; ++k) d2 += (atom_xyz[3 * X + k] - atom_xyz[3 * Y + k]) * (atom_xyz[3 * X + k] - atom_xyz[3 * Y + k]);
+      if (d2 <= r2 || X == Y) {
+        if (col && nnz < max_nnz) col[nnz] = Y;
+        ++nnz;
+      }
+    }
+    if (nnz > (1LL << 31) - 1) return periodic_fail("hfx_distance_pattern: more than 2^31 - 1 pairs");
+    if (row_ptr) row_ptr[X + 1] = (int)nnz;
+  }
+  return nnz;
 }
 
 hfx_status hfx_periodic_pack_host(const hfx_shell_desc* shells, int n_shells, int n_home_atoms, const int* ext_home,

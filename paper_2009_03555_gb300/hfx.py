@@ -83,6 +83,7 @@ EXPORTED = ["hfx_create_basis", "hfx_build_quartets", "hfx_value_count", "hfx_bu
             "hfx_pack_dense_host", "hfx_setup_bytes_estimate", "hfx_server_create", "hfx_server_submit",
             "hfx_server_step", "hfx_server_poll", "hfx_server_release", "hfx_server_get_info", "hfx_server_destroy",
             "hfx_server_cancel", "hfx_server_inject_setup_failure", "hfx_periodic_images", "hfx_periodic_pack_host",
+            "hfx_create_basis_periodic", "hfx_basis_atoms", "hfx_periodic_extend", "hfx_distance_pattern",
             "hfx_destroy_basis", "hfx_destroy_quartets", "hfx_last_error"]
 
 _lib = None
@@ -164,9 +165,14 @@ def load(path: str = LIB_PATH):
     lib.hfx_server_destroy.restype = None
     lib.hfx_periodic_images.argtypes = [V, I, V, D, LL, V, V]
     lib.hfx_periodic_pack_host.argtypes = [ctypes.POINTER(ShellDesc), I, I, V, ctypes.POINTER(Pattern), V, V]
+    lib.hfx_create_basis_periodic.argtypes = [ctypes.POINTER(ShellDesc), I, V, I, V, D, V, PV]
+    lib.hfx_basis_atoms.argtypes = [V, V, V, V]
+    lib.hfx_periodic_extend.argtypes = [V, I, V, D, LL, V, V, V]
+    lib.hfx_distance_pattern.argtypes = [V, I, D, V, V, LL]
     for name in EXPORTED:
         if name in ("hfx_quartets_device_bytes", "hfx_basis_device_bytes", "hfx_pattern_value_count",
-                    "hfx_setup_bytes_estimate", "hfx_periodic_images"):
+                    "hfx_setup_bytes_estimate", "hfx_periodic_images", "hfx_periodic_extend",
+                    "hfx_distance_pattern"):
             getattr(lib, name).restype = LL
         elif name not in ("hfx_value_count", "hfx_destroy_basis", "hfx_destroy_quartets", "hfx_last_error",
                           "hfx_batch_destroy", "hfx_server_destroy"):
@@ -372,10 +378,10 @@ class Quartets:
     """Owns an hfx_quartets (screened quartet lists + work queue) for one
     basis, options and atom-pair pattern."""
 
-    def __init__(self, basis: Basis, opts: Opts, mask, stream=None):
+    def __init__(self, basis, opts: Opts, mask=None, stream=None, csr=None):
         self.basis = basis
         self.opts = opts
-        row_ptr, col = pattern_from_mask(mask)
+        row_ptr, col = csr if csr is not None else pattern_from_mask(mask)
         self.handle = hfx_build_quartets(basis.handle, opts, row_ptr, col, stream)
         self.n_values = hfx_value_count(self.handle)
 
@@ -499,71 +505,121 @@ def hfx_periodic_images(atom_xyz, lattice, r_ext):
     return atom[:n], shift[:n]
 
 
-class ExtendedSystem:
-    """Flat shell arrays of a periodic cell's extended atom set: the home atoms,
-    then the images, each with its home atom's shells at the translated centre."""
+class ExtendedLayout:
+    """Function layout of a periodic cell's extended atom set (from the
+    library's ``ext_home``): every extended atom carries its home atom's
+    functions, so only counts and offsets are derived here."""
 
     def __init__(self, home, ext_home, ext_xyz):
-        sa = np.asarray(home.shell_atom)
-        s0 = np.searchsorted(sa, np.arange(home.n_atoms + 1))  # home atom -> its shell range
-        src = np.concatenate([np.arange(s0[h], s0[h + 1]) for h in ext_home])
-        self.atom_xyz = np.ascontiguousarray(ext_xyz, dtype=np.float64)
-        self.atom_Z = np.asarray(home.atom_Z)[ext_home]
-        self.shell_atom = np.repeat(np.arange(len(ext_home), dtype=np.int32), np.diff(s0)[ext_home])
-        self.shell_l = np.asarray(home.shell_l, dtype=np.int32)[src]
-        po = np.asarray(home.prim_off)
-        n_p = (po[1:] - po[:-1])[src]
-        self.prim_off = np.concatenate([[0], np.cumsum(n_p)]).astype(np.int32)
-        take = np.concatenate([np.arange(po[S], po[S + 1]) for S in src])
-        self.alpha = np.asarray(home.alpha, dtype=np.float64)[take]
-        self.coef = np.asarray(home.coef, dtype=np.float64)[take]
-        nf = (self.shell_l + 1) * (self.shell_l + 2) // 2
-        self.func_off = np.concatenate([[0], np.cumsum(nf)]).astype(np.int64)
-        af = np.zeros(len(ext_home) + 1, dtype=np.int64)
-        np.add.at(af, self.shell_atom + 1, nf)
-        self.atom_func_off = np.cumsum(af)
-        self.n_atoms, self.n_shells, self.n_bf = len(ext_home), len(self.shell_l), int(self.func_off[-1])
+        nf_home = np.diff(np.asarray(home.atom_func_off))
+        ns_home = np.bincount(np.asarray(home.shell_atom), minlength=home.n_atoms)
+        self.atom_xyz = ext_xyz
+        self.n_atoms = len(ext_home)
+        self.n_shells = int(ns_home[ext_home].sum())
+        self.atom_func_off = np.concatenate([[0], np.cumsum(nf_home[ext_home])]).astype(np.int64)
+        self.n_bf = int(self.atom_func_off[-1])
 
 
 class Periodic:
-    """A periodic system handed to the molecular path as its extended atom set
-    (Sec. 2, Eq. H-HFX; see the periodic section of hfx.h).
+    """A periodic cell (Sec. 2, Eq. H-HFX; see the periodic section of hfx.h).
 
     ``system``: the home cell (flat shell arrays, shells grouped by atom);
-    ``lattice``: 3 x 3 lattice vectors as rows (bohr).  Images within ``r_ext``
-    of a home atom join the set; the density pattern is every pair of extended
-    atoms at most ``r_P`` apart.  ``system`` (extended), ``mask`` and
-    ``pack`` feed ``Basis``/``Quartets``; the first ``n_home_bf`` rows of the
-    extended K are K^G, and the first ``n_home_values`` values are the home
-    rows (the per-cell exchange energy)."""
+    ``lattice``: 3 x 3 lattice vectors as rows (bohr).  The library builds the
+    extended atom set (images within ``r_ext`` of a home atom,
+    hfx_periodic_extend) and the density pattern (extended atoms at most
+    ``r_P`` apart, hfx_distance_pattern); ``basis()`` creates the device basis
+    (hfx_create_basis_periodic), whose quartet lists evaluate only quartets with
+    a home-cell shell.  The first ``n_home_bf`` rows of K are K^G (the first
+    ``n_home_values`` values), the image rows are zero, and hfx_exchange_energy
+    gives the exchange energy per cell."""
 
     def __init__(self, system, lattice, r_ext=10.0, r_P=14.0):
+        lib = load()
         self.home = system
         self.lattice = np.ascontiguousarray(lattice, dtype=np.float64).reshape(3, 3)
+        self.r_ext, self.r_P = float(r_ext), float(r_P)
+        xyz = np.ascontiguousarray(system.atom_xyz, dtype=np.float64)
         n_home = int(system.n_atoms)
-        atom, shift = hfx_periodic_images(system.atom_xyz, self.lattice, r_ext)
-        self.ext_home = np.concatenate([np.arange(n_home), atom]).astype(np.int32)
-        self.ext_shift = np.vstack([np.zeros((n_home, 3), dtype=np.int32), shift]).astype(np.int32)
-        ext_xyz = np.asarray(system.atom_xyz, dtype=np.float64)[self.ext_home] + self.ext_shift @ self.lattice
-        self.system = ExtendedSystem(system, self.ext_home, ext_xyz)
-        d = np.linalg.norm(ext_xyz[:, None, :] - ext_xyz[None, :, :], axis=-1)
-        self.mask = d <= r_P
-        self._inp = _SystemInput(self.system, self.mask)
+        n = lib.hfx_periodic_extend(_ptr(xyz), n_home, _ptr(self.lattice), self.r_ext, 0, None, None, None)
+        if n < 0:
+            raise HFXError(1, lib.hfx_last_error().decode(errors="replace"))
+        self.ext_home = np.zeros(n, dtype=np.int32)
+        self.ext_shift = np.zeros((n, 3), dtype=np.int32)
+        ext_xyz = np.zeros((n, 3))
+        m = lib.hfx_periodic_extend(_ptr(xyz), n_home, _ptr(self.lattice), self.r_ext, int(n), _ptr(self.ext_home),
+                                    _ptr(self.ext_shift), _ptr(ext_xyz))
+        assert m == n
+        self.system = ExtendedLayout(system, self.ext_home, ext_xyz)
+        nnz = lib.hfx_distance_pattern(_ptr(ext_xyz), int(n), self.r_P, None, None, 0)
+        if nnz < 0:
+            raise HFXError(1, lib.hfx_last_error().decode(errors="replace"))
+        self.row_ptr = np.zeros(n + 1, dtype=np.int32)
+        self.col = np.zeros(max(int(nnz), 1), dtype=np.int32)
+        lib.hfx_distance_pattern(_ptr(ext_xyz), int(n), self.r_P, _ptr(self.row_ptr), _ptr(self.col), int(nnz))
+        self.col = self.col[:nnz]
+        self.pattern = Pattern()
+        self.pattern.n_atoms, self.pattern.row_ptr, self.pattern.col = int(n), self.row_ptr.ctypes.data, \
+            self.col.ctypes.data
         self._home_descs, self._home_keep = shell_descs(system.shell_l, system.shell_atom, system.prim_off,
                                                         system.alpha, system.coef)
-        self.n_values = self._inp.value_count()
         nfa = np.diff(self.system.atom_func_off)
+        self.n_values = int(sum(nfa[X] * nfa[self.col[self.row_ptr[X]:self.row_ptr[X + 1]]].sum()
+                                for X in range(n)))
         self.n_home_bf = int(nfa[:n_home].sum())
-        self.n_home_values = int(sum(nfa[X] * nfa[self.mask[X]].sum() for X in range(n_home)))
+        self.n_home_values = int(sum(nfa[X] * nfa[self.col[self.row_ptr[X]:self.row_ptr[X + 1]]].sum()
+                                     for X in range(n_home)))
+
+    @property
+    def mask(self) -> np.ndarray:
+        """The density pattern as a dense boolean atom-pair matrix."""
+        n = len(self.ext_home)
+        m = np.zeros((n, n), dtype=bool)
+        for X in range(n):
+            m[X, self.col[self.row_ptr[X]:self.row_ptr[X + 1]]] = True
+        return m
+
+    def basis(self, stream=None) -> "PeriodicBasis":
+        return PeriodicBasis(self, stream)
+
+    def quartets(self, opts: Opts, stream=None) -> "Quartets":
+        """Basis and quartet lists of the cell on its density pattern."""
+        return Quartets(self.basis(stream), opts, csr=(self.row_ptr, self.col), stream=stream)
 
     def pack(self, P_home) -> np.ndarray:
         """Values of the real-space density on the extended pattern (host)."""
         P = np.ascontiguousarray(P_home, dtype=np.float64)
         out = np.empty(self.n_values)
         _check(load().hfx_periodic_pack_host(self._home_descs, len(self.home.shell_l), int(self.home.n_atoms),
-                                             _ptr(self.ext_home), ctypes.byref(self._inp.pattern), _ptr(P),
+                                             _ptr(self.ext_home), ctypes.byref(self.pattern), _ptr(P),
                                              _ptr(out)))
         return out
+
+
+class PeriodicBasis:
+    """Owns the hfx_basis of a periodic cell (hfx_create_basis_periodic)."""
+
+    def __init__(self, per: Periodic, stream=None):
+        lib = load()
+        home = per.home
+        descs, _keep = shell_descs(home.shell_l, home.shell_atom, home.prim_off, home.alpha, home.coef)
+        xyz = np.ascontiguousarray(home.atom_xyz, dtype=np.float64)
+        h = ctypes.c_void_p()
+        _check(lib.hfx_create_basis_periodic(descs, len(home.shell_l), _ptr(xyz), int(home.n_atoms),
+                                             _ptr(per.lattice), per.r_ext, _stream(stream), ctypes.byref(h)))
+        self.handle = h
+        self.nbf = per.system.n_bf
+        nh = ctypes.c_int()
+        n = lib.hfx_basis_atoms(h, ctypes.byref(nh), None, None)
+        self.ext_home = np.zeros(n, dtype=np.int32)
+        self.ext_shift = np.zeros((n, 3), dtype=np.int32)
+        lib.hfx_basis_atoms(h, None, _ptr(self.ext_home), _ptr(self.ext_shift))
+        self.n_home_atoms = nh.value
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and _lib is not None:
+            _lib.hfx_destroy_basis(h)
+            self.handle = None
 
 
 class Server:

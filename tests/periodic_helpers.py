@@ -34,3 +34,25 @@ def formed_blocks_error(K_rows, per, ref_blocks, home_func_off):
             else:
                 outside = max(outside, float(np.abs(K_rows[rows, cols]).max()))
     return err, outside, n_formed
+
+
+def extended_system(per):
+    """The extended atom set of a ``hfx.Periodic`` as a plain molecular system
+    (every extended atom with its home atom's shells at its own centre), built
+    from the library's ext_home and extended coordinates; lets the oracle's
+    molecular exchange, or the library's molecular path, run on the same set."""
+    import synth
+    home = per.home
+    sa = np.asarray(home.shell_atom)
+    s0 = np.searchsorted(sa, np.arange(home.n_atoms + 1))
+    src = np.concatenate([np.arange(s0[h], s0[h + 1]) for h in per.ext_home])
+    po = np.asarray(home.prim_off)
+    n_p = (po[1:] - po[:-1])[src]
+    take = np.concatenate([np.arange(po[S], po[S + 1]) for S in src])
+    return synth.System(name=home.name + "_ext", atom_Z=np.asarray(home.atom_Z)[per.ext_home],
+                        atom_xyz=np.ascontiguousarray(per.system.atom_xyz),
+                        shell_atom=np.repeat(np.arange(len(per.ext_home), dtype=np.int32), np.diff(s0)[per.ext_home]),
+                        shell_l=np.asarray(home.shell_l, dtype=np.int32)[src],
+                        prim_off=np.concatenate([[0], np.cumsum(n_p)]).astype(np.int32),
+                        alpha=np.asarray(home.alpha, dtype=np.float64)[take],
+                        coef=np.asarray(home.coef, dtype=np.float64)[take])

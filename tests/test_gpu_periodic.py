@@ -1,7 +1,9 @@
 """GPU parity of periodic systems: the exchange rows K^G_{mu lambda} of the
-home cell (Sec. 2, Eq. H-HFX) built by the CUDA path on the extended atom set
-(hfx_periodic_images, hfx_periodic_pack_host, then hfx_build_K), against the
-oracle's brute-force lattice sum over its own image set.
+home cell (Sec. 2, Eq. H-HFX) built by the CUDA path on the library's extended
+atom set (hfx_create_basis_periodic, hfx_distance_pattern,
+hfx_periodic_pack_host, then hfx_build_K with only the quartets that have a
+home-cell shell), against the oracle's brute-force lattice sum over its own
+image set.
 
 The library forms K on the pattern of P only (the pairs of extended atoms at
 most r_P apart), so the rows are compared on those blocks and must be zero on
@@ -14,7 +16,7 @@ import pytest
 
 import oracle
 import synth
-from periodic_helpers import formed_blocks_error
+from periodic_helpers import extended_system, formed_blocks_error
 
 pytestmark = pytest.mark.gpu
 
@@ -30,18 +32,21 @@ def gpu_periodic(s, P, A, r_ext, r_P, **opt_kw):
     from paper_2009_03555_gb300 import hfx
 
     per = hfx.Periodic(s, A, r_ext=r_ext, r_P=r_P)
-    q = hfx.Quartets(hfx.Basis(per.system), hfx.make_opts(**opt_kw), per.mask)
+    q = per.quartets(hfx.make_opts(**opt_kw))
     assert q.n_values == per.n_values
     dev = torch.device("cuda")
     Pv = torch.from_numpy(per.pack(P)).to(dev)
     Kv = torch.empty_like(Pv)
     q.build_K(Pv, Kv)
-    E = torch.zeros(1, dtype=torch.float64, device=dev)
-    hfx.hfx_exchange_energy_noalloc(Pv, Kv, per.n_home_values, E)  # the home rows are the value prefix
+    E = q.exchange_energy(Pv, Kv)  # image rows are zero: the energy per cell
+    E_pre = torch.zeros(1, dtype=torch.float64, device=dev)
+    hfx.hfx_exchange_energy_noalloc(Pv, Kv, per.n_home_values, E_pre)  # the home rows are the value prefix
     Kd = torch.empty((per.system.n_bf, per.system.n_bf), dtype=torch.float64, device=dev)
     q.unpack(Kv, Kd)
     torch.cuda.synchronize()
-    return Kd[:per.n_home_bf].cpu().numpy(), float(E.item()), per
+    assert abs(E - float(E_pre.item())) <= 1e-13 * abs(E)
+    assert float(Kv[per.n_home_values:].abs().max()) == 0.0  # rows of image atoms
+    return Kd[:per.n_home_bf].cpu().numpy(), E, per
 
 
 def oracle_rows_by_key(s, P, A, r_ext, r_P, **kw):
@@ -95,3 +100,31 @@ def test_periodic_energy_mixed():
     _, E, _ = gpu_periodic(s, P, SKEW, 5.0, 4.0, kernel=hfx.HFX_KERNEL_ERFC, precision=hfx.HFX_PREC_MIXED)
     _, E_ref = oracle_rows_by_key(s, P, SKEW, 5.0, 4.0, **KW["erfc"])
     assert abs(E - E_ref) <= 1e-6, (E, E_ref)
+
+
+def test_home_cell_quartets_only():
+    """The periodic basis evaluates only the quartets with a home-cell shell:
+    fewer than the molecular exchange of the same extended set (library's
+    molecular path on the same shells and pattern), with the same home rows
+    (the skipped quartets reach image rows only)."""
+    import torch
+    from paper_2009_03555_gb300 import hfx
+    s = synth.periodic_cell(3, SKEW, sub=34, recipe=D_RECIPE)
+    P = synth.periodic_density_matrix(s, cutoff=4.0, sub=34)
+    per = hfx.Periodic(s, SKEW, r_ext=6.0, r_P=4.0)
+    opts = hfx.make_opts(kernel=hfx.HFX_KERNEL_ERFC, screen=True, density_screen=True,
+                         precision=hfx.HFX_PREC_FP64)
+    dev = torch.device("cuda")
+    Pv = torch.from_numpy(per.pack(P)).to(dev)
+    qp = per.quartets(opts)
+    Kp = torch.empty_like(Pv)
+    qp.build_K(Pv, Kp)
+    qm = hfx.Quartets(hfx.Basis(extended_system(per)), opts, per.mask)
+    Km = torch.empty_like(Pv)
+    qm.build_K(Pv, Km)
+    torch.cuda.synchronize()
+    n_p, n_m = sum(qp.stats().n_quartets_computed), sum(qm.stats().n_quartets_computed)
+    assert 0 < n_p < n_m
+    h = per.n_home_values
+    scale = float(Km[:h].abs().max())
+    assert float((Kp[:h] - Km[:h]).abs().max()) <= 1e-12 * scale

@@ -13,7 +13,7 @@ import pytest
 
 import oracle
 import synth
-from periodic_helpers import formed_blocks_error
+from periodic_helpers import extended_system, formed_blocks_error
 
 SKEW = np.array([[6.0, 0.0, 0.0], [1.0, 6.0, 0.0], [0.0, 1.0, 6.0]])
 FCC = 7.0 * np.array([[0.0, 0.5, 0.5], [0.5, 0.0, 0.5], [0.5, 0.5, 0.0]])
@@ -95,8 +95,14 @@ def test_extended_set_and_density_reproduce_oracle_rows(hfx, opts, A, n_atoms, r
     s = synth.periodic_cell(n_atoms, A, sub=22, recipe=D_RECIPE)
     P = synth.periodic_density_matrix(s, cutoff=r_P, sub=22)
     per = hfx.Periodic(s, A, r_ext=r_ext, r_P=r_P)
-    e = per.system
-    assert per.n_home_bf == s.n_bf and e.n_atoms == len(per.ext_home)
+    e = extended_system(per)
+    assert per.n_home_bf == s.n_bf and e.n_atoms == len(per.ext_home) == per.system.n_atoms
+    np.testing.assert_array_equal(e.atom_func_off, per.system.atom_func_off)
+    assert e.n_shells == per.system.n_shells and e.n_bf == per.system.n_bf
+    # the library's extended coordinates and density pattern
+    np.testing.assert_allclose(per.system.atom_xyz, s.atom_xyz[per.ext_home] + per.ext_shift @ A, rtol=0, atol=1e-12)
+    d = np.linalg.norm(e.atom_xyz[:, None, :] - e.atom_xyz[None, :, :], axis=-1)
+    np.testing.assert_array_equal(per.mask, d <= r_P)
     Pv = per.pack(P)
     Pe = unpack(e, per.mask, Pv)
     np.testing.assert_array_equal(Pe, Pe.T)
@@ -118,6 +124,7 @@ def test_extended_set_and_density_reproduce_oracle_rows(hfx, opts, A, n_atoms, r
     # what the GPU test sees: K kept on the pattern only (the library forms no
     # other block), compared on the formed blocks with zeros required elsewhere
     Kv = hfx._SystemInput(e, per.mask).pack(Km)
+    assert len(Kv) == per.n_values
     Kpat = unpack(e, per.mask, Kv)[:s.n_bf]
     ref = {k: Kref[:, col[k][0]:col[k][1]] for k in keys}
     err, outside, n_formed = formed_blocks_error(Kpat, per, ref, s.atom_func_off)
