@@ -191,7 +191,8 @@ def run_ours(args, rank, world):
     prec = hfx.HFX_PREC_MIXED if args.precision == "mixed" else hfx.HFX_PREC_FP64
     opts = hfx.make_opts(kernel=hfx.HFX_KERNEL_ERFC, omega=0.11, screen=True, tau=1e-8, density_screen=True,
                          eps=1e-8, prim_cutoff=args.prim_cutoff, precision=prec,
-                         fp64_promote_bound=args.promote, n_block=args.n_block, promote_min_l=args.promote_min_l)
+                         fp64_promote_bound=args.promote, n_block=args.n_block, promote_min_l=args.promote_min_l,
+                         prim_density_screen=bool(args.prim_dscreen))
     basis = hfx.Basis(s)
     q = hfx.Quartets(basis, opts, mask)
     Pd = torch.from_numpy(P).to(dev)
@@ -245,6 +246,31 @@ def run_ours(args, rank, world):
             te.append(time.perf_counter() - t0)
         e2e = {"value": world * 1.0 / (sum(te) / len(te)), "unit": "builds/s",
                "h2d_bytes_per_step": int(q.n_values * 8), "d2h_bytes_per_step": int(q.n_values * 8 + 8)}
+
+    # the metric's comparison: one plain FP64 build of the same workload
+    # (outside the timed region), its time, and the mixed result's error
+    # against it (energy and the largest |dK| element)
+    fp64 = None
+    if prec == hfx.HFX_PREC_MIXED and not args.no_fp64_check:
+        opts64 = hfx.make_opts(kernel=hfx.HFX_KERNEL_ERFC, omega=0.11, screen=True, tau=1e-8, density_screen=True,
+                               eps=1e-8, prim_cutoff=args.prim_cutoff, precision=hfx.HFX_PREC_FP64,
+                               n_block=args.n_block)
+        q64 = hfx.Quartets(basis, opts64, mask)
+        K64 = torch.empty_like(Kv)
+        q.build_K(Pv, Kv)  # the mixed K of the same P
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        q64.build_K(Pv, K64)
+        E64 = q64.exchange_energy(Pv, K64)
+        e1.record(stream)
+        e1.synchronize()
+        fp64 = {"fp64_ms_per_build": e0.elapsed_time(e1), "E_x_fp64": E64, "dE_x_vs_fp64": E - E64,
+                "max_abs_dK_vs_fp64": float((Kv - K64).abs().max()), "max_abs_K": float(K64.abs().max()),
+                "quartets_fp64": int(sum(q64.stats().n_quartets_computed)),
+                "mixed_speedup_vs_fp64": e0.elapsed_time(e1) / ms}
+        del q64, K64
+        st = q.stats()
 
     # roofline of the dominant kernel (largest device time in the last build)
     best = None
@@ -314,6 +340,7 @@ def run_ours(args, rank, world):
         "gpu_launches": args.steps * (5 + sum(1 for p in range(2) for c in range(hfx.N_CLASSES)
                                             if st.n_quartets_pass[p][c] > 0 or st.ms_class_pass[p][c] > 0)),
         "clocks": clocks, "e2e": e2e, "roofline": roof, "per_class": per_class,
+        "vs_fp64": fp64,
     }
     return res, s, q
 
@@ -397,7 +424,8 @@ def run_serve(args):
     promote = args.promote if prec == hfx.HFX_PREC_MIXED else math.inf
     opts = hfx.make_opts(kernel=hfx.HFX_KERNEL_ERFC, omega=0.11, screen=True, tau=1e-8, density_screen=True,
                          eps=1e-8, prim_cutoff=args.prim_cutoff, precision=prec, n_block=args.n_block,
-                         fp64_promote_bound=promote, promote_min_l=args.promote_min_l)
+                         fp64_promote_bound=promote, promote_min_l=args.promote_min_l,
+                         prim_density_screen=bool(args.prim_dscreen))
     reqs = []
     for i, (k, na) in enumerate(zip(kinds, sizes)):
         s = synth.ch_chain(na, sub=i) if k == 0 else synth.ch_slab(na, sub=i)
@@ -473,7 +501,8 @@ def run_batch(args):
     promote = args.promote if prec == hfx.HFX_PREC_MIXED else math.inf
     opts = hfx.make_opts(kernel=hfx.HFX_KERNEL_ERFC, omega=0.11, screen=True, tau=1e-8, density_screen=True,
                          eps=1e-8, prim_cutoff=args.prim_cutoff, precision=prec, n_block=args.n_block,
-                         fp64_promote_bound=promote, promote_min_l=args.promote_min_l)
+                         fp64_promote_bound=promote, promote_min_l=args.promote_min_l,
+                         prim_density_screen=bool(args.prim_dscreen))
     mem = []
     for i, na in enumerate(sizes):
         s = synth.ch_cluster(int(na), 3, sub=i)
@@ -546,7 +575,8 @@ def run_periodic(args):
     promote = args.promote if prec == hfx.HFX_PREC_MIXED else math.inf
     opts = hfx.make_opts(kernel=hfx.HFX_KERNEL_ERFC, omega=0.11, screen=True, tau=1e-8, density_screen=True,
                          eps=1e-8, prim_cutoff=args.prim_cutoff, precision=prec, fp64_promote_bound=promote,
-                         n_block=args.n_block, promote_min_l=args.promote_min_l)
+                         n_block=args.n_block, promote_min_l=args.promote_min_l,
+                         prim_density_screen=bool(args.prim_dscreen))
     t0 = time.perf_counter()
     q = per.quartets(opts)
     torch.cuda.synchronize()
@@ -602,7 +632,8 @@ def run_incremental(args):
     promote = args.promote if prec == hfx.HFX_PREC_MIXED else math.inf
     opts = hfx.make_opts(kernel=hfx.HFX_KERNEL_ERFC, omega=0.11, screen=True, tau=1e-8, density_screen=True,
                          eps=1e-8, prim_cutoff=args.prim_cutoff, precision=prec, fp64_promote_bound=promote,
-                         n_block=args.n_block, promote_min_l=args.promote_min_l)
+                         n_block=args.n_block, promote_min_l=args.promote_min_l,
+                         prim_density_screen=bool(args.prim_dscreen))
     q = hfx.Quartets(hfx.Basis(s), opts, mask)
 
     def values(P):
@@ -653,10 +684,11 @@ def run_precision_check(args):
     dev = torch.device("cuda")
     s, P, mask = workload(args.atoms)
 
-    def one(prec, promote, min_l=0):
+    def one(prec, promote, min_l=0, pds=False):
         opts = hfx.make_opts(kernel=hfx.HFX_KERNEL_ERFC, omega=0.11, screen=True, tau=1e-8, density_screen=True,
                              eps=1e-8, prim_cutoff=args.prim_cutoff, precision=prec,
-                             fp64_promote_bound=promote, n_block=args.n_block, promote_min_l=min_l)
+                             fp64_promote_bound=promote, n_block=args.n_block, promote_min_l=min_l,
+                             prim_density_screen=pds)
         b = hfx.Basis(s)
         q = hfx.Quartets(b, opts, mask)
         Pv = torch.empty(q.n_values, dtype=torch.float64, device=dev)
@@ -672,22 +704,26 @@ def run_precision_check(args):
         st = q.stats()
         n1 = sum(st.n_quartets_pass[1])
         n = sum(st.n_quartets_computed)
+        one.n_pq = int(sum(st.n_prim_quartets_pass[0]) + sum(st.n_prim_quartets_pass[1]))
         return E, Kv.cpu().numpy(), dt, (n1 / n if n else 0.0)
 
+    n_pq64 = None
     if args.fp64_energy is None:
         E64, K64, t64, _ = one(hfx.HFX_PREC_FP64, math.inf)
+        n_pq64 = one.n_pq
     else:  # FP64 energy of an earlier run of the same workload (energies only)
         E64, K64, t64 = args.fp64_energy, None, None
     rows = []
     for item in args.promote_sweep.split(","):  # bound, or bound:min_l
         b, _, ml = item.partition(":")
         b, ml = float(b), int(ml or 0)
-        E, K, dt, frac = one(hfx.HFX_PREC_MIXED, b, ml)
+        E, K, dt, frac = one(hfx.HFX_PREC_MIXED, b, ml, bool(args.prim_dscreen))
         rows.append({"promote": _json_num(b), "promote_min_l": ml, "E_x": E, "abs_dE_x": abs(E - E64),
                      "max_abs_dK": float(np.abs(K - K64).max()) if K64 is not None else None,
-                     "s": dt, "fp64_quartet_share": frac})
-    return {"check": "mixed_vs_fp64", "atoms": args.atoms, "prim_cutoff": args.prim_cutoff, "E_x_fp64": E64,
-            "s_fp64": t64, "max_abs_K": float(np.abs(K64).max()) if K64 is not None else None, "mixed": rows}
+                     "s": dt, "fp64_quartet_share": frac, "prim_quartets": one.n_pq})
+    return {"check": "mixed_vs_fp64", "atoms": args.atoms, "prim_cutoff": args.prim_cutoff,
+            "prim_dscreen_mixed": bool(args.prim_dscreen), "E_x_fp64": E64,
+            "s_fp64": t64, "prim_quartets_fp64": n_pq64, "max_abs_K": float(np.abs(K64).max()) if K64 is not None else None, "mixed": rows}
 
 
 def main():
@@ -703,10 +739,14 @@ def main():
     ap.add_argument("--promote", type=float, default=1e-5)
     ap.add_argument("--promote-min-l", type=int, default=8, help="promotion only in classes of total l >= this")
     ap.add_argument("--prim-cutoff", type=float, default=1e-13)
+    ap.add_argument("--prim-dscreen", type=int, default=0,
+                    help="1: the primitive cutoff applies to bound_ab bound_cd P_scr (density-weighted)")
     ap.add_argument("--n-block", type=int, default=128)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    ap.add_argument("--no-fp64-check", action="store_true",
+                    help="skip the FP64 build after the timed steps (mixed vs FP64 time and error)")
     ap.add_argument("--ref-quartets-per-build", type=float, default=None)
     ap.add_argument("--serve", action="store_true", help="continuous-batching serving stream instead of one build")
     ap.add_argument("--serve-requests", type=int, default=48)

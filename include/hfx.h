@@ -81,7 +81,9 @@ typedef struct {
   double fp64_promote_bound;  /* MIXED: quartets with Q_IJ Q_KL P_scr above this run in FP64 */
   int n_block;                /* quartets per work-queue batch (the paper's n_block, Sec. 4); 0 = default */
   int promote_min_l;          /* MIXED: promotion only in classes with la+lb+lc+ld >= this (0: every class) */
-  int reserved[2];
+  int prim_density_screen;    /* 1: prim_cutoff applies to bound_ab bound_cd P_scr (the largest |P| the quartet
+                                 contracts with, Eq. dmscreening) instead of bound_ab bound_cd */
+  int reserved;
 } hfx_opts;
 
 /* Atom-pair block pattern: CSR over atoms (host arrays). */

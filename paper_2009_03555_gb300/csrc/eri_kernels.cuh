@@ -78,6 +78,7 @@ struct BuildArgs {
   int dscreen;            // density screening on
   double eps;             // density-screening threshold
   float eps_prim;         // primitive quartets with bound_ab bound_cd below this are skipped
+  int prim_dscreen;       // 1: the primitive cutoff applies to bound_ab bound_cd P_scr instead
   int route;              // 0: all quartets, 1: only bound <= promote, 2: only bound > promote
   double promote;         // FP64 promotion bound on Q_AB Q_CD P_scr
   unsigned long long* n_done;  // [0] quartets computed, [1] primitive quartets computed
@@ -280,6 +281,26 @@ __device__ __forceinline__ void scatter_K(const SysArgs& a, int sA, int sB, int 
   }
 }
 
+// P_scr of quartet (AB|CD): the largest |P| over the four exchange blocks
+// AC, AD, BC, BD it contracts with (Sec. 2, Eq. dmscreening).
+__device__ __forceinline__ double quartet_pscr(const SysArgs& S, const PairRec& bra, const PairRec& ket) {
+  const double* pm = S.pmax;
+  const int ns = S.ns;
+  return fmax(fmax(__ldg(pm + bra.A * ns + ket.A), __ldg(pm + bra.A * ns + ket.B)),
+              fmax(__ldg(pm + bra.B * ns + ket.A), __ldg(pm + bra.B * ns + ket.B)));
+}
+
+// Primitive cutoff of one quartet.  A primitive quartet adds at most about
+// bound_ab bound_cd |P| to any K element, so with prim_dscreen the cutoff is
+// applied to that product (the density screening of Eq. dmscreening carried
+// down to primitives): eps_prim / P_scr on the bound product.
+__device__ __forceinline__ float quartet_prim_cutoff(const BuildArgs& a, const SysArgs& S, const PairRec& bra,
+                                                     const PairRec& ket) {
+  if (!a.prim_dscreen) return a.eps_prim;
+  const double pscr = quartet_pscr(S, bra, ket);
+  return pscr > 0.0 ? (float)fmin((double)a.eps_prim / pscr, 3.0e38) : 3.0e38f;
+}
+
 // Screening of quartet (bra | ket k) (Sec. 2: Eq. schwarz and Eq. dmscreening;
 // exact skip when every P block it touches is zero) and precision routing.
 __device__ __forceinline__ bool keep_quartet(const BuildArgs& a, const SysArgs& S, const PairRec& bra,
@@ -288,12 +309,7 @@ __device__ __forceinline__ bool keep_quartet(const BuildArgs& a, const SysArgs& 
   if (min(min(bra.A, bra.B), min(ket.A, ket.B)) >= nh) return false;  // no home-cell shell
   const double qq = bra.Q * ket.Q;
   double pscr = 0.0;
-  if (a.screen || a.route) {
-    const double* pm = S.pmax;
-    const int ns = S.ns;
-    pscr = fmax(fmax(__ldg(pm + bra.A * ns + ket.A), __ldg(pm + bra.A * ns + ket.B)),
-                fmax(__ldg(pm + bra.B * ns + ket.A), __ldg(pm + bra.B * ns + ket.B)));
-  }
+  if (a.screen || a.route) pscr = quartet_pscr(S, bra, ket);
   if (a.screen) {
     if (!(qq > a.tau) || !(pscr > 0.0)) return false;
     if (a.dscreen && !(pscr * qq > a.eps)) return false;
@@ -334,7 +350,8 @@ __global__ void __launch_bounds__(kThreadsK) k_build_K(const BuildArgs a) {
     R out[C::NOUT];
     pdone += (unsigned long long)contracted_quartet<C, R>(bra, S.prims[a.bra_class], ket, S.prims[a.ket_class],
                                                           a.boys, a.boysf, a.kernel, a.omega2,
-                                                          ds{a.omega2_hi, a.omega2_lo}, a.eps_prim, out);
+                                                          ds{a.omega2_hi, a.omega2_lo},
+                                                          quartet_prim_cutoff(a, S, bra, ket), out);
     scatter_K<C, R>(S, bra.A, bra.B, ket.A, ket.B, out, fac);
     ++done;
   };
@@ -671,7 +688,9 @@ template <class C, typename R>
 __device__ __forceinline__ void coop_quartet(const BuildArgs& a, const SysArgs& S, int bi, int ki, R* ws, R* pbuf,
                                              R* sg, unsigned long long& pdone) {
   const PairRec bra = S.pairs[a.bra_class][bi], ket = S.pairs[a.ket_class][ki];
-  coop_accumulate<C, R>(eri_params(a), bra, S.prims[a.bra_class], ket, S.prims[a.ket_class], ws, pbuf, sg, pdone);
+  EriParams ep = eri_params(a);
+  ep.eps_prim = quartet_prim_cutoff(a, S, bra, ket);
+  coop_accumulate<C, R>(ep, bra, S.prims[a.bra_class], ket, S.prims[a.ket_class], ws, pbuf, sg, pdone);
   quartet_epilogue<C, R>(a, S, bra, ket, bi, ki, ws, pbuf);
 }
 
@@ -885,6 +904,7 @@ __global__ void __launch_bounds__(SplitShape<C, R>::THREADS, SplitShape<C, R>::M
   // current shell quartet
   bool have = false;
   int bi = 0, ki = 0, bpoff = 0, kpoff = 0, nk = 1, total = 0, t0 = 0, qn = 0;
+  float eps_q = a.eps_prim;  // primitive cutoff of the current quartet
 #ifdef HFX_SPLIT_SMEM_ACC
   R* const acc = Lay::acc_base(ws) + lane * Lay::ACC_STRIDE;
   R* const comp = acc + 32 * Lay::ACC_STRIDE;
@@ -907,6 +927,7 @@ __global__ void __launch_bounds__(SplitShape<C, R>::THREADS, SplitShape<C, R>::M
 #endif
         bpoff = bra.poff;
         kpoff = ket.poff;
+        eps_q = quartet_prim_cutoff(a, S, bra, ket);
         nk = ket.pcnt > 0 ? ket.pcnt : 1;
         total = bra.pcnt * ket.pcnt;
         t0 = 0;
@@ -953,7 +974,7 @@ __global__ void __launch_bounds__(SplitShape<C, R>::THREADS, SplitShape<C, R>::M
         bool valid = false;
         if (t < total) {
           const int ib = t / nk, ik = t - ib * nk;
-          valid = bprims[bpoff + ib].bound * kprims[kpoff + ik].bound >= a.eps_prim;
+          valid = bprims[bpoff + ib].bound * kprims[kpoff + ik].bound >= eps_q;
         }
         const unsigned m = __ballot_sync(0xffffffffu, valid);
         if (valid) pq[qn + __popc(m & ((1u << lane) - 1u))] = t;

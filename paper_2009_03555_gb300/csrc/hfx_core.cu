@@ -716,6 +716,7 @@ static BuildArgs plan_args(Plan& pl, int cls) {
   a.dscreen = o.density_screen;
   a.eps = o.eps;
   a.eps_prim = (float)o.prim_cutoff;
+  a.prim_dscreen = o.prim_density_screen;
   a.promote = o.fp64_promote_bound;
   a.route = 0;
   a.counter = nullptr;

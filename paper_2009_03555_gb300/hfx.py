@@ -46,7 +46,7 @@ class Opts(ctypes.Structure):
                 ("tau", ctypes.c_double), ("density_screen", ctypes.c_int), ("eps", ctypes.c_double),
                 ("prim_cutoff", ctypes.c_double), ("precision", ctypes.c_int),
                 ("fp64_promote_bound", ctypes.c_double), ("n_block", ctypes.c_int),
-                ("promote_min_l", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
+                ("promote_min_l", ctypes.c_int), ("prim_density_screen", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
 class Pattern(ctypes.Structure):
@@ -241,7 +241,7 @@ def hfx_create_basis(shell_l, shell_atom, prim_off, alpha, coef, atom_xyz, strea
 
 def make_opts(kernel=HFX_KERNEL_ERFC, omega=0.11, screen=True, tau=1e-8, density_screen=True, eps=None,
               prim_cutoff=1e-15, precision=HFX_PREC_FP64, fp64_promote_bound=math.inf, n_block=128,
-              promote_min_l=0) -> Opts:
+              promote_min_l=0, prim_density_screen=False) -> Opts:
     o = Opts()
     o.kernel, o.omega, o.screen, o.tau = int(kernel), float(omega), int(bool(screen)), float(tau)
     o.density_screen = int(bool(density_screen))
@@ -249,6 +249,7 @@ def make_opts(kernel=HFX_KERNEL_ERFC, omega=0.11, screen=True, tau=1e-8, density
     o.prim_cutoff, o.precision = float(prim_cutoff), int(precision)
     o.fp64_promote_bound, o.n_block = float(fp64_promote_bound), int(n_block)
     o.promote_min_l = int(promote_min_l)
+    o.prim_density_screen = int(bool(prim_density_screen))
     return o
 
 
