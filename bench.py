@@ -192,7 +192,7 @@ def run_ours(args, rank, world):
     opts = hfx.make_opts(kernel=hfx.HFX_KERNEL_ERFC, omega=0.11, screen=True, tau=1e-8, density_screen=True,
                          eps=1e-8, prim_cutoff=args.prim_cutoff, precision=prec,
                          fp64_promote_bound=args.promote, n_block=args.n_block, promote_min_l=args.promote_min_l,
-                         prim_density_screen=bool(args.prim_dscreen))
+                         prim_density_screen=bool(args.prim_dscreen), promote_prims=bool(args.promote_prims))
     basis = hfx.Basis(s)
     q = hfx.Quartets(basis, opts, mask)
     Pd = torch.from_numpy(P).to(dev)
@@ -202,8 +202,14 @@ def run_ours(args, rank, world):
     del Pd
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
 
+    shard = world > 1 and not args.replicas
+
     def step():
-        q.build_K(Pv, Kv)
+        if shard:  # this rank's share of the batches, then the sum all-reduce of K (Algorithm 4)
+            q.build_K_shard(Pv, Kv, rank, world)
+            torch.distributed.all_reduce(Kv)
+        else:
+            q.build_K(Pv, Kv)
         return q.exchange_energy(Pv, Kv)
 
     for _ in range(args.warmup):
@@ -239,19 +245,18 @@ def run_ours(args, rank, world):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             Pv.copy_(Ph, non_blocking=True)
-            q.build_K(Pv, Kv)
-            q.exchange_energy(Pv, Kv)
+            step()
             Kh.copy_(Kv, non_blocking=True)
             torch.cuda.synchronize()
             te.append(time.perf_counter() - t0)
-        e2e = {"value": world * 1.0 / (sum(te) / len(te)), "unit": "builds/s",
+        e2e = {"value": (1 if shard else world) * 1.0 / (sum(te) / len(te)), "unit": "builds/s",
                "h2d_bytes_per_step": int(q.n_values * 8), "d2h_bytes_per_step": int(q.n_values * 8 + 8)}
 
     # the metric's comparison: one plain FP64 build of the same workload
     # (outside the timed region), its time, and the mixed result's error
     # against it (energy and the largest |dK| element)
     fp64 = None
-    if prec == hfx.HFX_PREC_MIXED and not args.no_fp64_check:
+    if prec == hfx.HFX_PREC_MIXED and not args.no_fp64_check and world == 1:
         opts64 = hfx.make_opts(kernel=hfx.HFX_KERNEL_ERFC, omega=0.11, screen=True, tau=1e-8, density_screen=True,
                                eps=1e-8, prim_cutoff=args.prim_cutoff, precision=hfx.HFX_PREC_FP64,
                                n_block=args.n_block)
@@ -317,10 +322,14 @@ def run_ours(args, rank, world):
                                   "alu_frac": round(frac, 4)})
     n_q = int(sum(st.n_quartets_computed))
     n_pq = int(sum(st.n_prim_quartets_pass[0]) + sum(st.n_prim_quartets_pass[1]))
+    if shard:  # this rank's share: the build's counts are the sums over the ranks
+        t = torch.tensor([n_q, n_pq], dtype=torch.int64, device=dev)
+        torch.distributed.all_reduce(t)
+        n_q, n_pq = int(t[0]), int(t[1])
     res = {
-        "metric": "hfx_builds_per_s", "value": world * 1000.0 / ms, "unit": "builds/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if prec == hfx.HFX_PREC_MIXED else "f64",
+        "metric": "hfx_builds_per_s", "value": (1 if shard else world) * 1000.0 / ms, "unit": "builds/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "strong" if shard else "weak", "vs_baseline": None, "dtype": "f32+f64" if prec == hfx.HFX_PREC_MIXED else "f64",
         "data": "synthetic",
         "config": {"workload": f"{args.atoms}-atom C/H cluster, HSE erfc w=0.11, Schwarz 1e-8 + density screening, "
                                f"P cut 14 bohr, {args.precision}"
@@ -330,9 +339,11 @@ def run_ours(args, rank, world):
                    "atoms": args.atoms, "n_bf": int(s.n_bf), "precision": args.precision,
                    "fp64_promote_bound": _json_num(args.promote), "promote_min_l": args.promote_min_l,
                    "n_block": args.n_block, "prim_cutoff": args.prim_cutoff,
-                   "l2": "flushed (256 MB write) between timed steps", "parallelism": f"replicas x{world}"},
+                   "l2": "flushed (256 MB write) between timed steps",
+                   "parallelism": (f"sharded x{world}: interleaved work-queue batches, NCCL sum all-reduce of K"
+                                   if shard else f"replicas x{world}")},
         "quartets_per_build": n_q, "prim_quartets_per_build": n_pq,
-        "eri_quartets_per_s": world * n_q / (ms * 1e-3),
+        "eri_quartets_per_s": (1 if shard else world) * n_q / (ms * 1e-3),
         "E_x": E, "setup_ms": st.ms_setup,
         "setup_phase_ms": dict(zip(("pairs", "schwarz", "sorted_lists", "work_queues"),
                                    (round(x, 3) for x in st.ms_setup_phase))),
@@ -345,7 +356,7 @@ def run_ours(args, rank, world):
     return res, s, q
 
 
-def run_cpu_oracle(args, sample_atoms=10, bra_stride=2, full_quartets=None):
+def run_cpu_oracle(args, sample_atoms=10, bra_stride=4, full_quartets=None):
     """The oracle (as it stands) on a bounded sample: the `sample_atoms` atoms of
     the workload nearest its centre, every `bra_stride`-th canonical bra pair.
     Returns quartets/s and cores used."""
@@ -390,7 +401,7 @@ def run_reference(args, rank, world):
         vals.append((qps, dt, n))
     qps = sum(v[0] for v in vals) / len(vals)
     value = qps / qpb
-    sample = (f"oracle on the 10 atoms nearest the centre of the {args.atoms}-atom cluster, every 2nd canonical "
+    sample = (f"oracle on the 10 atoms nearest the centre of the {args.atoms}-atom cluster, every 4th canonical "
               f"bra pair ({vals[-1][2]} quartets, {vals[-1][1]:.1f} s per step); builds/s = quartets/s / "
               f"{qpb:.4g} quartets per full build")
     return {"impl": "reference", "metric": "hfx_builds_per_s", "value": value, "unit": "builds/s", "n_gpus": world,
@@ -425,7 +436,7 @@ def run_serve(args):
     opts = hfx.make_opts(kernel=hfx.HFX_KERNEL_ERFC, omega=0.11, screen=True, tau=1e-8, density_screen=True,
                          eps=1e-8, prim_cutoff=args.prim_cutoff, precision=prec, n_block=args.n_block,
                          fp64_promote_bound=promote, promote_min_l=args.promote_min_l,
-                         prim_density_screen=bool(args.prim_dscreen))
+                         prim_density_screen=bool(args.prim_dscreen), promote_prims=bool(args.promote_prims))
     reqs = []
     for i, (k, na) in enumerate(zip(kinds, sizes)):
         s = synth.ch_chain(na, sub=i) if k == 0 else synth.ch_slab(na, sub=i)
@@ -502,7 +513,7 @@ def run_batch(args):
     opts = hfx.make_opts(kernel=hfx.HFX_KERNEL_ERFC, omega=0.11, screen=True, tau=1e-8, density_screen=True,
                          eps=1e-8, prim_cutoff=args.prim_cutoff, precision=prec, n_block=args.n_block,
                          fp64_promote_bound=promote, promote_min_l=args.promote_min_l,
-                         prim_density_screen=bool(args.prim_dscreen))
+                         prim_density_screen=bool(args.prim_dscreen), promote_prims=bool(args.promote_prims))
     mem = []
     for i, na in enumerate(sizes):
         s = synth.ch_cluster(int(na), 3, sub=i)
@@ -576,7 +587,7 @@ def run_periodic(args):
     opts = hfx.make_opts(kernel=hfx.HFX_KERNEL_ERFC, omega=0.11, screen=True, tau=1e-8, density_screen=True,
                          eps=1e-8, prim_cutoff=args.prim_cutoff, precision=prec, fp64_promote_bound=promote,
                          n_block=args.n_block, promote_min_l=args.promote_min_l,
-                         prim_density_screen=bool(args.prim_dscreen))
+                         prim_density_screen=bool(args.prim_dscreen), promote_prims=bool(args.promote_prims))
     t0 = time.perf_counter()
     q = per.quartets(opts)
     torch.cuda.synchronize()
@@ -633,7 +644,7 @@ def run_incremental(args):
     opts = hfx.make_opts(kernel=hfx.HFX_KERNEL_ERFC, omega=0.11, screen=True, tau=1e-8, density_screen=True,
                          eps=1e-8, prim_cutoff=args.prim_cutoff, precision=prec, fp64_promote_bound=promote,
                          n_block=args.n_block, promote_min_l=args.promote_min_l,
-                         prim_density_screen=bool(args.prim_dscreen))
+                         prim_density_screen=bool(args.prim_dscreen), promote_prims=bool(args.promote_prims))
     q = hfx.Quartets(hfx.Basis(s), opts, mask)
 
     def values(P):
@@ -684,11 +695,11 @@ def run_precision_check(args):
     dev = torch.device("cuda")
     s, P, mask = workload(args.atoms)
 
-    def one(prec, promote, min_l=0, pds=False):
+    def one(prec, promote, min_l=0, pds=False, pp=False):
         opts = hfx.make_opts(kernel=hfx.HFX_KERNEL_ERFC, omega=0.11, screen=True, tau=1e-8, density_screen=True,
                              eps=1e-8, prim_cutoff=args.prim_cutoff, precision=prec,
                              fp64_promote_bound=promote, n_block=args.n_block, promote_min_l=min_l,
-                             prim_density_screen=pds)
+                             prim_density_screen=pds, promote_prims=pp)
         b = hfx.Basis(s)
         q = hfx.Quartets(b, opts, mask)
         Pv = torch.empty(q.n_values, dtype=torch.float64, device=dev)
@@ -705,6 +716,7 @@ def run_precision_check(args):
         n1 = sum(st.n_quartets_pass[1])
         n = sum(st.n_quartets_computed)
         one.n_pq = int(sum(st.n_prim_quartets_pass[0]) + sum(st.n_prim_quartets_pass[1]))
+        one.n_pq1 = int(sum(st.n_prim_quartets_pass[1]))
         return E, Kv.cpu().numpy(), dt, (n1 / n if n else 0.0)
 
     n_pq64 = None
@@ -714,13 +726,16 @@ def run_precision_check(args):
     else:  # FP64 energy of an earlier run of the same workload (energies only)
         E64, K64, t64 = args.fp64_energy, None, None
     rows = []
-    for item in args.promote_sweep.split(","):  # bound, or bound:min_l
-        b, _, ml = item.partition(":")
-        b, ml = float(b), int(ml or 0)
-        E, K, dt, frac = one(hfx.HFX_PREC_MIXED, b, ml, bool(args.prim_dscreen))
-        rows.append({"promote": _json_num(b), "promote_min_l": ml, "E_x": E, "abs_dE_x": abs(E - E64),
+    for item in args.promote_sweep.split(","):  # bound, bound:min_l or bound:min_l:p (per primitive quartet)
+        b, _, rest = item.partition(":")
+        ml, _, pp = rest.partition(":")
+        b, ml, pp = float(b), int(ml or 0), pp == "p"
+        E, K, dt, frac = one(hfx.HFX_PREC_MIXED, b, ml, bool(args.prim_dscreen), pp)
+        rows.append({"promote": _json_num(b), "promote_min_l": ml, "promote_prims": pp, "E_x": E,
+                     "abs_dE_x": abs(E - E64),
                      "max_abs_dK": float(np.abs(K - K64).max()) if K64 is not None else None,
-                     "s": dt, "fp64_quartet_share": frac, "prim_quartets": one.n_pq})
+                     "s": dt, "fp64_quartet_share": frac, "prim_quartets": one.n_pq,
+                     "fp64_prim_quartets": one.n_pq1})
     return {"check": "mixed_vs_fp64", "atoms": args.atoms, "prim_cutoff": args.prim_cutoff,
             "prim_dscreen_mixed": bool(args.prim_dscreen), "E_x_fp64": E64,
             "s_fp64": t64, "prim_quartets_fp64": n_pq64, "max_abs_K": float(np.abs(K64).max()) if K64 is not None else None, "mixed": rows}
@@ -739,10 +754,14 @@ def main():
     ap.add_argument("--promote", type=float, default=1e-5)
     ap.add_argument("--promote-min-l", type=int, default=8, help="promotion only in classes of total l >= this")
     ap.add_argument("--prim-cutoff", type=float, default=1e-13)
+    ap.add_argument("--promote-prims", type=int, default=0,
+                    help="1: FP64 promotion per primitive quartet (bound_ab bound_cd P_scr above --promote)")
     ap.add_argument("--prim-dscreen", type=int, default=0,
                     help="1: the primitive cutoff applies to bound_ab bound_cd P_scr (density-weighted)")
     ap.add_argument("--n-block", type=int, default=128)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--replicas", action="store_true",
+                    help="with several GPUs: independent replicas of the build instead of one sharded build")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--no-fp64-check", action="store_true",
@@ -802,7 +821,7 @@ def main():
             qpb = res["quartets_per_build"]
             res["cpu_baseline"] = {"value": qps / qpb, "unit": "builds/s", "cores": nt, "kind": "oracle",
                                    "sample": f"oracle on the 10 atoms nearest the centre of the {args.atoms}-atom "
-                                             f"cluster, every 2nd canonical bra pair ({n} quartets in {dt:.1f} s, "
+                                             f"cluster, every 4th canonical bra pair ({n} quartets in {dt:.1f} s, "
                                              f"{qps:.4g} quartets/s), scaled by {qpb} quartets per full build"}
         print(json.dumps(res), flush=True)
     if world > 1:

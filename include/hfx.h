@@ -83,7 +83,9 @@ typedef struct {
   int promote_min_l;          /* MIXED: promotion only in classes with la+lb+lc+ld >= this (0: every class) */
   int prim_density_screen;    /* 1: prim_cutoff applies to bound_ab bound_cd P_scr (the largest |P| the quartet
                                  contracts with, Eq. dmscreening) instead of bound_ab bound_cd */
-  int reserved;
+  int promote_prims;          /* MIXED with promotion: 1 = promote per primitive quartet: of a quartet above
+                                 fp64_promote_bound only the primitive quartets with bound_ab bound_cd P_scr
+                                 above it run in FP64, the others in FP32 */
 } hfx_opts;
 
 /* Atom-pair block pattern: CSR over atoms (host arrays). */
@@ -148,6 +150,17 @@ long long hfx_value_count(const hfx_quartets* q);
  * evaluation with the fused exchange contraction, symmetrisation.  P_val, K_val:
  * device arrays of hfx_value_count() doubles.  Asynchronous on `stream`. */
 hfx_status hfx_build_K(hfx_quartets* q, const double* P_val, double* K_val, void* stream);
+
+/* One rank's share of a build sharded over n_ranks processes (one GPU each):
+ * the work-queue batches of every quartet class with index % n_ranks == rank,
+ * the interleaved static split of the paper's distributed construction
+ * (Sec. 3, Algorithms 3 and 4).  K_val receives the symmetrised exchange of
+ * that share (zeroed first); the sum of the K_val arrays over the ranks -- the
+ * sum all-reduce of Algorithm 4 (MPI_ALLREDUCE in the paper, NCCL here) -- is
+ * the K of hfx_build_K.  Every rank needs the whole P_val.  Asynchronous on
+ * `stream`; HFX_ERR_INVALID_ARG unless 0 <= rank < n_ranks. */
+hfx_status hfx_build_K_shard(hfx_quartets* q, const double* P_val, double* K_val, int rank, int n_ranks,
+                             void* stream);
 
 /* Incremental build: K_val += K(dP_val).  K is linear in the density
  * (Eq. H-HFX), so an SCF step n can form K(P_n) = K(P_{n-1}) + K(P_n - P_{n-1}).

@@ -63,7 +63,8 @@ struct SysArgs {
 struct BuildArgs {
   const SysArgs* sys;     // device table of systems
   const Desc* desc;       // batches of this quartet class (Desc::sys = system id)
-  int n_desc;
+  int n_desc;             // batches this launch takes: desc[desc_first + i * desc_stride], i < n_desc
+  int desc_first, desc_stride;  // one rank's share of a sharded build (0, 1: every batch)
   int n_sys;              // entries of sys
   int* counter;           // work-queue head (zeroed before the launch)
   int bra_class, ket_class;
@@ -81,6 +82,9 @@ struct BuildArgs {
   int prim_dscreen;       // 1: the primitive cutoff applies to bound_ab bound_cd P_scr instead
   int route;              // 0: all quartets, 1: only bound <= promote, 2: only bound > promote
   double promote;         // FP64 promotion bound on Q_AB Q_CD P_scr
+  int promote_prims;      // promotion per primitive quartet: route 1 takes every quartet and, in those
+                          // above the bound, the primitive quartets with bound_ab bound_cd P_scr <= promote;
+                          // route 2 the primitive quartets above it
   unsigned long long* n_done;  // [0] quartets computed, [1] primitive quartets computed
 };
 
@@ -92,10 +96,17 @@ struct EriParams {
   double omega2;
   ds w2;           // omega^2 as a double-single pair (mixed path)
   float eps_prim;  // primitive quartets with bound_ab bound_cd below this are skipped
+  float prim_hi;   // ... and those above this (the other pass of a promotion per primitive quartet)
+};
+
+// The primitive quartets of one quartet that a launch evaluates: bound
+// products bound_ab bound_cd in [lo, hi] (see quartet_prim_range).
+struct PrimRange {
+  float lo, hi;
 };
 
 __device__ __forceinline__ EriParams eri_params(const BuildArgs& a) {
-  return EriParams{a.boys, a.boysf, a.kernel, a.omega2, ds{a.omega2_hi, a.omega2_lo}, a.eps_prim};
+  return EriParams{a.boys, a.boysf, a.kernel, a.omega2, ds{a.omega2_hi, a.omega2_lo}, a.eps_prim, 3.0e38f};
 }
 
 struct SchwarzArgs {
@@ -131,14 +142,14 @@ struct EvalArgs {
 // (argument, prefactor, Boys function, erfc difference) is FP64; the
 // recursions, the contraction and the horizontal recursion run in R.
 // Primitive pairs are sorted by descending bound, so the loops stop at the
-// first primitive quartet whose bound product falls below eps_prim.
+// first primitive quartet whose bound product falls below the range (pr).
 // Returns the number of primitive quartets evaluated.
 template <class C, typename R>
 __device__ __forceinline__ int contracted_quartet(const PairRec& bra, const PrimPair* __restrict__ bprims,
                                                   const PairRec& ket, const PrimPair* __restrict__ kprims,
                                                   const double* __restrict__ boys,
                                                   const float* __restrict__ boysf, int kernel, double omega2,
-                                                  ds w2, float eps_prim, R* __restrict__ out) {
+                                                  ds w2, PrimRange pr, R* __restrict__ out) {
   constexpr bool kMixed = sizeof(R) == 4;
   constexpr int NR = kMixed ? 1 : 2;
   R acc[C::NACC], comp[C::NACC];
@@ -151,10 +162,12 @@ __device__ __forceinline__ int contracted_quartet(const PairRec& bra, const Prim
   const float kmax = ket.pcnt > 0 ? kprims[ket.poff].bound : 0.f;
   for (int ib = 0; ib < bra.pcnt; ++ib) {
     const PrimPair pb = bprims[bra.poff + ib];
-    if (pb.bound * kmax < eps_prim) break;
+    if (pb.bound * kmax < pr.lo) break;
     for (int ik = 0; ik < ket.pcnt; ++ik) {
       const PrimPair pk = kprims[ket.poff + ik];
-      if (pb.bound * pk.bound < eps_prim) break;
+      const float bb = pb.bound * pk.bound;
+      if (bb < pr.lo) break;
+      if (bb > pr.hi) continue;
       ++n;
       R G[C::L + 1], PQ[3], rinv;
       if constexpr (kMixed) {
@@ -301,6 +314,29 @@ __device__ __forceinline__ float quartet_prim_cutoff(const BuildArgs& a, const S
   return pscr > 0.0 ? (float)fmin((double)a.eps_prim / pscr, 3.0e38) : 3.0e38f;
 }
 
+// The range of primitive quartets a launch evaluates of one quartet.
+// Without promotion, or for a quartet below the promotion bound, [cutoff, inf).  With promotion per
+// primitive quartet, a quartet above the bound (Q_AB Q_CD P_scr > promote)
+// splits at thr = promote / P_scr: the FP32 launch takes [cutoff, thr], the
+// FP64 launch (thr, inf) and the cutoff; together every primitive quartet of
+// the cutoff's range runs exactly once.
+__device__ __forceinline__ PrimRange quartet_prim_range(const BuildArgs& a, const SysArgs& S, const PairRec& bra,
+                                                        const PairRec& ket) {
+  const float eps = quartet_prim_cutoff(a, S, bra, ket);
+  PrimRange r{eps, 3.0e38f};
+  if (a.promote_prims && a.route) {
+    const double pscr = quartet_pscr(S, bra, ket);
+    if (bra.Q * ket.Q * pscr > a.promote) {
+      const float thr = (float)fmin(a.promote / pscr, 3.0e38);
+      if (a.route == 1)
+        r.hi = thr;
+      else
+        r.lo = fmaxf(eps, nextafterf(thr, 3.4e38f));
+    }
+  }
+  return r;
+}
+
 // Screening of quartet (bra | ket k) (Sec. 2: Eq. schwarz and Eq. dmscreening;
 // exact skip when every P block it touches is zero) and precision routing.
 __device__ __forceinline__ bool keep_quartet(const BuildArgs& a, const SysArgs& S, const PairRec& bra,
@@ -316,10 +352,74 @@ __device__ __forceinline__ bool keep_quartet(const BuildArgs& a, const SysArgs& 
   }
   if (a.route) {
     const bool big = qq * pscr > a.promote;
+    if (a.promote_prims && a.route == 1) return true;  // big quartets split by primitive quartet
     return (a.route == 1) ? !big : big;
   }
   return true;
 }
+
+// Number of primitive quartets of (bra|ket) inside the range pr: the
+// primitive pairs are sorted by descending bound, so for each bra primitive
+// pair the kept ket primitive pairs are a prefix (a staircase).
+__device__ __forceinline__ int prim_quartet_count(const PrimPair* __restrict__ bp, const PairRec& bra,
+                                                  const PrimPair* __restrict__ kp, const PairRec& ket, PrimRange pr) {
+  const float kmax = ket.pcnt > 0 ? kp[ket.poff].bound : 0.f;
+  int n = 0;
+  for (int ib = 0; ib < bra.pcnt; ++ib) {
+    const float b = bp[bra.poff + ib].bound;
+    if (b * kmax < pr.lo) break;
+    for (int ik = 0; ik < ket.pcnt; ++ik) {
+      const float bb = b * kp[ket.poff + ik].bound;
+      if (bb < pr.lo) break;
+      if (bb <= pr.hi) ++n;
+    }
+  }
+  return n;
+}
+
+// Bitonic sort, descending, of the 32 * NPER keys of a warp; key position
+// p = 32 j + lane is held by `lane` in k[j].  Strides below 32 exchange
+// between lanes (shuffles), larger strides between a lane's registers.
+template <int NPER>
+__device__ __forceinline__ void warp_sort_desc(unsigned (&k)[NPER]) {
+  const int lane = threadIdx.x & 31;
+  constexpr int N = 32 * NPER;
+#pragma unroll
+  for (int size = 2; size <= N; size <<= 1) {
+#pragma unroll
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      if (stride >= 32) {
+        const int js = stride >> 5;
+#pragma unroll
+        for (int j = 0; j < NPER; ++j) {
+          if (j & js) continue;
+          const bool desc = ((j * 32) & size) == 0;
+          const unsigned a0 = k[j], a1 = k[j | js];
+          const unsigned hi = a0 > a1 ? a0 : a1, lo = a0 > a1 ? a1 : a0;
+          k[j] = desc ? hi : lo;
+          k[j | js] = desc ? lo : hi;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < NPER; ++j) {
+          const unsigned v = __shfl_xor_sync(0xffffffffu, k[j], stride);
+          const bool lower = (lane & stride) == 0;
+          const bool desc = ((j * 32 + lane) & size) == 0;
+          const unsigned hi = k[j] > v ? k[j] : v, lo = k[j] > v ? v : k[j];
+          k[j] = (lower == desc) ? hi : lo;
+        }
+      }
+    }
+  }
+}
+
+// Survivors a warp collects before it sorts and runs them (power of two,
+// 32..256).
+#ifndef HFX_SORT_CAP
+#define HFX_SORT_CAP 256
+#endif
+constexpr int kSortCap = HFX_SORT_CAP;
+static_assert(kSortCap >= 32 && kSortCap <= 256 && (kSortCap & (kSortCap - 1)) == 0, "HFX_SORT_CAP");
 
 // Persistent exchange-build kernel for one quartet class.  The device work
 // queue replaces the paper's master/sub-master/worker message passing
@@ -327,15 +427,22 @@ __device__ __forceinline__ bool keep_quartet(const BuildArgs& a, const SysArgs& 
 // with one atomicAdd on the queue head (the master handing out the indexes of
 // the batched ERIs); a head past the end is the terminal token.  The warp
 // screens the batch's quartets 32 at a time and appends the survivors to a
-// per-warp queue in shared memory (ballot + prefix count); whenever 32 are
-// queued, each lane takes one and runs the body of Algorithm 4 for it
-// (compute the shell quartet, accumulate into K).  Lanes therefore never idle
-// on screened-out quartets.
+// per-warp queue in shared memory (ballot + prefix count), so lanes never idle
+// on screened-out quartets.  Each lane runs one quartet at a time (the body of
+// Algorithm 4: compute the shell quartet, accumulate into K), and its loop
+// over primitive quartets stops at the primitive cutoff, so quartets differ
+// in length.  Once kSortCap survivors are queued the warp counts the
+// primitive quartets of each, sorts them by that count (bitonic, in
+// registers) and runs them in rounds of 32 in that order: the lanes of a
+// round then have quartets of nearly equal length.
 template <class C, typename R>
 __global__ void __launch_bounds__(kThreadsK) k_build_K(const BuildArgs a) {
-  __shared__ int4 s_queue[kWarpsK][64];
-  const int lane = threadIdx.x & 31;
-  int4* Qw = s_queue[threadIdx.x >> 5];
+  constexpr int NPER = kSortCap / 32;
+  __shared__ int4 s_queue[kWarpsK][kSortCap + 32];
+  __shared__ unsigned s_key[kWarpsK][kSortCap];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int4* Qw = s_queue[warp];
+  unsigned* Kw = s_key[warp];
   int qn = 0;
   unsigned long long done = 0, pdone = 0;
 
@@ -351,9 +458,39 @@ __global__ void __launch_bounds__(kThreadsK) k_build_K(const BuildArgs a) {
     pdone += (unsigned long long)contracted_quartet<C, R>(bra, S.prims[a.bra_class], ket, S.prims[a.ket_class],
                                                           a.boys, a.boysf, a.kernel, a.omega2,
                                                           ds{a.omega2_hi, a.omega2_lo},
-                                                          quartet_prim_cutoff(a, S, bra, ket), out);
+                                                          quartet_prim_range(a, S, bra, ket), out);
     scatter_K<C, R>(S, bra.A, bra.B, ket.A, ket.B, out, fac);
     ++done;
+  };
+
+  // the first m (<= kSortCap) queued quartets, longest first in rounds of 32
+  auto run_sorted = [&](int m) {
+    unsigned k[NPER];
+#pragma unroll
+    for (int j = 0; j < NPER; ++j) {
+      const int p = 32 * j + lane;
+      k[j] = 0u;  // padding sorts last
+      if (p < m) {
+        const int4 it = Qw[p];
+        const SysArgs& S = a.sys[it.x];
+        const PairRec bra = S.pairs[a.bra_class][it.y];
+        const PairRec ket = S.pairs[a.ket_class][it.z];
+        const int n = prim_quartet_count(S.prims[a.bra_class], bra, S.prims[a.ket_class], ket,
+                                         quartet_prim_range(a, S, bra, ket));
+        k[j] = ((unsigned)(n + 1) << 8) | (unsigned)p;
+      }
+    }
+    warp_sort_desc<NPER>(k);
+#pragma unroll
+    for (int j = 0; j < NPER; ++j) Kw[32 * j + lane] = k[j];
+    __syncwarp();
+    const int rounds = (m + 31) >> 5;
+#pragma unroll 1
+    for (int r = 0; r < rounds; ++r) {
+      const unsigned key = Kw[32 * r + lane];
+      if (key != 0u) process(Qw[key & 0xffu]);
+    }
+    __syncwarp();
   };
 
   for (;;) {
@@ -361,7 +498,7 @@ __global__ void __launch_bounds__(kThreadsK) k_build_K(const BuildArgs a) {
     if (lane == 0) d = atomicAdd(a.counter, 1);
     d = __shfl_sync(0xffffffffu, d, 0);
     if (d >= a.n_desc) break;
-    const Desc ds = a.desc[d];
+    const Desc ds = a.desc[a.desc_first + (long long)d * a.desc_stride];
     const SysArgs& S = a.sys[ds.sys];
     const PairRec bra = S.pairs[a.bra_class][ds.bra];
     const PairRec* __restrict__ kets = S.pairs[a.ket_class];
@@ -373,17 +510,15 @@ __global__ void __launch_bounds__(kThreadsK) k_build_K(const BuildArgs a) {
       if (ok) Qw[qn + __popc(m & ((1u << lane) - 1u))] = make_int4(ds.sys, ds.bra, k, 0);
       qn += __popc(m);
       __syncwarp();
-      if (qn >= 32) {
-        const int4 it = Qw[lane];
+      if (qn >= kSortCap) {
+        run_sorted(kSortCap);
+        if (lane < qn - kSortCap) Qw[lane] = Qw[kSortCap + lane];
         __syncwarp();
-        if (lane < qn - 32) Qw[lane] = Qw[32 + lane];
-        __syncwarp();
-        qn -= 32;
-        process(it);
+        qn -= kSortCap;
       }
     }
   }
-  if (lane < qn) process(Qw[lane]);
+  if (qn > 0) run_sorted(qn);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     done += __shfl_down_sync(0xffffffffu, done, o);
@@ -576,7 +711,8 @@ __device__ __forceinline__ void coop_accumulate(const EriParams& a, const PairRe
       const int ib = t / nk, ik = t - ib * nk;
       const PrimPair& pb = bprims[bra.poff + ib];
       const PrimPair& pk = kprims[ket.poff + ik];
-      valid = pb.bound * pk.bound >= a.eps_prim;
+      const float bb = pb.bound * pk.bound;
+      valid = bb >= a.eps_prim && bb <= a.prim_hi;
       if (valid) {
         R* rec = pbuf + lane * Lay::PB;
         R G[NG], PQ[3], rinv;
@@ -689,7 +825,9 @@ __device__ __forceinline__ void coop_quartet(const BuildArgs& a, const SysArgs& 
                                              R* sg, unsigned long long& pdone) {
   const PairRec bra = S.pairs[a.bra_class][bi], ket = S.pairs[a.ket_class][ki];
   EriParams ep = eri_params(a);
-  ep.eps_prim = quartet_prim_cutoff(a, S, bra, ket);
+  const PrimRange r = quartet_prim_range(a, S, bra, ket);
+  ep.eps_prim = r.lo;
+  ep.prim_hi = r.hi;
   coop_accumulate<C, R>(ep, bra, S.prims[a.bra_class], ket, S.prims[a.ket_class], ws, pbuf, sg, pdone);
   quartet_epilogue<C, R>(a, S, bra, ket, bi, ki, ws, pbuf);
 }
@@ -712,7 +850,7 @@ __global__ void __launch_bounds__(kThreadsCoop) k_build_K_coop(const BuildArgs a
     if (lane == 0) d = atomicAdd(a.counter, 1);
     d = __shfl_sync(0xffffffffu, d, 0);
     if (d >= a.n_desc) break;
-    const Desc ds = a.desc[d];
+    const Desc ds = a.desc[a.desc_first + (long long)d * a.desc_stride];
 #ifdef HFX_CHECKED
     {
       const int cc = a.bra_class * 10 + a.ket_class;
@@ -904,7 +1042,7 @@ __global__ void __launch_bounds__(SplitShape<C, R>::THREADS, SplitShape<C, R>::M
   // current shell quartet
   bool have = false;
   int bi = 0, ki = 0, bpoff = 0, kpoff = 0, nk = 1, total = 0, t0 = 0, qn = 0;
-  float eps_q = a.eps_prim;  // primitive cutoff of the current quartet
+  PrimRange pr_q{a.eps_prim, 3.0e38f};  // primitive quartets of the current quartet this launch takes
 #ifdef HFX_SPLIT_SMEM_ACC
   R* const acc = Lay::acc_base(ws) + lane * Lay::ACC_STRIDE;
   R* const comp = acc + 32 * Lay::ACC_STRIDE;
@@ -927,7 +1065,7 @@ __global__ void __launch_bounds__(SplitShape<C, R>::THREADS, SplitShape<C, R>::M
 #endif
         bpoff = bra.poff;
         kpoff = ket.poff;
-        eps_q = quartet_prim_cutoff(a, S, bra, ket);
+        pr_q = quartet_prim_range(a, S, bra, ket);
         nk = ket.pcnt > 0 ? ket.pcnt : 1;
         total = bra.pcnt * ket.pcnt;
         t0 = 0;
@@ -946,7 +1084,7 @@ __global__ void __launch_bounds__(SplitShape<C, R>::THREADS, SplitShape<C, R>::M
             exhausted = true;
             break;
           }
-          cur = a.desc[d];
+          cur = a.desc[a.desc_first + (long long)d * a.desc_stride];
           cur_ok = true;
 #ifdef HFX_CHECKED
           cur_ok = split_desc_ok(a, cur);
@@ -974,7 +1112,8 @@ __global__ void __launch_bounds__(SplitShape<C, R>::THREADS, SplitShape<C, R>::M
         bool valid = false;
         if (t < total) {
           const int ib = t / nk, ik = t - ib * nk;
-          valid = bprims[bpoff + ib].bound * kprims[kpoff + ik].bound >= eps_q;
+          const float bb = bprims[bpoff + ib].bound * kprims[kpoff + ik].bound;
+          valid = bb >= pr_q.lo && bb <= pr_q.hi;
         }
         const unsigned m = __ballot_sync(0xffffffffu, valid);
         if (valid) pq[qn + __popc(m & ((1u << lane) - 1u))] = t;
@@ -1028,7 +1167,7 @@ __global__ void __launch_bounds__(64) k_schwarz(const SchwarzArgs a) {
     if (i >= a.n_pairs || a.pair_class[i] != a.cls) return;
     const PairRec pr = a.pairs[i];
     double out[C::NOUT];
-    contracted_quartet<C, double>(pr, a.prims, pr, a.prims, a.boys, nullptr, a.kernel, a.omega2, ds{0.f, 0.f}, 0.f,
+    contracted_quartet<C, double>(pr, a.prims, pr, a.prims, a.boys, nullptr, a.kernel, a.omega2, ds{0.f, 0.f}, PrimRange{0.f, 3.0e38f},
                                   out);
     double mx = 0.0;
 #pragma unroll
@@ -1111,7 +1250,7 @@ __global__ void __launch_bounds__(64) k_eval(const EvalArgs a) {
   const PairRec bra = a.pairs[q.x], ket = a.pairs[q.y];
   R out[C::NOUT];
   contracted_quartet<C, R>(bra, a.prims, ket, a.prims, a.boys, a.boysf, a.kernel, a.omega2,
-                           ds{a.omega2_hi, a.omega2_lo}, 0.f, out);
+                           ds{a.omega2_hi, a.omega2_lo}, PrimRange{0.f, 3.0e38f}, out);
   const int4 st = a.strides[i];
   double* o = a.out + a.out_off[i];
 #pragma unroll

@@ -104,6 +104,7 @@ struct Plan {
   int n_desc[HFX_NCLASS] = {0};
   int n_block[HFX_NCLASS] = {0};
   int grid[2][HFX_NCLASS] = {{0}};  // persistent grid per (precision, class); 0 = occupancy x SMs
+  int shard_rank = 0, shard_n = 1;   // batches i with i % shard_n == shard_rank (sharded builds)
   long long max_values = 0, max_ns2 = 0;
   int max_blocks = 0;
   DBuf<int> counters;                // 2 x HFX_NCLASS
@@ -700,7 +701,11 @@ static BuildArgs plan_args(Plan& pl, int cls) {
   BuildArgs a;
   a.sys = pl.d_sys.p;
   a.desc = pl.descp[cls];
-  a.n_desc = pl.n_desc[cls];
+  // a sharded build takes every shard_n-th batch from shard_rank on
+  const int nd = pl.n_desc[cls];
+  a.desc_first = pl.shard_rank;
+  a.desc_stride = pl.shard_n;
+  a.n_desc = nd > pl.shard_rank ? (nd - pl.shard_rank + pl.shard_n - 1) / pl.shard_n : 0;
   a.n_sys = pl.n;
   a.bra_class = hfx_class_table[cls][0];
   a.ket_class = hfx_class_table[cls][1];
@@ -718,6 +723,7 @@ static BuildArgs plan_args(Plan& pl, int cls) {
   a.eps_prim = (float)o.prim_cutoff;
   a.prim_dscreen = o.prim_density_screen;
   a.promote = o.fp64_promote_bound;
+  a.promote_prims = o.promote_prims;
   a.route = 0;
   a.counter = nullptr;
   a.n_done = nullptr;
@@ -809,7 +815,9 @@ static void plan_stats(Plan& pl, hfx_stats* out) {
     out->n_quartets_computed[c] = 0;
     for (int pass = 0; pass < 2; ++pass) {
       const unsigned long long* d = done + 2 * (pass * HFX_NCLASS + c);
-      out->n_quartets_computed[c] += (long long)d[0];
+      // with promotion per primitive quartet the FP32 pass sees every quartet
+      // and the FP64 pass again those above the bound
+      if (!(pl.opts.promote_prims && pass == 1)) out->n_quartets_computed[c] += (long long)d[0];
       out->n_quartets_pass[pass][c] = (long long)d[0];
       out->n_prim_quartets_pass[pass][c] = (long long)d[1];
       float ms = 0.f;
@@ -1349,6 +1357,18 @@ hfx_status hfx_build_K(hfx_quartets* q, const double* P, double* K, void* stream
   pl.h_sys[0].P = P;
   pl.h_sys[0].K = K;
   return plan_build(pl, (cudaStream_t)stream, false, true);
+}
+
+hfx_status hfx_build_K_shard(hfx_quartets* q, const double* P, double* K, int rank, int n_ranks, void* stream) {
+  if (!q || !P || !K) return fail(HFX_ERR_INVALID_ARG, "NULL argument");
+  if (n_ranks < 1 || rank < 0 || rank >= n_ranks) return fail(HFX_ERR_INVALID_ARG, "need 0 <= rank < n_ranks");
+  Plan& pl = q->plan;
+  pl.shard_rank = rank;
+  pl.shard_n = n_ranks;
+  const hfx_status st = hfx_build_K(q, P, K, stream);
+  pl.shard_rank = 0;
+  pl.shard_n = 1;
+  return st;
 }
 
 hfx_status hfx_build_K_delta(hfx_quartets* q, const double* dP, double* K, void* stream) {

@@ -46,7 +46,7 @@ class Opts(ctypes.Structure):
                 ("tau", ctypes.c_double), ("density_screen", ctypes.c_int), ("eps", ctypes.c_double),
                 ("prim_cutoff", ctypes.c_double), ("precision", ctypes.c_int),
                 ("fp64_promote_bound", ctypes.c_double), ("n_block", ctypes.c_int),
-                ("promote_min_l", ctypes.c_int), ("prim_density_screen", ctypes.c_int), ("reserved", ctypes.c_int)]
+                ("promote_min_l", ctypes.c_int), ("prim_density_screen", ctypes.c_int), ("promote_prims", ctypes.c_int)]
 
 
 class Pattern(ctypes.Structure):
@@ -75,6 +75,7 @@ KERNEL_KIND_NAMES = ("k_build_K", "k_build_K_split", "k_build_K_coop")
 
 
 EXPORTED = ["hfx_create_basis", "hfx_build_quartets", "hfx_value_count", "hfx_build_K", "hfx_build_K_delta",
+            "hfx_build_K_shard",
             "hfx_exchange_energy",
             "hfx_pack_dense", "hfx_unpack_dense", "hfx_eval_quartets", "hfx_boys_eval", "hfx_get_stats",
             "hfx_get_class_info", "hfx_exchange_energy_noalloc", "hfx_batch_create", "hfx_batch_build_K",
@@ -126,6 +127,7 @@ def load(path: str = LIB_PATH):
     lib.hfx_value_count.restype = LL
     lib.hfx_build_K.argtypes = [V, V, V, V]
     lib.hfx_build_K_delta.argtypes = [V, V, V, V]
+    lib.hfx_build_K_shard.argtypes = [V, V, V, I, I, V]
     lib.hfx_exchange_energy.argtypes = [V, V, V, ctypes.POINTER(D), V]
     lib.hfx_pack_dense.argtypes = [V, V, V, V]
     lib.hfx_unpack_dense.argtypes = [V, V, V, V]
@@ -241,7 +243,7 @@ def hfx_create_basis(shell_l, shell_atom, prim_off, alpha, coef, atom_xyz, strea
 
 def make_opts(kernel=HFX_KERNEL_ERFC, omega=0.11, screen=True, tau=1e-8, density_screen=True, eps=None,
               prim_cutoff=1e-15, precision=HFX_PREC_FP64, fp64_promote_bound=math.inf, n_block=128,
-              promote_min_l=0, prim_density_screen=False) -> Opts:
+              promote_min_l=0, prim_density_screen=False, promote_prims=False) -> Opts:
     o = Opts()
     o.kernel, o.omega, o.screen, o.tau = int(kernel), float(omega), int(bool(screen)), float(tau)
     o.density_screen = int(bool(density_screen))
@@ -250,6 +252,7 @@ def make_opts(kernel=HFX_KERNEL_ERFC, omega=0.11, screen=True, tau=1e-8, density
     o.fp64_promote_bound, o.n_block = float(fp64_promote_bound), int(n_block)
     o.promote_min_l = int(promote_min_l)
     o.prim_density_screen = int(bool(prim_density_screen))
+    o.promote_prims = int(bool(promote_prims))
     return o
 
 
@@ -391,6 +394,11 @@ class Quartets:
 
     def build_K_delta(self, dP_val, K_val, stream=None):
         hfx_build_K_delta(self.handle, dP_val, K_val, stream)
+
+    def build_K_shard(self, P_val, K_val, rank, n_ranks, stream=None):
+        """This rank's share of a sharded build (sum over ranks = build_K)."""
+        _check(load().hfx_build_K_shard(self.handle, _ptr(P_val), _ptr(K_val), int(rank), int(n_ranks),
+                                        _stream(stream)))
 
     def exchange_energy(self, P_val, K_val, stream=None) -> float:
         return hfx_exchange_energy(self.handle, P_val, K_val, stream)

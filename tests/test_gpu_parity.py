@@ -248,3 +248,35 @@ def test_sixteen_primitive_d_shell(prec):
         assert abs(E - Eref) <= 1e-9 * abs(Eref)
     else:
         assert abs(E - Eref) <= 1e-6
+
+
+def test_promotion_per_primitive_quartet():
+    """Promotion per primitive quartet: of the quartets above the bound, the
+    primitive quartets with bound_ab bound_cd P_scr above it run in FP64, the
+    rest in FP32.  Every primitive quartet runs exactly once over the two
+    launches (their counts add up to the unpromoted build's), bound 0 sends
+    every primitive quartet to FP64 (K at the FP64 tolerance), and a bound in
+    between keeps the energy within 1e-6 Ha of the oracle."""
+    from paper_2009_03555_gb300 import hfx
+    s = synth.ch_cluster(5, 15)
+    mask = pattern_mask(s, 6.0)
+    P = synth.density_matrix(s, 15) * mask_dense(s, mask)
+    kw = dict(kernel=oracle.KERNEL_ERFC, omega=0.11, screen=True, tau=1e-8, density_screen=True, eps=1e-8)
+    Kref, n = oracle.build_K(oracle.Basis(s), P, **kw)
+    Eref = oracle.exchange_energy(P, Kref)
+    md = mask_dense(s, mask)
+    _, _, q0 = run_gpu_K(s, P, mask=mask, prim_cutoff=1e-14, precision=hfx.HFX_PREC_MIXED, **kw)
+    npq0 = sum(q0.stats().n_prim_quartets_pass[0])
+    K, E, q = run_gpu_K(s, P, mask=mask, prim_cutoff=1e-14, precision=hfx.HFX_PREC_MIXED, fp64_promote_bound=0.0,
+                        promote_prims=True, **kw)
+    st = q.stats()
+    assert sum(st.n_prim_quartets_pass[0]) == 0 and sum(st.n_prim_quartets_pass[1]) == npq0
+    assert sum(st.n_quartets_computed) == n
+    assert np.abs((K - Kref) * md).max() <= 1e-10
+    K, E, q = run_gpu_K(s, P, mask=mask, prim_cutoff=1e-14, precision=hfx.HFX_PREC_MIXED, fp64_promote_bound=1e-4,
+                        promote_prims=True, **kw)
+    st = q.stats()
+    n1 = sum(st.n_prim_quartets_pass[1])
+    assert 0 < n1 < npq0 and sum(st.n_prim_quartets_pass[0]) + n1 == npq0
+    assert sum(st.n_quartets_computed) == n
+    assert abs(E - Eref) <= 1e-6
