@@ -429,8 +429,10 @@ def run_serve(args):
     arrivals = np.cumsum(rng.exponential(1.0 / args.serve_rate, size=n))
     c0, c1 = (int(x) for x in args.serve_chain.split(","))
     s0, s1 = (int(x) for x in args.serve_slab.split(","))
-    kinds = rng.integers(0, 2, size=n)
-    sizes = [int(rng.integers(c0, c1 + 1)) if k == 0 else int(rng.integers(s0, s1 + 1)) for k in kinds]
+    u = rng.uniform(size=n)
+    kinds = np.where(u < args.serve_periodic_share, 2, rng.integers(0, 2, size=n))
+    sizes = [int(rng.integers(c0, c1 + 1)) if k == 0 else (int(rng.integers(s0, s1 + 1)) if k == 1 else 0)
+             for k in kinds]
     prec = hfx.HFX_PREC_MIXED if args.precision == "mixed" else hfx.HFX_PREC_FP64
     promote = args.promote if prec == hfx.HFX_PREC_MIXED else math.inf
     opts = hfx.make_opts(kernel=hfx.HFX_KERNEL_ERFC, omega=0.11, screen=True, tau=1e-8, density_screen=True,
@@ -438,18 +440,24 @@ def run_serve(args):
                          fp64_promote_bound=promote, promote_min_l=args.promote_min_l,
                          prim_density_screen=bool(args.prim_dscreen), promote_prims=bool(args.promote_prims))
     reqs = []
+    si = synth.si_supercell(args.serve_periodic_cells) if args.serve_periodic_share > 0 else None
+    per = hfx.Periodic(si, si.lattice, r_ext=10.0, r_P=14.0) if si is not None else None
     for i, (k, na) in enumerate(zip(kinds, sizes)):
-        s = synth.ch_chain(na, sub=i) if k == 0 else synth.ch_slab(na, sub=i)
-        mask = synth.atom_pair_mask(s, 14.0)
-        P = synth.density_matrix(s, 4, cutoff=14.0, sub=i)
         pr = np.random.default_rng(2009_03555 + 1000 + i)
+        if k == 2:  # periodic Si cell: the same cell, its own density sequence
+            P = synth.periodic_density_matrix(si, cutoff=14.0, sub=i)
+            s, mask = si, None
+        else:
+            s = synth.ch_chain(na, sub=i) if k == 0 else synth.ch_slab(na, sub=i)
+            mask = synth.atom_pair_mask(s, 14.0)
+            P = synth.density_matrix(s, 4, cutoff=14.0, sub=i)
         Ps = [P]
         for _ in range(args.serve_builds - 1):
             Ps.append(synth.perturb_density(Ps[-1], pr))
         reqs.append((s, mask, Ps))
 
     def serve(use_graph, m):
-        srv = hfx.Server(use_graph=use_graph)
+        srv = hfx.Server(use_graph=use_graph, incremental=bool(args.serve_incremental))
         tickets = [None] * m
         t0 = time.perf_counter()
         nxt, finished, lat = 0, 0, [None] * m
@@ -457,7 +465,8 @@ def run_serve(args):
             now = time.perf_counter() - t0
             while nxt < m and arrivals[nxt] <= now:
                 s, mask, Ps = reqs[nxt]
-                tickets[nxt] = srv.submit(s, mask, opts, Ps, want_K=False)
+                tickets[nxt] = (srv.submit_periodic(per, opts, Ps, want_K=False) if mask is None
+                                else srv.submit(s, mask, opts, Ps, want_K=False))
                 nxt += 1
             info = srv.info()
             if info.n_active == 0 and info.n_queued == 0:
@@ -485,8 +494,16 @@ def run_serve(args):
             "higher_is_better": True, "dtype": "f32+f64" if prec == hfx.HFX_PREC_MIXED else "f64",
             "data": "synthetic",
             "config": {"workload": f"{n} requests, Poisson {args.serve_rate}/s, {args.serve_builds} builds each "
-                                   f"(P perturbed 1e-3), C/H chains {c0}-{c1} atoms and slabs {s0}-{s1} atoms, "
-                                   f"HSE erfc w=0.11, Schwarz 1e-8 + density screening, {args.precision}",
+                                   f"(P perturbed 1e-3), C/H chains {c0}-{c1} atoms and slabs {s0}-{s1} atoms"
+                                   + (f", periodic Si diamond {args.serve_periodic_cells}^3 cells "
+                                      f"({8 * args.serve_periodic_cells ** 3} atoms, images within 10 bohr) for "
+                                      f"{args.serve_periodic_share:.0%} of the requests"
+                                      if args.serve_periodic_share > 0 else "")
+                                   + f", HSE erfc w=0.11, Schwarz 1e-8 + density screening, {args.precision}"
+                                   + (", incremental builds after the first" if args.serve_incremental else ""),
+                       "requests": {"chain": int(np.sum(kinds == 0)), "slab": int(np.sum(kinds == 1)),
+                                    "periodic": int(np.sum(kinds == 2))},
+                       "incremental": bool(args.serve_incremental),
                        "use_graph": bool(args.serve_graph), "precision": args.precision,
                        "fp64_promote_bound": _json_num(promote), "promote_min_l": args.promote_min_l},
             "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3),
@@ -774,6 +791,12 @@ def main():
     ap.add_argument("--serve-chain", default="20,60", help="chain sizes (atoms), min,max")
     ap.add_argument("--serve-slab", default="16,36", help="slab sizes (atoms), min,max")
     ap.add_argument("--serve-graph", type=int, default=0)
+    ap.add_argument("--serve-incremental", type=int, default=1,
+                    help="1: builds after a request's first from the density difference")
+    ap.add_argument("--serve-periodic-share", type=float, default=0.2,
+                    help="share of requests that are the periodic Si cell")
+    ap.add_argument("--serve-periodic-cells", type=int, default=1,
+                    help="conventional cells per axis of the served Si cell (8 atoms per cell)")
     ap.add_argument("--batch", action="store_true", help="many small systems per build (batched vs sequential)")
     ap.add_argument("--batch-systems", type=int, default=64)
     ap.add_argument("--batch-atoms", default="8,24", help="cluster sizes (atoms), min,max")

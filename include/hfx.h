@@ -358,9 +358,11 @@ hfx_status hfx_periodic_pack_host(const hfx_shell_desc* shells, int n_shells, in
  * whole budget fails with HFX_ERR_OOM, otherwise the queue head waits for
  * retirements --, runs one build of every active request (requests sharing
  * kernel, precision and screening options share one batched build, see the
- * batch functions), and retires finished requests.  One host thread drives a
- * server (not thread-safe); all work is on the stream given at creation, and
- * hfx_server_step() synchronises it. */
+ * batch functions), and retires finished requests.  The setup of requests
+ * admitted while others are active runs on a second stream of the server,
+ * during the active requests' builds, and they join at the next step.  One
+ * host thread drives a server (not thread-safe); builds run on the stream
+ * given at creation, and hfx_server_step() synchronises both streams. */
 typedef struct hfx_server_s hfx_server;
 
 typedef enum {
@@ -375,7 +377,9 @@ typedef struct {
   long long mem_budget; /* device bytes for admitted requests; <= 0: 80% of the free memory at creation */
   int max_active;       /* at most this many active requests; <= 0: 64 */
   int use_graph;        /* capture each batched build as a CUDA graph (re-captured when the active set changes) */
-  int reserved[4];
+  int incremental;      /* builds after a request's first: K(P_n) = K(P_{n-1}) + K(P_n - P_{n-1}), the difference
+                           screened on its own shell maxima (twice the P/K device arrays per request) */
+  int reserved[3];
 } hfx_server_opts;
 
 typedef struct {
@@ -408,6 +412,17 @@ hfx_status hfx_server_create(const hfx_server_opts* opts, void* stream, hfx_serv
 hfx_status hfx_server_submit(hfx_server* srv, const hfx_shell_desc* shells, int n_shells, const double* atom_xyz,
                              int n_atoms, const hfx_pattern* pattern, const hfx_opts* opts, int n_builds,
                              const double* P_host, double* K_out, long long* ticket);
+
+/* Queue a periodic request (Sec. 2, Eq. H-HFX): the home cell (shells,
+ * atom_xyz, lattice as rows, r_ext) as for hfx_create_basis_periodic, which
+ * its setup calls; ext_pattern: the density pattern over the extended atoms
+ * (hfx_periodic_extend, e.g. hfx_distance_pattern); P_host: n_builds x value
+ * count doubles in that layout (hfx_periodic_pack_host); K_out as for
+ * hfx_server_submit (image rows zero).  Energies are per cell. */
+hfx_status hfx_server_submit_periodic(hfx_server* srv, const hfx_shell_desc* shells, int n_shells,
+                                      const double* atom_xyz, int n_atoms, const double* lattice, double r_ext,
+                                      const hfx_pattern* ext_pattern, const hfx_opts* opts, int n_builds,
+                                      const double* P_host, double* K_out, long long* ticket);
 
 /* Admission, one build of every active request, retirement (see above).
  * *n_active (may be NULL): active requests after the step. */

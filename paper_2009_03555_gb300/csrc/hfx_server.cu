@@ -7,16 +7,25 @@
 // up before the SCF loop for the same reason).
 //
 // Each hfx_server_step():
-//   1. admits queued requests in arrival order while the device memory they
-//      are estimated to need fits under the server's budget (a request that
-//      could never fit fails with HFX_ERR_OOM; the head of the queue waits
-//      otherwise), and runs their setup;
-//   2. runs one build of every active request: requests with the same kernel,
-//      precision and screening options share one batched build (one launch
-//      per quartet class over all of their work queues, hfx_batch_*), whose
-//      plan is rebuilt only when the active set changes;
-//   3. retires the requests whose last build is done: copies their last K to
-//      the caller's host array, frees their device memory.
+//   1. launches one build of every active request: requests with the same
+//      kernel, precision and screening options share one batched build (one
+//      launch per quartet class over all of their work queues, hfx_batch_*),
+//      whose plan is rebuilt only when the active set changes;
+//   2. while those builds run, admits queued requests in arrival order while
+//      the device memory they are estimated to need fits under the server's
+//      budget (a request that could never fit fails with HFX_ERR_OOM; the head
+//      of the queue waits otherwise) and runs their setup on a second stream,
+//      so arrivals do not stall the active requests; they join at the next
+//      step (when nothing is active they are admitted first and built at once);
+//   3. collects the energies and retires the requests whose last build is
+//      done: copies their last K to the caller's host array, frees their
+//      device memory.
+// With `incremental`, every build of a request after its first is built from
+// the density difference: K(P_n) = K(P_{n-1}) + K(P_n - P_{n-1}) (K is linear
+// in P, Eq. H-HFX), the difference screened on its own shell maxima
+// (Eq. dmscreening), which are small between SCF-like iterations.
+// Periodic requests (hfx_server_submit_periodic) are set up on the library's
+// periodic basis and build the home rows K^G (the energy is per cell).
 //
 // One host thread drives a server; its calls are not thread-safe.
 #include <cuda_runtime.h>
@@ -45,8 +54,43 @@ bool same_options(const hfx_opts& a, const hfx_opts& b) {
          a.tau == b.tau && a.density_screen == b.density_screen && a.eps == b.eps && a.prim_cutoff == b.prim_cutoff &&
          (a.fp64_promote_bound == b.fp64_promote_bound ||
           (a.fp64_promote_bound != a.fp64_promote_bound && b.fp64_promote_bound != b.fp64_promote_bound)) &&
-         a.promote_min_l == b.promote_min_l;
+         a.promote_min_l == b.promote_min_l && a.prim_density_screen == b.prim_density_screen &&
+         a.promote_prims == b.promote_prims;
 }
+
+// new P of one build into d, and d - P into d, P := new (incremental builds)
+__global__ void k_delta_in(long long n, double* __restrict__ d, double* __restrict__ P) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const double t = d[i];
+    d[i] = t - P[i];
+    P[i] = t;
+  }
+}
+
+__global__ void k_add_into(long long n, const double* __restrict__ x, double* __restrict__ y) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) y[i] += x[i];
+}
+
+// E[slot] = -1/2 sum_i P_i K_i (E zeroed before; one atomicAdd per block)
+__global__ void k_energy_into(long long n, const double* __restrict__ P, const double* __restrict__ K, double* E) {
+  double v = 0.0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) v = fma(P[i], K[i], v);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __shared__ double w[8];
+  if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += w[k];
+    atomicAdd(E, -0.5 * t);
+  }
+}
+
+unsigned grid_for(long long n) { return (unsigned)std::max<long long>(1, std::min<long long>(1024, (n + 255) / 256)); }
 
 struct Request {
   long long ticket = 0;
@@ -55,7 +99,11 @@ struct Request {
   std::vector<hfx_shell_desc> shells;
   std::vector<double> prim;  // alpha then coef of every shell, back to back
   std::vector<double> xyz;
-  int n_atoms = 0;
+  int n_atoms = 0;               // atoms of xyz (the home cell of a periodic request)
+  int pattern_atoms = 0;         // atoms of the pattern (the extended set of a periodic request)
+  bool periodic = false;
+  double lattice[9] = {0};
+  double r_ext = 0.0;
   std::vector<int> row_ptr, col;
   hfx_opts opts{};
   const double* P_host = nullptr;  // n_builds x n_values
@@ -70,10 +118,12 @@ struct Request {
   hfx_quartets* q = nullptr;
   double* P = nullptr;
   double* K = nullptr;
+  double* dP = nullptr;  // incremental builds: density difference and its exchange
+  double* dK = nullptr;
 
   hfx_pattern pattern() const {
     hfx_pattern p;
-    p.n_atoms = n_atoms;
+    p.n_atoms = pattern_atoms;
     p.row_ptr = row_ptr.data();
     p.col = col.data();
     return p;
@@ -83,9 +133,11 @@ struct Request {
     if (basis) hfx_destroy_basis(basis);
     if (P) cudaFree(P);
     if (K) cudaFree(K);
+    if (dP) cudaFree(dP);
+    if (dK) cudaFree(dK);
     q = nullptr;
     basis = nullptr;
-    P = K = nullptr;
+    P = K = dP = dK = nullptr;
   }
   ~Request() { release_device(); }
 };
@@ -101,6 +153,9 @@ struct Group {
 struct hfx_server_s {
   hfx_server_opts o{};
   cudaStream_t stream = nullptr;
+  cudaStream_t setup_stream = nullptr;  // admissions overlap the active builds
+  double* energies = nullptr;           // incremental builds: per-member energies of a group
+  size_t n_energies = 0;
   std::chrono::steady_clock::time_point t0;
   long long next_ticket = 1;
   std::deque<Request*> queue;
@@ -119,7 +174,11 @@ struct hfx_server_s {
     groups.clear();
     dirty = true;
   }
-  ~hfx_server_s() { drop_groups(); }
+  ~hfx_server_s() {
+    drop_groups();
+    if (setup_stream) cudaStreamDestroy(setup_stream);
+    if (energies) cudaFree(energies);
+  }
 };
 
 namespace {
@@ -139,33 +198,42 @@ hfx_status setup_request(hfx_server_s* s, Request* r) {
     r->inject = HFX_OK;
     return srv_fail(st, "injected setup failure");
   }
-  hfx_status st = hfx_create_basis(r->shells.data(), (int)r->shells.size(), r->xyz.data(), r->n_atoms, s->stream,
-                                   &r->basis);
+  hfx_status st = r->periodic ? hfx_create_basis_periodic(r->shells.data(), (int)r->shells.size(), r->xyz.data(),
+                                                          r->n_atoms, r->lattice, r->r_ext, s->setup_stream, &r->basis)
+                               : hfx_create_basis(r->shells.data(), (int)r->shells.size(), r->xyz.data(), r->n_atoms,
+                                                  s->setup_stream, &r->basis);
   if (st != HFX_OK) return st;
   const hfx_pattern pat = r->pattern();
-  st = hfx_build_quartets(r->basis, &r->opts, &pat, s->stream, &r->q);
+  st = hfx_build_quartets(r->basis, &r->opts, &pat, s->setup_stream, &r->q);
   if (st != HFX_OK) return st;
   const size_t bytes = (size_t)std::max<long long>(r->n_values, 1) * sizeof(double);
+  const int n_arrays = s->o.incremental ? 4 : 2;
   cudaError_t e = cudaMalloc(&r->P, bytes);
   if (e == cudaSuccess) e = cudaMalloc(&r->K, bytes);
+  if (e == cudaSuccess && s->o.incremental) e = cudaMalloc(&r->dP, bytes);
+  if (e == cudaSuccess && s->o.incremental) e = cudaMalloc(&r->dK, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return srv_fail(e == cudaErrorMemoryAllocation ? HFX_ERR_OOM : HFX_ERR_CUDA,
                     std::string("request buffers: ") + cudaGetErrorString(e));
   }
-  r->info.device_bytes = hfx_basis_device_bytes(r->basis) + hfx_quartets_device_bytes(r->q) + 2 * (long long)bytes;
+  r->info.device_bytes =
+      hfx_basis_device_bytes(r->basis) + hfx_quartets_device_bytes(r->q) + n_arrays * (long long)bytes;
   return HFX_OK;
 }
 
-hfx_status admit(hfx_server_s* s) {
-  while (!s->queue.empty() && (int)s->active.size() < s->o.max_active) {
+// Admission into `into` (the active set, or the requests joining it at the
+// end of this step); `holding`: requests already holding device memory.
+hfx_status admit(hfx_server_s* s, std::vector<Request*>& into, size_t holding) {
+  while (!s->queue.empty() && holding + into.size() < (size_t)s->o.max_active) {
     Request* r = s->queue.front();
     if (r->estimate > s->o.mem_budget) {
       s->queue.pop_front();
       finish(s, r, HFX_REQ_FAILED, HFX_ERR_OOM);
       continue;
     }
-    if (s->stats.used_bytes + r->estimate > s->o.mem_budget && !s->active.empty()) break;  // wait for retirements
+    if (s->stats.used_bytes + r->estimate > s->o.mem_budget && holding + into.size() > 0)
+      break;  // wait for retirements
     s->queue.pop_front();
     r->info.t_admit = s->now();
     const hfx_status st = setup_request(s, r);
@@ -177,10 +245,9 @@ hfx_status admit(hfx_server_s* s) {
     r->info.state = HFX_REQ_ACTIVE;
     s->stats.used_bytes += r->info.device_bytes;
     s->stats.peak_used_bytes = std::max(s->stats.peak_used_bytes, s->stats.used_bytes);
-    s->active.push_back(r);
-    s->dirty = true;
+    into.push_back(r);
   }
-  s->stats.max_active_seen = std::max(s->stats.max_active_seen, (int)s->active.size());
+  s->stats.max_active_seen = std::max(s->stats.max_active_seen, (int)(holding + into.size()));
   return HFX_OK;
 }
 
@@ -224,27 +291,33 @@ hfx_status hfx_server_create(const hfx_server_opts* opts, void* stream, hfx_serv
     s->o.mem_budget = (long long)(0.8 * (double)fr);
   }
   s->stream = (cudaStream_t)stream;
+  const cudaError_t es = cudaStreamCreateWithFlags(&s->setup_stream, cudaStreamNonBlocking);
+  if (es != cudaSuccess) return srv_fail(HFX_ERR_CUDA, std::string("setup stream: ") + cudaGetErrorString(es));
   s->t0 = std::chrono::steady_clock::now();
   s->stats.mem_budget = s->o.mem_budget;
   *out = s.release();
   return HFX_OK;
 }
 
-hfx_status hfx_server_submit(hfx_server* s, const hfx_shell_desc* shells, int n_shells, const double* atom_xyz,
-                             int n_atoms, const hfx_pattern* pattern, const hfx_opts* opts, int n_builds,
-                             const double* P_host, double* K_out, long long* ticket) {
-  if (!s || !shells || n_shells <= 0 || !atom_xyz || n_atoms <= 0 || !pattern || !opts || !P_host || !ticket)
-    return srv_fail(HFX_ERR_INVALID_ARG, "NULL or empty argument");
-  if (n_builds < 1) return srv_fail(HFX_ERR_INVALID_ARG, "n_builds must be >= 1");
-  if (pattern->n_atoms != n_atoms) return srv_fail(HFX_ERR_INVALID_ARG, "pattern must cover the atoms");
-  const long long nv = hfx_pattern_value_count(shells, n_shells, pattern);
+}  // extern "C"
+
+namespace {
+
+// Queue a request: shells, coordinates (n_atoms: home cell of a periodic
+// request), the pattern over pattern_shells (the extended shells of a
+// periodic request), options, densities and the K destination.
+hfx_status submit_common(hfx_server* s, const hfx_shell_desc* shells, int n_shells, const double* atom_xyz,
+                         int n_atoms, const hfx_shell_desc* pattern_shells, int n_pattern_shells,
+                         const hfx_pattern* pattern, const hfx_opts* opts, int n_builds, const double* P_host,
+                         double* K_out, long long* ticket, std::unique_ptr<Request>& r) {
+  const long long nv = hfx_pattern_value_count(pattern_shells, n_pattern_shells, pattern);
   if (nv < 0) return srv_fail(HFX_ERR_INVALID_ARG, "inconsistent shells or pattern");
-  std::unique_ptr<Request> r(new Request());
   r->ticket = s->next_ticket++;
   r->n_atoms = n_atoms;
+  r->pattern_atoms = pattern->n_atoms;
   r->xyz.assign(atom_xyz, atom_xyz + 3 * (size_t)n_atoms);
-  r->row_ptr.assign(pattern->row_ptr, pattern->row_ptr + n_atoms + 1);
-  r->col.assign(pattern->col, pattern->col + r->row_ptr[n_atoms]);
+  r->row_ptr.assign(pattern->row_ptr, pattern->row_ptr + pattern->n_atoms + 1);
+  r->col.assign(pattern->col, pattern->col + r->row_ptr[(size_t)pattern->n_atoms]);
   size_t np = 0;
   for (int i = 0; i < n_shells; ++i) {
     if (shells[i].nprim < 1 || !shells[i].alpha || !shells[i].coef)
@@ -265,7 +338,8 @@ hfx_status hfx_server_submit(hfx_server* s, const hfx_shell_desc* shells, int n_
   r->P_host = P_host;
   r->K_out = K_out;
   r->n_values = nv;
-  r->estimate = hfx_setup_bytes_estimate(shells, n_shells, pattern) + 2 * std::max<long long>(nv, 1) * 8;
+  r->estimate = hfx_setup_bytes_estimate(pattern_shells, n_pattern_shells, pattern) +
+                (s->o.incremental ? 4 : 2) * std::max<long long>(nv, 1) * 8;
   r->E.assign((size_t)n_builds, 0.0);
   r->info.state = HFX_REQ_QUEUED;
   r->info.n_builds = n_builds;
@@ -275,6 +349,58 @@ hfx_status hfx_server_submit(hfx_server* s, const hfx_shell_desc* shells, int n_
   s->queue.push_back(r.get());
   s->all[r->ticket] = std::move(r);
   return HFX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+hfx_status hfx_server_submit(hfx_server* s, const hfx_shell_desc* shells, int n_shells, const double* atom_xyz,
+                             int n_atoms, const hfx_pattern* pattern, const hfx_opts* opts, int n_builds,
+                             const double* P_host, double* K_out, long long* ticket) {
+  if (!s || !shells || n_shells <= 0 || !atom_xyz || n_atoms <= 0 || !pattern || !opts || !P_host || !ticket)
+    return srv_fail(HFX_ERR_INVALID_ARG, "NULL or empty argument");
+  if (n_builds < 1) return srv_fail(HFX_ERR_INVALID_ARG, "n_builds must be >= 1");
+  if (pattern->n_atoms != n_atoms) return srv_fail(HFX_ERR_INVALID_ARG, "pattern must cover the atoms");
+  std::unique_ptr<Request> r(new Request());
+  return submit_common(s, shells, n_shells, atom_xyz, n_atoms, shells, n_shells, pattern, opts, n_builds, P_host,
+                       K_out, ticket, r);
+}
+
+hfx_status hfx_server_submit_periodic(hfx_server* s, const hfx_shell_desc* shells, int n_shells,
+                                      const double* atom_xyz, int n_atoms, const double* lattice, double r_ext,
+                                      const hfx_pattern* ext_pattern, const hfx_opts* opts, int n_builds,
+                                      const double* P_host, double* K_out, long long* ticket) {
+  if (!s || !shells || n_shells <= 0 || !atom_xyz || n_atoms <= 0 || !lattice || !ext_pattern || !opts ||
+      !P_host || !ticket)
+    return srv_fail(HFX_ERR_INVALID_ARG, "NULL or empty argument");
+  if (n_builds < 1) return srv_fail(HFX_ERR_INVALID_ARG, "n_builds must be >= 1");
+  for (int i = 0; i < n_shells; ++i)
+    if (shells[i].atom < 0 || shells[i].atom >= n_atoms || (i > 0 && shells[i].atom < shells[i - 1].atom))
+      return srv_fail(HFX_ERR_INVALID_ARG, "shells must be grouped by atom in increasing atom order");
+  // the extended set the setup will build (hfx_create_basis_periodic): sizes
+  // the values and the memory estimate
+  const long long n_ext = hfx_periodic_extend(atom_xyz, n_atoms, lattice, r_ext, 0, nullptr, nullptr, nullptr);
+  if (n_ext < 0) return HFX_ERR_INVALID_ARG;  // message set by hfx_periodic_extend
+  if (ext_pattern->n_atoms != n_ext)
+    return srv_fail(HFX_ERR_INVALID_ARG, "pattern must cover the extended atoms (hfx_periodic_extend)");
+  std::vector<int> ext_home((size_t)n_ext), ext_shift(3 * (size_t)n_ext);
+  std::vector<double> ext_xyz(3 * (size_t)n_ext);
+  hfx_periodic_extend(atom_xyz, n_atoms, lattice, r_ext, n_ext, ext_home.data(), ext_shift.data(), ext_xyz.data());
+  std::vector<hfx_shell_desc> ext;
+  for (long long X = 0; X < n_ext; ++X)
+    for (int i = 0; i < n_shells; ++i)
+      if (shells[i].atom == ext_home[(size_t)X]) {
+        hfx_shell_desc d = shells[i];
+        d.atom = (int)X;
+        ext.push_back(d);
+      }
+  std::unique_ptr<Request> r(new Request());
+  r->periodic = true;
+  std::copy(lattice, lattice + 9, r->lattice);
+  r->r_ext = r_ext;
+  return submit_common(s, shells, n_shells, atom_xyz, n_atoms, ext.data(), (int)ext.size(), ext_pattern, opts,
+                       n_builds, P_host, K_out, ticket, r);
 }
 
 hfx_status hfx_server_step(hfx_server* s, int* n_active) {
@@ -289,34 +415,70 @@ hfx_status hfx_server_step(hfx_server* s, int* n_active) {
       s->active.swap(keep);
     }
   }
-  hfx_status st = admit(s);
-  if (st != HFX_OK) return st;
+  hfx_status st = HFX_OK;
+  std::vector<Request*> incoming;  // admitted during this step's builds, active from the next
+  const bool overlap = !s->active.empty();
+  if (!overlap) {  // nothing to overlap with: admit now and build at once
+    st = admit(s, s->active, 0);
+    if (st != HFX_OK) return st;
+    if (!s->active.empty()) s->dirty = true;
+  }
   if (n_active) *n_active = (int)s->active.size();
   if (s->active.empty()) return HFX_OK;
   if (s->dirty) {
     st = regroup(s);
     if (st != HFX_OK) return st;
   }
-  // this build's density of every active request
+  // 1. this build's density of every active request, then the builds (async)
   for (Request* r : s->active) {
+    const bool delta = s->o.incremental && r->info.builds_done > 0;
     const double* src = r->P_host + (size_t)r->info.builds_done * (size_t)r->n_values;
-    const cudaError_t e =
-        cudaMemcpyAsync(r->P, src, (size_t)r->n_values * sizeof(double), cudaMemcpyHostToDevice, s->stream);
+    const cudaError_t e = cudaMemcpyAsync(delta ? r->dP : r->P, src, (size_t)r->n_values * sizeof(double),
+                                          cudaMemcpyHostToDevice, s->stream);
     if (e != cudaSuccess) return srv_fail(HFX_ERR_CUDA, std::string("P upload: ") + cudaGetErrorString(e));
+    if (delta) k_delta_in<<<grid_for(r->n_values), 256, 0, s->stream>>>(r->n_values, r->dP, r->P);
   }
-  std::vector<double> E;
   for (auto& g : s->groups) {
     std::vector<const double*> Ps;
     std::vector<double*> Ks;
     for (Request* r : g.members) {
-      Ps.push_back(r->P);
-      Ks.push_back(r->K);
+      const bool delta = s->o.incremental && r->info.builds_done > 0;
+      Ps.push_back(delta ? r->dP : r->P);
+      Ks.push_back(delta ? r->dK : r->K);
     }
     st = hfx_batch_build_K(g.batch, Ps.data(), Ks.data(), s->o.use_graph, s->stream);
     if (st != HFX_OK) return st;
-    E.assign(g.members.size(), 0.0);
-    st = hfx_batch_energies(g.batch, E.data(), s->stream);
+  }
+  // 2. admissions (setup on the second stream) while the builds run
+  if (overlap) {
+    st = admit(s, incoming, s->active.size());
     if (st != HFX_OK) return st;
+  }
+  // 3. energies, retirement
+  for (auto& g : s->groups) {
+    std::vector<double> E(g.members.size(), 0.0);
+    if (s->o.incremental) {  // K += K(dP), then -1/2 P.K of the whole density
+      if (!s->energies || s->n_energies < g.members.size()) {
+        if (s->energies) cudaFree(s->energies);
+        s->energies = nullptr;
+        const cudaError_t e = cudaMalloc(&s->energies, std::max<size_t>(g.members.size(), 64) * sizeof(double));
+        if (e != cudaSuccess) return srv_fail(HFX_ERR_OOM, std::string("energies: ") + cudaGetErrorString(e));
+        s->n_energies = std::max<size_t>(g.members.size(), 64);
+      }
+      cudaMemsetAsync(s->energies, 0, g.members.size() * sizeof(double), s->stream);
+      for (size_t i = 0; i < g.members.size(); ++i) {
+        Request* r = g.members[i];
+        if (r->info.builds_done > 0) k_add_into<<<grid_for(r->n_values), 256, 0, s->stream>>>(r->n_values, r->dK, r->K);
+        k_energy_into<<<grid_for(r->n_values), 256, 0, s->stream>>>(r->n_values, r->P, r->K, s->energies + i);
+      }
+      cudaError_t e = cudaMemcpyAsync(E.data(), s->energies, E.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                                      s->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+      if (e != cudaSuccess) return srv_fail(HFX_ERR_CUDA, std::string("energies: ") + cudaGetErrorString(e));
+    } else {
+      st = hfx_batch_energies(g.batch, E.data(), s->stream);
+      if (st != HFX_OK) return st;
+    }
     for (size_t i = 0; i < g.members.size(); ++i) {
       Request* r = g.members[i];
       r->E[(size_t)r->info.builds_done] = E[i];
@@ -325,7 +487,6 @@ hfx_status hfx_server_step(hfx_server* s, int* n_active) {
     }
   }
   s->stats.steps += 1;
-  // retire finished requests
   std::vector<Request*> still, gone;
   for (Request* r : s->active) (r->info.builds_done < r->info.n_builds ? still : gone).push_back(r);
   if (!gone.empty()) {
@@ -341,6 +502,10 @@ hfx_status hfx_server_step(hfx_server* s, int* n_active) {
     }
   }
   s->active.swap(still);
+  if (!incoming.empty()) {
+    s->active.insert(s->active.end(), incoming.begin(), incoming.end());
+    s->dirty = true;
+  }
   if (n_active) *n_active = (int)s->active.size();
   return HFX_OK;
 }

@@ -85,6 +85,7 @@ EXPORTED = ["hfx_create_basis", "hfx_build_quartets", "hfx_value_count", "hfx_bu
             "hfx_server_step", "hfx_server_poll", "hfx_server_release", "hfx_server_get_info", "hfx_server_destroy",
             "hfx_server_cancel", "hfx_server_inject_setup_failure", "hfx_periodic_images", "hfx_periodic_pack_host",
             "hfx_create_basis_periodic", "hfx_basis_atoms", "hfx_periodic_extend", "hfx_distance_pattern",
+            "hfx_server_submit_periodic",
             "hfx_destroy_basis", "hfx_destroy_quartets", "hfx_last_error"]
 
 _lib = None
@@ -92,7 +93,7 @@ _lib = None
 
 class ServerOpts(ctypes.Structure):
     _fields_ = [("mem_budget", ctypes.c_longlong), ("max_active", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("reserved", ctypes.c_int * 4)]
+                ("incremental", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 class RequestInfo(ctypes.Structure):
@@ -157,6 +158,8 @@ def load(path: str = LIB_PATH):
     lib.hfx_server_create.argtypes = [ctypes.POINTER(ServerOpts), V, PV]
     lib.hfx_server_submit.argtypes = [V, ctypes.POINTER(ShellDesc), I, V, I, ctypes.POINTER(Pattern),
                                       ctypes.POINTER(Opts), I, V, V, ctypes.POINTER(LL)]
+    lib.hfx_server_submit_periodic.argtypes = [V, ctypes.POINTER(ShellDesc), I, V, I, V, D, ctypes.POINTER(Pattern),
+                                               ctypes.POINTER(Opts), I, V, V, ctypes.POINTER(LL)]
     lib.hfx_server_step.argtypes = [V, ctypes.POINTER(I)]
     lib.hfx_server_poll.argtypes = [V, LL, ctypes.POINTER(RequestInfo), V]
     lib.hfx_server_release.argtypes = [V, LL]
@@ -634,9 +637,10 @@ class PeriodicBasis:
 class Server:
     """Owns an hfx_server (continuous batching of SCF-like requests)."""
 
-    def __init__(self, mem_budget=0, max_active=64, use_graph=False, stream=None):
+    def __init__(self, mem_budget=0, max_active=64, use_graph=False, incremental=False, stream=None):
         o = ServerOpts()
         o.mem_budget, o.max_active, o.use_graph = int(mem_budget), int(max_active), int(bool(use_graph))
+        o.incremental = int(bool(incremental))
         h = ctypes.c_void_p()
         _check(load().hfx_server_create(ctypes.byref(o), _stream(stream), ctypes.byref(h)))
         self.handle = h
@@ -655,6 +659,24 @@ class Server:
                                         ctypes.byref(inp.pattern), ctypes.byref(opts), len(P_list), _ptr(P),
                                         _ptr(K), ctypes.byref(t)))
         self._req[t.value] = (inp, P, K, len(P_list))
+        return t.value
+
+    def submit_periodic(self, per: "Periodic", opts: Opts, P_list, want_K=True) -> int:
+        """Queue a periodic cell (``Periodic``: home cell, lattice, r_ext and its
+        density pattern) with one dense home-cell density matrix per build."""
+        nv = per.n_values
+        P = np.empty((len(P_list), nv))
+        for i, Pi in enumerate(P_list):
+            P[i] = per.pack(Pi)
+        K = np.zeros(nv) if want_K else None
+        home = per.home
+        descs, keep = shell_descs(home.shell_l, home.shell_atom, home.prim_off, home.alpha, home.coef)
+        xyz = np.ascontiguousarray(home.atom_xyz, dtype=np.float64)
+        t = ctypes.c_longlong()
+        _check(load().hfx_server_submit_periodic(self.handle, descs, len(home.shell_l), _ptr(xyz), int(home.n_atoms),
+                                                 _ptr(per.lattice), per.r_ext, ctypes.byref(per.pattern),
+                                                 ctypes.byref(opts), len(P_list), _ptr(P), _ptr(K), ctypes.byref(t)))
+        self._req[t.value] = ((descs, keep, xyz, per), P, K, len(P_list))
         return t.value
 
     def step(self) -> int:

@@ -189,3 +189,79 @@ def test_cancel_and_injected_setup_failure():
     assert ri.state == hfx.HFX_REQ_CANCELLED and ri.builds_done == 1
     assert srv2.info().used_bytes == 0 and srv2.info().n_active == 0
     srv2.release(u)
+
+
+def test_incremental_server_matches_direct_delta_builds():
+    """With incremental builds every build after a request's first is
+    K(P_{n-1}) + K(P_n - P_{n-1}) (hfx_build_K_delta through the batched path):
+    its energies equal those of the direct API's same sequence (1e-10 |E|, the
+    same arithmetic in a different atomic order), stay within 1e-7 Ha of full
+    builds, and the request also gives them in a mix."""
+    import torch
+    from paper_2009_03555_gb300 import hfx
+    reqs = _requests(n_builds=(4, 3, 3))
+    opts = _opts(0)
+    srv = hfx.Server(incremental=True)
+    res = _run(srv, reqs, opts)
+    full = _run(hfx.Server(), reqs, opts)
+    for i, (s, mask, Ps) in enumerate(reqs):
+        q = hfx.Quartets(hfx.Basis(s), opts, mask)
+        dev = torch.device("cuda")
+        vals = []
+        for P in Ps:
+            v = torch.empty(q.n_values, dtype=torch.float64, device=dev)
+            q.pack(torch.from_numpy(np.ascontiguousarray(P)).to(dev), v)
+            vals.append(v)
+        K = torch.empty_like(vals[0])
+        q.build_K(vals[0], K)
+        E = [q.exchange_energy(vals[0], K)]
+        for n in range(1, len(Ps)):
+            q.build_K_delta(vals[n] - vals[n - 1], K)
+            E.append(q.exchange_energy(vals[n], K))
+        info, Es, Ks = res[i]
+        assert info.state == hfx.HFX_REQ_DONE and info.builds_done == len(Ps)
+        np.testing.assert_allclose(Es, E, rtol=1e-10, atol=0)
+        np.testing.assert_allclose(Es, full[i][1], rtol=0, atol=1e-7)
+        assert np.abs(Ks - K.cpu().numpy()).max() <= 1e-10 * np.abs(Ks).max()
+
+
+def test_periodic_request_alone_and_in_mix():
+    """A periodic cell served (hfx_server_submit_periodic) gives the per-cell
+    energies of the library's periodic path built directly, alone and mixed
+    with molecular requests."""
+    import torch
+    from paper_2009_03555_gb300 import hfx
+    A = np.array([[6.0, 0.0, 0.0], [1.0, 6.0, 0.0], [0.0, 1.0, 6.0]])
+    cell = synth.periodic_cell(3, A, sub=35, recipe={"C": [0, 1, 2], "H": [0, 1]})
+    P0 = synth.periodic_density_matrix(cell, cutoff=4.0, sub=35)
+    rng = np.random.default_rng(2009_03555 + 77)
+    Ps = [P0, synth.perturb_density(P0, rng), None]
+    Ps[2] = synth.perturb_density(Ps[1], rng)
+    per = hfx.Periodic(cell, A, r_ext=5.0, r_P=4.0)
+    opts = _opts(0)
+    # direct
+    q = per.quartets(opts)
+    dev = torch.device("cuda")
+    E_dir = []
+    for P in Ps:
+        Pv = torch.from_numpy(per.pack(P)).to(dev)
+        Kv = torch.empty_like(Pv)
+        q.build_K(Pv, Kv)
+        E_dir.append(q.exchange_energy(Pv, Kv))
+    for mix in (False, True):
+        srv = hfx.Server()
+        t = srv.submit_periodic(per, opts, Ps)
+        others = {}
+        if mix:
+            for i, (s, mask, Pm) in enumerate(_requests()):
+                others[i] = srv.submit(s, mask, opts, Pm)
+        for _ in range(100):
+            srv.step()
+            if srv.info().n_active == 0 and srv.info().n_queued == 0:
+                break
+        info, E = srv.poll(t)
+        assert info.state == hfx.HFX_REQ_DONE, info.status
+        np.testing.assert_allclose(E, E_dir, rtol=1e-12, atol=0)
+        assert np.all(srv.K_values(t)[per.n_home_values:] == 0.0)
+        for tt in others.values():
+            assert srv.poll(tt)[0].state == hfx.HFX_REQ_DONE
