@@ -86,6 +86,10 @@ typedef struct {
   int promote_prims;          /* MIXED with promotion: 1 = promote per primitive quartet: of a quartet above
                                  fp64_promote_bound only the primitive quartets with bound_ab bound_cd P_scr
                                  above it run in FP64, the others in FP32 */
+  int spherical;              /* 1: P and K in real solid harmonics, 2l+1 per shell (Sec. 2: the Cartesian
+                                 integrals are transformed to spherical harmonics); order per d shell:
+                                 xy, yz, z^2, xz, x^2-y^2 (s, p unchanged); not for batches or the server */
+  int reserved2[3];
 } hfx_opts;
 
 /* Atom-pair block pattern: CSR over atoms (host arrays). */
@@ -143,7 +147,8 @@ hfx_status hfx_create_basis(const hfx_shell_desc* shells, int n_shells, const do
 hfx_status hfx_build_quartets(hfx_basis* basis, const hfx_opts* opts, const hfx_pattern* pattern, void* stream,
                               hfx_quartets** out);
 
-/* Number of doubles in the P / K value arrays of this pattern. */
+/* Number of doubles in the P / K value arrays of this pattern (in the
+ * spherical layout when opts.spherical). */
 long long hfx_value_count(const hfx_quartets* q);
 
 /* One exchange build (Algorithm 4): zero K, shell-pair Pmax of P, screened ERI
@@ -178,7 +183,8 @@ hfx_status hfx_build_K_delta(hfx_quartets* q, const double* dP_val, double* K_va
 hfx_status hfx_exchange_energy(hfx_quartets* q, const double* P_val, const double* K_val, double* E_x,
                                void* stream);
 
-/* Dense <-> block-sparse conversion on the device (dense: nbf x nbf row-major).
+/* Dense <-> block-sparse conversion on the device (dense: nbf x nbf row-major,
+ * nbf counting 2l+1 functions per shell when opts.spherical).
  * Pack reads only the pattern's blocks; unpack writes zeros outside it. */
 hfx_status hfx_pack_dense(const hfx_quartets* q, const double* dense, double* val, void* stream);
 hfx_status hfx_unpack_dense(const hfx_quartets* q, const double* val, double* dense, void* stream);

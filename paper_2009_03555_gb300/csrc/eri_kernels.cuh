@@ -419,6 +419,9 @@ __device__ __forceinline__ void warp_sort_desc(unsigned (&k)[NPER]) {
 #define HFX_SORT_CAP 256
 #endif
 constexpr int kSortCap = HFX_SORT_CAP;
+#ifndef HFX_PT_MINB
+#define HFX_PT_MINB 1
+#endif
 static_assert(kSortCap >= 32 && kSortCap <= 256 && (kSortCap & (kSortCap - 1)) == 0, "HFX_SORT_CAP");
 
 // Persistent exchange-build kernel for one quartet class.  The device work
@@ -436,7 +439,7 @@ static_assert(kSortCap >= 32 && kSortCap <= 256 && (kSortCap & (kSortCap - 1)) =
 // registers) and runs them in rounds of 32 in that order: the lanes of a
 // round then have quartets of nearly equal length.
 template <class C, typename R>
-__global__ void __launch_bounds__(kThreadsK) k_build_K(const BuildArgs a) {
+__global__ void __launch_bounds__(kThreadsK, HFX_PT_MINB) k_build_K(const BuildArgs a) {
   constexpr int NPER = kSortCap / 32;
   __shared__ int4 s_queue[kWarpsK][kSortCap + 32];
   __shared__ unsigned s_key[kWarpsK][kSortCap];
@@ -912,6 +915,12 @@ __global__ void __launch_bounds__(kThreadsCoop) k_build_K_coop(const BuildArgs a
 #ifndef HFX_WIDE_MIN_FLOPS
 #define HFX_WIDE_MIN_FLOPS 2000
 #endif
+// Lockstep classes below HFX_WIDE_MIN_FLOPS run blocks of HFX_MID_WARPS warps
+// (4: three blocks per SM; 12: one block per SM, all twelve warps in one
+// lockstep stream).
+#ifndef HFX_MID_WARPS
+#define HFX_MID_WARPS 4
+#endif
 template <class C, typename R>
 struct SplitShape {
   static constexpr bool LOCKSTEP = C::VRR_FLOPS >= HFX_LOCKSTEP_MIN_FLOPS;
@@ -919,9 +928,10 @@ struct SplitShape {
   // 4-warp blocks only: (dd|dd) in FP64 (6254 slots x 8 B); in FP32 its eight
   // warps take 205 KB of shared memory, like the FP64 four
   static constexpr bool BIG_HRR = C::Coop::HRR_SLOTS * sizeof(R) > 4096 * sizeof(double);
-  static constexpr int WARPS = (C::VRR_FLOPS >= HFX_WIDE_MIN_FLOPS && !BIG_HRR) ? 8 : 4;
+  static constexpr int WARPS = (C::VRR_FLOPS >= HFX_WIDE_MIN_FLOPS && !BIG_HRR) ? 8
+                               : ((LOCKSTEP && !BIG_HRR) ? HFX_MID_WARPS : 4);
   static constexpr int THREADS = 32 * WARPS;
-  static constexpr int MIN_BLOCKS = (WARPS == 8 || BIG_HRR) ? 1 : 3;
+  static constexpr int MIN_BLOCKS = (WARPS >= 8 || BIG_HRR) ? 1 : 3;
 };
 
 template <class C, typename R>

@@ -160,6 +160,16 @@ struct hfx_quartets_s {
   DBuf<double> pmax;                       // n_shells x n_shells
   DBuf<double> scratch;                    // energy accumulator
   DBuf<double> delta_K;                    // K of a density difference (hfx_build_K_delta)
+  // spherical-harmonic layout (opts.spherical): the caller's P and K hold
+  // 2l+1 real solid harmonics per shell; the build runs on Cartesian copies
+  long long n_values_ext = 0;              // values of the caller's arrays
+  DBuf<long long> blk_val_off_sph;         // block offsets in the spherical layout
+  DBuf<int> atom_nf_sph;
+  DBuf<long long> afoff_cart, afoff_sph;   // first function of each atom in each layout
+  DBuf<int4> fmap_cart, fmap_sph;          // per function: (other layout's shell offset in the atom, l, component)
+  DBuf<double> P_cart, K_cart;
+  std::vector<long long> h_afoff_sph;
+  long long nbf_sph = 0;
   float ms_setup = 0.f;
   float ms_setup_phase[4] = {0.f, 0.f, 0.f, 0.f};
   SysArgs h_sys{};  // this system's entry of a build table (P, K unset)
@@ -460,6 +470,56 @@ __global__ void k_pack(int n_blocks, const int* bx, const int* by, const long lo
   }
 }
 
+
+// Real solid harmonics of a d shell from its Cartesian components (xx, xy, xz,
+// yy, yz, zz; normalisation of the x^2 component), in the order
+// xy, yz, z^2, xz, x^2 - y^2:
+//   sqrt3 xy, sqrt3 yz, (2 zz - xx - yy)/2, sqrt3 xz, sqrt3/2 (xx - yy);
+// with the Cartesian normalisation every one of them has unit norm.  s and p
+// shells are unchanged (the p order x, y, z is kept).
+__device__ __forceinline__ double sph_coef(int l, int m, int c) {
+  if (l < 2) return m == c ? 1.0 : 0.0;
+  const double r3 = 1.7320508075688772935, h3 = 0.86602540378443864676;
+  switch (m) {
+    case 0: return c == 1 ? r3 : 0.0;
+    case 1: return c == 4 ? r3 : 0.0;
+    case 2: return c == 5 ? 1.0 : ((c == 0 || c == 3) ? -0.5 : 0.0);
+    case 3: return c == 2 ? r3 : 0.0;
+    default: return c == 0 ? h3 : (c == 3 ? -h3 : 0.0);
+  }
+}
+
+// One layout change of every pattern block: to_sph: out = T in T^T (Cartesian
+// to spherical, K); otherwise out = T^T in T (spherical to Cartesian, P).
+// map_out[afoff_out[X] + r] = (offset of r's shell in atom X's input layout,
+// l, component of r).
+__global__ void k_sph_transform(int n_blocks, const int* __restrict__ bx, const int* __restrict__ by,
+                                const long long* __restrict__ off_in, const long long* __restrict__ off_out,
+                                const long long* __restrict__ afoff_out, const int* __restrict__ nf_in,
+                                const int* __restrict__ nf_out, const int4* __restrict__ map_out, int to_sph,
+                                const double* __restrict__ in, double* __restrict__ out) {
+  const int b = blockIdx.x;
+  if (b >= n_blocks) return;
+  const int X = bx[b], Y = by[b];
+  const int nXo = nf_out[X], nYo = nf_out[Y], nYi = nf_in[Y];
+  for (int e = threadIdx.x; e < nXo * nYo; e += blockDim.x) {
+    const int r = e / nYo, c = e % nYo;
+    const int4 mr = map_out[afoff_out[X] + r], mc = map_out[afoff_out[Y] + c];
+    const int nr = to_sph ? (mr.y + 1) * (mr.y + 2) / 2 : 2 * mr.y + 1;  // input components of the shells
+    const int nc = to_sph ? (mc.y + 1) * (mc.y + 2) / 2 : 2 * mc.y + 1;
+    double acc = 0.0;
+    for (int i = 0; i < nr; ++i) {
+      const double wr = to_sph ? sph_coef(mr.y, mr.z, i) : sph_coef(mr.y, i, mr.z);
+      if (wr == 0.0) continue;
+      const double* row = in + off_in[b] + (long long)(mr.x + i) * nYi + mc.x;
+      for (int j = 0; j < nc; ++j) {
+        const double wc = to_sph ? sph_coef(mc.y, mc.z, j) : sph_coef(mc.y, j, mc.z);
+        acc = fma(wr * wc, row[j], acc);
+      }
+    }
+    out[off_out[b] + e] = acc;
+  }
+}
 
 // ---------------------------------------------------------------- batched
 // Small kernels of a build over every system of a batch at once: 2-D grids,
@@ -1024,10 +1084,46 @@ static hfx_status setup_pattern(hfx_quartets_s* q, const hfx_pattern* pat, cudaS
   }
   q->n_atoms = na;
   q->n_values = nv;
+  q->n_values_ext = nv;
   q->n_blocks = (int)bx.size();
   HFX_CK(upload(q->blk_off, off, s));
   HFX_CK(upload(q->blk_x, bx, s));
   HFX_CK(upload(q->blk_y, by, s));
+  if (q->opts.spherical) {
+    // caller's layout: 2l+1 solid harmonics per shell, blocks in the same order
+    std::vector<int> nfs((size_t)na, 0), loc_sph((size_t)b->n_shells);
+    for (int i = 0; i < b->n_shells; ++i) {
+      loc_sph[(size_t)i] = nfs[(size_t)b->h_atom[i]];
+      nfs[(size_t)b->h_atom[i]] += 2 * b->h_l[i] + 1;
+    }
+    std::vector<long long> afs((size_t)na + 1, 0);
+    for (int X = 0; X < na; ++X) afs[(size_t)X + 1] = afs[(size_t)X] + nfs[(size_t)X];
+    std::vector<int4> mc((size_t)b->nbf), ms((size_t)afs[(size_t)na]);
+    for (int i = 0; i < b->n_shells; ++i) {
+      const int X = b->h_atom[i], l = b->h_l[i];
+      for (int c = 0; c < ncart(l); ++c)
+        mc[(size_t)(b->h_atom_foff[X] + b->h_loc[i] + c)] = make_int4(loc_sph[(size_t)i], l, c, 0);
+      for (int m = 0; m < 2 * l + 1; ++m)
+        ms[(size_t)(afs[(size_t)X] + loc_sph[(size_t)i] + m)] = make_int4(b->h_loc[i], l, m, 0);
+    }
+    std::vector<long long> bos;
+    long long nvs = 0;
+    for (size_t k = 0; k < bx.size(); ++k) {
+      bos.push_back(nvs);
+      nvs += (long long)nfs[(size_t)bx[k]] * nfs[(size_t)by[k]];
+    }
+    q->n_values_ext = nvs;
+    q->nbf_sph = afs[(size_t)na];
+    q->h_afoff_sph = afs;
+    HFX_CK(upload(q->blk_val_off_sph, bos, s));
+    HFX_CK(upload(q->atom_nf_sph, nfs, s));
+    HFX_CK(upload(q->afoff_cart, b->h_atom_foff, s));
+    HFX_CK(upload(q->afoff_sph, afs, s));
+    HFX_CK(upload(q->fmap_cart, mc, s));
+    HFX_CK(upload(q->fmap_sph, ms, s));
+    HFX_CK(q->P_cart.alloc((size_t)std::max<long long>(nv, 1)));
+    HFX_CK(q->K_cart.alloc((size_t)std::max<long long>(nv, 1)));
+  }
   HFX_CK(upload(q->blk_val_off, bo, s));
   return HFX_OK;
 }
@@ -1246,7 +1342,7 @@ hfx_status hfx_build_quartets(hfx_basis* b, const hfx_opts* opts_in, const hfx_p
 
 void hfx_destroy_quartets(hfx_quartets* q) { delete q; }
 
-long long hfx_value_count(const hfx_quartets* q) { return q ? q->n_values : -1; }
+long long hfx_value_count(const hfx_quartets* q) { return q ? q->n_values_ext : -1; }
 
 }  // extern "C"
 
@@ -1352,11 +1448,24 @@ long long hfx_setup_bytes_estimate(const hfx_shell_desc* shells, int n_shells, c
 hfx_status hfx_build_K(hfx_quartets* q, const double* P, double* K, void* stream) {
   if (!q || !P || !K) return fail(HFX_ERR_INVALID_ARG, "NULL argument");
   Plan& pl = q->plan;
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool sph = q->opts.spherical != 0;
+  if (sph && q->n_blocks > 0)  // P = T^T P_sph T (Cartesian copy)
+    k_sph_transform<<<q->n_blocks, 128, 0, s>>>(q->n_blocks, q->blk_x.p, q->blk_y.p, q->blk_val_off_sph.p,
+                                                q->blk_val_off.p, q->afoff_cart.p, q->atom_nf_sph.p,
+                                                q->basis->atom_nf.p, q->fmap_cart.p, 0, P, q->P_cart.p);
   HFX_CK(cudaEventSynchronize(pl.sys_copied));
   pl.h_sys[0] = q->h_sys;
-  pl.h_sys[0].P = P;
-  pl.h_sys[0].K = K;
-  return plan_build(pl, (cudaStream_t)stream, false, true);
+  pl.h_sys[0].P = sph ? q->P_cart.p : P;
+  pl.h_sys[0].K = sph ? q->K_cart.p : K;
+  const hfx_status st = plan_build(pl, s, false, true);
+  if (st != HFX_OK || !sph) return st;
+  if (q->n_blocks > 0)  // K_sph = T K T^T
+    k_sph_transform<<<q->n_blocks, 128, 0, s>>>(q->n_blocks, q->blk_x.p, q->blk_y.p, q->blk_val_off.p,
+                                                q->blk_val_off_sph.p, q->afoff_sph.p, q->basis->atom_nf.p,
+                                                q->atom_nf_sph.p, q->fmap_sph.p, 1, q->K_cart.p, K);
+  HFX_CK(cudaGetLastError());
+  return HFX_OK;
 }
 
 hfx_status hfx_build_K_shard(hfx_quartets* q, const double* P, double* K, int rank, int n_ranks, void* stream) {
@@ -1374,12 +1483,13 @@ hfx_status hfx_build_K_shard(hfx_quartets* q, const double* P, double* K, int ra
 hfx_status hfx_build_K_delta(hfx_quartets* q, const double* dP, double* K, void* stream) {
   if (!q || !dP || !K) return fail(HFX_ERR_INVALID_ARG, "NULL argument");
   cudaStream_t s = (cudaStream_t)stream;
-  if (q->delta_K.p == nullptr || q->delta_K.n < (size_t)q->n_values) HFX_CK(q->delta_K.alloc((size_t)q->n_values));
+  const long long nv = q->n_values_ext;
+  if (q->delta_K.p == nullptr || q->delta_K.n < (size_t)nv) HFX_CK(q->delta_K.alloc((size_t)nv));
   const hfx_status st = hfx_build_K(q, dP, q->delta_K.p, stream);
   if (st != HFX_OK) return st;
-  if (q->n_values > 0) {
-    const int blocks = (int)std::max<long long>(1, std::min<long long>(4LL * q->n_sm, (q->n_values + 255) / 256));
-    k_axpy<<<blocks, 256, 0, s>>>(q->n_values, q->delta_K.p, K);
+  if (nv > 0) {
+    const int blocks = (int)std::max<long long>(1, std::min<long long>(4LL * q->n_sm, (nv + 255) / 256));
+    k_axpy<<<blocks, 256, 0, s>>>(nv, q->delta_K.p, K);
     HFX_CK(cudaGetLastError());
   }
   return HFX_OK;
@@ -1389,9 +1499,11 @@ hfx_status hfx_exchange_energy(hfx_quartets* q, const double* P, const double* K
   if (!q || !P || !K || !E_x) return fail(HFX_ERR_INVALID_ARG, "NULL argument");
   cudaStream_t s = (cudaStream_t)stream;
   HFX_CK(cudaMemsetAsync(q->scratch.p, 0, sizeof(double), s));
-  const int blocks = std::max(1, std::min<int>(4 * q->n_sm, (int)((q->n_values / 2 + 255) / 256)));
+  // over the caller's layout (tr(P K) is the same in both: the transforms are orthogonal per shell block)
+  const long long nv = q->n_values_ext;
+  const int blocks = std::max(1, std::min<int>(4 * q->n_sm, (int)((nv / 2 + 255) / 256)));
   const int vec = ((reinterpret_cast<uintptr_t>(P) | reinterpret_cast<uintptr_t>(K)) & 15) == 0;
-  k_dot<<<blocks, 256, 0, s>>>(q->n_values, P, K, vec, q->scratch.p);
+  k_dot<<<blocks, 256, 0, s>>>(nv, P, K, vec, q->scratch.p);
   double h = 0.0;
   HFX_CK(cudaMemcpyAsync(&h, q->scratch.p, sizeof(double), cudaMemcpyDeviceToHost, s));
   HFX_CK(cudaStreamSynchronize(s));
@@ -1399,28 +1511,29 @@ hfx_status hfx_exchange_energy(hfx_quartets* q, const double* P, const double* K
   return HFX_OK;
 }
 
-hfx_status hfx_pack_dense(const hfx_quartets* q, const double* dense, double* val, void* stream) {
-  if (!q || !dense || !val) return fail(HFX_ERR_INVALID_ARG, "NULL argument");
+// Dense <-> values in the caller's layout (Cartesian, or spherical harmonics).
+static hfx_status pack_dense(const hfx_quartets* q, double* dense, double* val, int unpack, cudaStream_t s) {
+  const bool sph = q->opts.spherical != 0;
   DBuf<long long> afoff;
-  cudaStream_t s = (cudaStream_t)stream;
-  HFX_CK(upload(afoff, q->basis->h_atom_foff, s));
-  k_pack<<<q->n_blocks, 128, 0, s>>>(q->n_blocks, q->blk_x.p, q->blk_y.p, q->blk_val_off.p, afoff.p,
-                                     q->basis->atom_nf.p, q->basis->nbf, const_cast<double*>(dense), val, 0);
+  HFX_CK(upload(afoff, sph ? q->h_afoff_sph : q->basis->h_atom_foff, s));
+  const long long nbf = sph ? q->nbf_sph : (long long)q->basis->nbf;
+  if (unpack) HFX_CK(cudaMemsetAsync(dense, 0, (size_t)nbf * (size_t)nbf * sizeof(double), s));
+  if (q->n_blocks > 0)
+    k_pack<<<q->n_blocks, 128, 0, s>>>(q->n_blocks, q->blk_x.p, q->blk_y.p,
+                                       sph ? q->blk_val_off_sph.p : q->blk_val_off.p, afoff.p,
+                                       sph ? q->atom_nf_sph.p : q->basis->atom_nf.p, nbf, dense, val, unpack);
   HFX_CK(cudaStreamSynchronize(s));
   return HFX_OK;
 }
 
+hfx_status hfx_pack_dense(const hfx_quartets* q, const double* dense, double* val, void* stream) {
+  if (!q || !dense || !val) return fail(HFX_ERR_INVALID_ARG, "NULL argument");
+  return pack_dense(q, const_cast<double*>(dense), val, 0, (cudaStream_t)stream);
+}
+
 hfx_status hfx_unpack_dense(const hfx_quartets* q, const double* val, double* dense, void* stream) {
   if (!q || !dense || !val) return fail(HFX_ERR_INVALID_ARG, "NULL argument");
-  DBuf<long long> afoff;
-  cudaStream_t s = (cudaStream_t)stream;
-  HFX_CK(upload(afoff, q->basis->h_atom_foff, s));
-  const size_t nbf = (size_t)q->basis->nbf;
-  HFX_CK(cudaMemsetAsync(dense, 0, nbf * nbf * sizeof(double), s));
-  k_pack<<<q->n_blocks, 128, 0, s>>>(q->n_blocks, q->blk_x.p, q->blk_y.p, q->blk_val_off.p, afoff.p,
-                                     q->basis->atom_nf.p, q->basis->nbf, dense, const_cast<double*>(val), 1);
-  HFX_CK(cudaStreamSynchronize(s));
-  return HFX_OK;
+  return pack_dense(q, dense, const_cast<double*>(val), 1, (cudaStream_t)stream);
 }
 
 hfx_status hfx_eval_quartets(hfx_basis* b, int kernel, double omega, int precision, int n, const int* quartets,
@@ -1537,7 +1650,7 @@ hfx_status hfx_get_stats(const hfx_quartets* q, hfx_stats* out) {
   for (int c = 0; c < 6; ++c) out->n_pairs_significant[c] = q->n_pairs[c];
   for (int c = 0; c < HFX_NCLASS; ++c) out->n_quartets_schwarz[c] = q->n_quartets[c];
   out->n_prim_pairs = q->n_prim_pairs;
-  out->n_values = q->n_values;
+  out->n_values = q->n_values_ext;
   out->ms_setup = q->ms_setup;
   for (int k = 0; k < 4; ++k) out->ms_setup_phase[k] = q->ms_setup_phase[k];
   plan_stats(const_cast<hfx_quartets_s*>(q)->plan, out);
@@ -1562,8 +1675,10 @@ hfx_status hfx_batch_create(hfx_quartets* const* members, int n, void* stream, h
     if (oi.kernel != o0.kernel || oi.omega != o0.omega || oi.precision != o0.precision ||
         oi.screen != o0.screen || oi.tau != o0.tau || oi.density_screen != o0.density_screen ||
         oi.eps != o0.eps || oi.prim_cutoff != o0.prim_cutoff ||
-        !(oi.fp64_promote_bound == o0.fp64_promote_bound) || oi.promote_min_l != o0.promote_min_l)
+        !(oi.fp64_promote_bound == o0.fp64_promote_bound) || oi.promote_min_l != o0.promote_min_l ||
+        oi.prim_density_screen != o0.prim_density_screen || oi.promote_prims != o0.promote_prims)
       return fail(HFX_ERR_INVALID_ARG, "batch members must share kernel, precision and screening options");
+    if (oi.spherical) return fail(HFX_ERR_UNSUPPORTED, "batches take Cartesian quartet lists only");
     b->members.push_back(members[i]);
   }
   hfx_status st = plan_alloc(b->plan, b->members, members[0]->n_sm);

@@ -310,6 +310,7 @@ hfx_status submit_common(hfx_server* s, const hfx_shell_desc* shells, int n_shel
                          int n_atoms, const hfx_shell_desc* pattern_shells, int n_pattern_shells,
                          const hfx_pattern* pattern, const hfx_opts* opts, int n_builds, const double* P_host,
                          double* K_out, long long* ticket, std::unique_ptr<Request>& r) {
+  if (opts->spherical) return srv_fail(HFX_ERR_UNSUPPORTED, "the server takes Cartesian requests only");
   const long long nv = hfx_pattern_value_count(pattern_shells, n_pattern_shells, pattern);
   if (nv < 0) return srv_fail(HFX_ERR_INVALID_ARG, "inconsistent shells or pattern");
   r->ticket = s->next_ticket++;

@@ -46,7 +46,8 @@ class Opts(ctypes.Structure):
                 ("tau", ctypes.c_double), ("density_screen", ctypes.c_int), ("eps", ctypes.c_double),
                 ("prim_cutoff", ctypes.c_double), ("precision", ctypes.c_int),
                 ("fp64_promote_bound", ctypes.c_double), ("n_block", ctypes.c_int),
-                ("promote_min_l", ctypes.c_int), ("prim_density_screen", ctypes.c_int), ("promote_prims", ctypes.c_int)]
+                ("promote_min_l", ctypes.c_int), ("prim_density_screen", ctypes.c_int), ("promote_prims", ctypes.c_int),
+                ("spherical", ctypes.c_int), ("reserved2", ctypes.c_int * 3)]
 
 
 class Pattern(ctypes.Structure):
@@ -246,7 +247,7 @@ def hfx_create_basis(shell_l, shell_atom, prim_off, alpha, coef, atom_xyz, strea
 
 def make_opts(kernel=HFX_KERNEL_ERFC, omega=0.11, screen=True, tau=1e-8, density_screen=True, eps=None,
               prim_cutoff=1e-15, precision=HFX_PREC_FP64, fp64_promote_bound=math.inf, n_block=128,
-              promote_min_l=0, prim_density_screen=False, promote_prims=False) -> Opts:
+              promote_min_l=0, prim_density_screen=False, promote_prims=False, spherical=False) -> Opts:
     o = Opts()
     o.kernel, o.omega, o.screen, o.tau = int(kernel), float(omega), int(bool(screen)), float(tau)
     o.density_screen = int(bool(density_screen))
@@ -256,6 +257,7 @@ def make_opts(kernel=HFX_KERNEL_ERFC, omega=0.11, screen=True, tau=1e-8, density
     o.promote_min_l = int(promote_min_l)
     o.prim_density_screen = int(bool(prim_density_screen))
     o.promote_prims = int(bool(promote_prims))
+    o.spherical = int(bool(spherical))
     return o
 
 
