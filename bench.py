@@ -74,19 +74,19 @@ def fp64_prologue_flops(L, kernel):
 
 # FP32 flops of the double-single operations of boys_ds.cuh (FMA = 2;
 # TwoSum 6, Fast-TwoSum 3)
-DS_ADD, DS_MUL, DS_MULF, DS_ADDF = 11, 10, 8, 10
-DS_RCP = 1 + 2 * DS_MULF + 2 * DS_ADDF            # seed, one Newton step: 37
-DS_RSQRT = 1 + 3 * DS_MULF + 2 * DS_ADDF + 1      # seed, one Newton step: 46
+DS_ADD, DS_MUL, DS_MULF, DS_ADDF = 11, 7, 5, 10  # products are left unnormalised
+DS_RCP = 1 + 2 * DS_MULF + 2 * DS_ADDF            # seed, one Newton step: 31
+DS_RSQRT = 1 + 3 * DS_MULF + 2 * DS_ADDF + 1      # seed, one Newton step: 37
 
 
 def ds_prologue_flops(L, kernel):
     """FP32 flops of the same prologue in double-single arithmetic
     (prologue_ds and boys_ds in boys_ds.cuh).  Argument and prefactor: p+q,
     1/(p+q), rho, three PQ components with their squares, T, prefactor
-    (reciprocal square root and three products) = 246.  Boys: grid offset 12,
-    Taylor series of F_L 86; for L > 0 exp(-T) 78 and 31 per downward step.
-    Coulomb: 11 per G_m.  erfc: attenuation factor 58, f T 10, f^{1/2} 56, a
-    second Boys evaluation, 42 per G_m."""
+    (reciprocal square root and three products) = 204.  Boys: grid offset 12,
+    Taylor series of F_L 74; for L > 0 exp(-T) 66 and 25 per downward step.
+    Coulomb: 8 per G_m.  erfc: attenuation factor 49, f T 7, f^{1/2} 44, a
+    second Boys evaluation, 33 per G_m."""
     base = DS_ADD + DS_RCP + 2 * DS_MUL + 3 * (6 + 2 + 3 + DS_MUL + DS_ADD) + DS_MUL + DS_RSQRT + DS_MUL + 2 * DS_MULF
     boys = 12 + 4 + DS_MULF + DS_ADD + 3 * (DS_MUL + DS_ADD)
     if L > 0:

@@ -89,7 +89,12 @@ typedef struct {
   int spherical;              /* 1: P and K in real solid harmonics, 2l+1 per shell (Sec. 2: the Cartesian
                                  integrals are transformed to spherical harmonics); order per d shell:
                                  xy, yz, z^2, xz, x^2-y^2 (s, p unchanged); not for batches or the server */
-  int reserved2[3];
+  double extent_eps;          /* > 0: distance screening (Sec. 2, with the NAO cutoff radii replaced by Gaussian
+                                 extents): shell S reaches R_S = sqrt(ln(1/extent_eps) / alpha_min(S)), the radius
+                                 where its most diffuse primitive exp(-alpha r^2) falls to extent_eps; shell pairs
+                                 farther apart than R_A + R_B are dropped before their Schwarz bounds are formed.
+                                 0: off */
+  int reserved2[2];
 } hfx_opts;
 
 /* Atom-pair block pattern: CSR over atoms (host arrays). */
@@ -118,6 +123,7 @@ typedef struct {
   long long n_prim_quartets_pass[2][21]; /* primitive quartets evaluated */
   float ms_class_pass[2][21];            /* device time of each class kernel (events) */
   float ms_setup_phase[4];               /* setup: pairs, Schwarz bounds, sorted pair lists, work queues */
+  long long n_pairs_distance;            /* shell pairs the distance screening kept (all pairs when it is off) */
 } hfx_stats;
 
 /* Class table entry (for throughput and roofline accounting). */

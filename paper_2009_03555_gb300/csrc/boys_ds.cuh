@@ -49,19 +49,24 @@ __device__ __forceinline__ ds ds_add(ds x, ds y) {
 
 __device__ __forceinline__ ds ds_sub(ds x, ds y) { return ds_add(x, {-y.hi, -y.lo}); }
 
+// Products are left unnormalised: (p, e) with p the FP32 product of the high
+// parts and e the rest, |e| within a few ulp of p.  Every operation here
+// reads such a pair correctly (the next product drops only the lo * lo term,
+// the next sum renormalises), so the final renormalisation of a product is
+// left out.
 __device__ __forceinline__ ds ds_mul(ds x, ds y) {
   const float p = __fmul_rn(x.hi, y.hi);
   float e = __fmaf_rn(x.hi, y.hi, -p);
   e = __fmaf_rn(x.hi, y.lo, e);
   e = __fmaf_rn(x.lo, y.hi, e);
-  return fast_two_sum(p, e);
+  return {p, e};
 }
 
 __device__ __forceinline__ ds ds_mulf(ds x, float f) {
   const float p = __fmul_rn(x.hi, f);
   float e = __fmaf_rn(x.hi, f, -p);
   e = __fmaf_rn(x.lo, f, e);
-  return fast_two_sum(p, e);
+  return {p, e};
 }
 
 __device__ __forceinline__ ds ds_addf(ds x, float f) {

@@ -419,9 +419,14 @@ __device__ __forceinline__ void warp_sort_desc(unsigned (&k)[NPER]) {
 #define HFX_SORT_CAP 256
 #endif
 constexpr int kSortCap = HFX_SORT_CAP;
+// HFX_PT_MINB (build switch, > 0) overrides every class's PT_MIN_BLOCKS.
 #ifndef HFX_PT_MINB
-#define HFX_PT_MINB 1
+#define HFX_PT_MINB 0
 #endif
+template <class C>
+struct PerThreadShape {
+  static constexpr int MIN_BLOCKS = HFX_PT_MINB > 0 ? HFX_PT_MINB : C::PT_MIN_BLOCKS;
+};
 static_assert(kSortCap >= 32 && kSortCap <= 256 && (kSortCap & (kSortCap - 1)) == 0, "HFX_SORT_CAP");
 
 // Persistent exchange-build kernel for one quartet class.  The device work
@@ -439,7 +444,7 @@ static_assert(kSortCap >= 32 && kSortCap <= 256 && (kSortCap & (kSortCap - 1)) =
 // registers) and runs them in rounds of 32 in that order: the lanes of a
 // round then have quartets of nearly equal length.
 template <class C, typename R>
-__global__ void __launch_bounds__(kThreadsK, HFX_PT_MINB) k_build_K(const BuildArgs a) {
+__global__ void __launch_bounds__(kThreadsK, PerThreadShape<C>::MIN_BLOCKS) k_build_K(const BuildArgs a) {
   constexpr int NPER = kSortCap / 32;
   __shared__ int4 s_queue[kWarpsK][kSortCap + 32];
   __shared__ unsigned s_key[kWarpsK][kSortCap];

@@ -83,6 +83,13 @@ AX = "xyz"
 # recursion functions (their working set lives in local memory anyway)
 INLINE_MAX_ACC = 160
 
+# Blocks per SM the per-thread kernel of a class is compiled for (launch bound;
+# 3 caps it at 168 registers).  Measured on GB300 (100-atom HSE cluster, mixed):
+# three blocks are 17-20 % faster for (pp|ps), (ds|ds) and (dd|ss) and 3 % for
+# (dp|ps) despite some spilling, but 43 % slower for (pp|pp) and 6 % for
+# (ds|pp), which keep one.
+PT_MIN_BLOCKS = {(1, 1, 1, 0): 3, (2, 0, 2, 0): 3, (2, 2, 0, 0): 3, (2, 1, 1, 0): 3}
+
 
 class VRR:
     def __init__(self, la, lb, lc, ld):
@@ -257,6 +264,7 @@ def gen_class(ib, ik, la, lb, lc, ld):
     src.append(f"  static constexpr int NE = {len(v.E)}, NF = {len(v.F)}, NACC = {len(v.E) * len(v.F)};")
     src.append(f"  static constexpr int NOUT = {NA * NB * NC * ND};")
     src.append(f"  static constexpr int VRR_FLOPS = {v.flops}, HRR_FLOPS = {h.flops};")
+    src.append(f"  static constexpr int PT_MIN_BLOCKS = {PT_MIN_BLOCKS.get((la, lb, lc, ld), 1)};")
     inl = "__forceinline__" if len(v.E) * len(v.F) <= INLINE_MAX_ACC else "__noinline__"
     src.append("  template <typename R>")
     src.append(f"  __device__ {inl} static void vrr(const R* __restrict__ G, const VrrGeo<R>& g, R* __restrict__ acc,")

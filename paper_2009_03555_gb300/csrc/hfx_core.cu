@@ -79,6 +79,7 @@ struct hfx_basis_s {
   int n_home_atoms = 0, n_home_shells = 0;
   std::vector<int> h_ext_home, h_ext_shift;  // per atom: home atom and lattice shift (n1, n2, n3)
   std::vector<double> h_atom_xyz;            // atom positions (bohr)
+  std::vector<double> h_alpha;               // primitive exponents (shell S: h_poff[S] .. h_poff[S+1])
   std::vector<int> h_l, h_atom, h_np, h_poff, h_loc, h_atom_nf;
   std::vector<long long> h_sh_foff, h_atom_foff;
   DBuf<double> sh_xyz, alpha, coef, boys;
@@ -152,6 +153,7 @@ struct hfx_quartets_s {
   DBuf<PairRec> pairs[6];
   DBuf<PrimPair> prims[6];
   long long n_prim_pairs = 0;
+  long long n_pairs_distance = 0;          // shell pairs kept by the distance screening (all pairs if off)
   // batches per quartet class
   DBuf<Desc> desc[HFX_NCLASS];
   int n_desc[HFX_NCLASS] = {0};
@@ -960,6 +962,7 @@ hfx_status hfx_create_basis(const hfx_shell_desc* shells, int n_shells, const do
     b->max_nprim = std::max(b->max_nprim, d.nprim);
   }
   b->h_poff = poff;
+  b->h_alpha = alpha;
   b->h_atom_foff.assign(n_atoms + 1, 0);
   for (int a = 0; a < n_atoms; ++a) b->h_atom_foff[a + 1] = b->h_atom_foff[a] + b->h_atom_nf[a];
   b->nbf = (int)b->h_atom_foff[n_atoms];
@@ -1161,23 +1164,41 @@ hfx_status hfx_build_quartets(hfx_basis* b, const hfx_opts* opts_in, const hfx_p
   hfx_status st = setup_pattern(q, pattern, s);
   if (st != HFX_OK) return st;
 
-  // 1. all shell pairs, oriented l_A >= l_B
+  // 1. all shell pairs, oriented l_A >= l_B; with distance screening only the
+  //    pairs whose extents reach each other (Sec. 2: NAO/distance screening)
   const int ns = b->n_shells;
-  const long long npair_ll = (long long)ns * (ns + 1) / 2;
-  if (npair_ll > (1LL << 30)) return fail(HFX_ERR_UNSUPPORTED, "too many shell pairs");
-  const int npair = (int)npair_ll;
+  const long long npair_all = (long long)ns * (ns + 1) / 2;
+  if (npair_all > (1LL << 30)) return fail(HFX_ERR_UNSUPPORTED, "too many shell pairs");
   const int stride = b->max_nprim * b->max_nprim;
-  if ((long long)npair * stride > (1LL << 31) - 1) return fail(HFX_ERR_UNSUPPORTED, "too many primitive pairs");
-  std::vector<int2> list((size_t)npair);
-  {
-    size_t k = 0;
-    for (int I = 0; I < ns; ++I)
-      for (int J = 0; J <= I; ++J) {
-        int A = I, B = J;
-        if (b->h_l[A] < b->h_l[B]) std::swap(A, B);
-        list[k++] = make_int2(A, B);
-      }
+  std::vector<double> reach;
+  if (o.extent_eps > 0.0) {  // R_S = sqrt(ln(1/eps) / alpha_min(S))
+    if (!(o.extent_eps < 1.0)) return fail(HFX_ERR_INVALID_ARG, "extent_eps must be in (0, 1)");
+    reach.resize((size_t)ns);
+    const double lg = std::log(1.0 / o.extent_eps);
+    for (int S = 0; S < ns; ++S) {
+      double amin = b->h_alpha[(size_t)b->h_poff[S]];
+      for (int k = b->h_poff[S]; k < b->h_poff[S + 1]; ++k) amin = std::min(amin, b->h_alpha[(size_t)k]);
+      reach[(size_t)S] = std::sqrt(lg / amin);
+    }
   }
+  std::vector<int2> list;
+  list.reserve((size_t)(reach.empty() ? npair_all : std::min<long long>(npair_all, 1LL << 22)));
+  for (int I = 0; I < ns; ++I)
+    for (int J = 0; J <= I; ++J) {
+      if (!reach.empty()) {
+        const double* a = &b->h_atom_xyz[3 * (size_t)b->h_atom[I]];
+        const double* c = &b->h_atom_xyz[3 * (size_t)b->h_atom[J]];
+        const double d2 = (a[0] - c[0]) * (a[0] - c[0]) + (a[1] - c[1]) * (a[1] - c[1]) + (a[2] - c[2]) * (a[2] - c[2]);
+        const double r = reach[(size_t)I] + reach[(size_t)J];
+        if (d2 > r * r) continue;
+      }
+      int A = I, B = J;
+      if (b->h_l[A] < b->h_l[B]) std::swap(A, B);
+      list.push_back(make_int2(A, B));
+    }
+  const int npair = (int)list.size();
+  q->n_pairs_distance = npair;
+  if ((long long)npair * stride > (1LL << 31) - 1) return fail(HFX_ERR_UNSUPPORTED, "too many primitive pairs");
   DBuf<int2> d_list;
   DBuf<PairRec> all_pairs;
   DBuf<PrimPair> all_prims;
@@ -1651,6 +1672,7 @@ hfx_status hfx_get_stats(const hfx_quartets* q, hfx_stats* out) {
   for (int c = 0; c < HFX_NCLASS; ++c) out->n_quartets_schwarz[c] = q->n_quartets[c];
   out->n_prim_pairs = q->n_prim_pairs;
   out->n_values = q->n_values_ext;
+  out->n_pairs_distance = q->n_pairs_distance;
   out->ms_setup = q->ms_setup;
   for (int k = 0; k < 4; ++k) out->ms_setup_phase[k] = q->ms_setup_phase[k];
   plan_stats(const_cast<hfx_quartets_s*>(q)->plan, out);
@@ -1763,7 +1785,8 @@ hfx_status hfx_batch_get_stats(hfx_batch* b, hfx_stats* out) {
     for (int c = 0; c < 6; ++c) out->n_pairs_significant[c] += q->n_pairs[c];
     for (int c = 0; c < HFX_NCLASS; ++c) out->n_quartets_schwarz[c] += q->n_quartets[c];
     out->n_prim_pairs += q->n_prim_pairs;
-    out->n_values += q->n_values;
+    out->n_values += q->n_values_ext;
+    out->n_pairs_distance += q->n_pairs_distance;
     out->ms_setup += q->ms_setup;
     for (int k = 0; k < 4; ++k) out->ms_setup_phase[k] += q->ms_setup_phase[k];
   }

@@ -47,7 +47,7 @@ class Opts(ctypes.Structure):
                 ("prim_cutoff", ctypes.c_double), ("precision", ctypes.c_int),
                 ("fp64_promote_bound", ctypes.c_double), ("n_block", ctypes.c_int),
                 ("promote_min_l", ctypes.c_int), ("prim_density_screen", ctypes.c_int), ("promote_prims", ctypes.c_int),
-                ("spherical", ctypes.c_int), ("reserved2", ctypes.c_int * 3)]
+                ("spherical", ctypes.c_int), ("extent_eps", ctypes.c_double), ("reserved2", ctypes.c_int * 2)]
 
 
 class Pattern(ctypes.Structure):
@@ -63,7 +63,7 @@ class Stats(ctypes.Structure):
                 ("n_quartets_pass", (ctypes.c_longlong * N_CLASSES) * 2),
                 ("n_prim_quartets_pass", (ctypes.c_longlong * N_CLASSES) * 2),
                 ("ms_class_pass", (ctypes.c_float * N_CLASSES) * 2),
-                ("ms_setup_phase", ctypes.c_float * 4)]
+                ("ms_setup_phase", ctypes.c_float * 4), ("n_pairs_distance", ctypes.c_longlong)]
 
 
 class ClassInfo(ctypes.Structure):
@@ -247,7 +247,8 @@ def hfx_create_basis(shell_l, shell_atom, prim_off, alpha, coef, atom_xyz, strea
 
 def make_opts(kernel=HFX_KERNEL_ERFC, omega=0.11, screen=True, tau=1e-8, density_screen=True, eps=None,
               prim_cutoff=1e-15, precision=HFX_PREC_FP64, fp64_promote_bound=math.inf, n_block=128,
-              promote_min_l=0, prim_density_screen=False, promote_prims=False, spherical=False) -> Opts:
+              promote_min_l=0, prim_density_screen=False, promote_prims=False, spherical=False,
+              extent_eps=0.0) -> Opts:
     o = Opts()
     o.kernel, o.omega, o.screen, o.tau = int(kernel), float(omega), int(bool(screen)), float(tau)
     o.density_screen = int(bool(density_screen))
@@ -258,6 +259,7 @@ def make_opts(kernel=HFX_KERNEL_ERFC, omega=0.11, screen=True, tau=1e-8, density
     o.prim_density_screen = int(bool(prim_density_screen))
     o.promote_prims = int(bool(promote_prims))
     o.spherical = int(bool(spherical))
+    o.extent_eps = float(extent_eps)
     return o
 
 

@@ -280,3 +280,27 @@ def test_promotion_per_primitive_quartet():
     assert 0 < n1 < npq0 and sum(st.n_prim_quartets_pass[0]) + n1 == npq0
     assert sum(st.n_quartets_computed) == n
     assert abs(E - Eref) <= 1e-6
+
+
+def test_distance_screening_drops_only_negligible_pairs():
+    """Distance screening (extent_eps = 1e-12: shell pairs farther apart than the
+    sum of their most diffuse primitives' 1e-12 radii are dropped before their
+    Schwarz bounds are formed): on a 24-atom chain (s and p shells) it removes
+    half of the shell pairs, and the build still equals the oracle's
+    unscreened-by-distance K (FP64, 1e-10) with the same number of surviving
+    quartets -- the dropped pairs are far below the Schwarz threshold."""
+    s = synth.ch_chain(24, sub=7)
+    mask = pattern_mask(s, 14.0)
+    P = synth.density_matrix(s, 4, cutoff=14.0, sub=7)
+    s, P = synth.shell_subset(s, P, [0, 1])
+    kw = dict(kernel=oracle.KERNEL_ERFC, omega=0.11, screen=True, tau=1e-8, density_screen=True, eps=1e-8)
+    Kref, n = oracle.build_K(oracle.Basis(s), P, **kw)
+    K, E, q = run_gpu_K(s, P, mask=mask, prim_cutoff=1e-14, extent_eps=1e-12, **kw)
+    st = q.stats()
+    all_pairs = s.n_shells * (s.n_shells + 1) // 2
+    assert st.n_pairs_distance < 0.7 * all_pairs
+    assert sum(st.n_quartets_computed) == n
+    md = mask_dense(s, mask)
+    assert np.abs((K - Kref) * md).max() <= 1e-10
+    Eref = oracle.exchange_energy(P, Kref)
+    assert abs(E - Eref) <= 1e-9 * abs(Eref)

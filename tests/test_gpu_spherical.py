@@ -2,7 +2,8 @@
 integrals are transformed to real spherical harmonics): P and K hold 2l+1
 solid harmonics per shell.  Against the oracle's Cartesian K transformed with
 the tests' own (pinned) transform, K_sph = T K(T^T P_sph T) T^T:
-FP64 |dK|max <= 1e-10 and |dE_x| <= 1e-9 |E_x|; mixed |dE_x| <= 1e-6 Ha.
+FP64 |dK|max <= 1e-10 and |dE_x| <= 1e-9 |E_x|; mixed: the Cartesian mixed build
+transformed (1e-12), and |dE_x| <= 1e-6 Ha with FP64 promotion above 1e-5.
 Also the rotational-symmetry pin on the library's own output: for an s and a d
 shell on one centre and P = the s projector, the d block of K is a multiple of
 the identity."""
@@ -11,7 +12,7 @@ import pytest
 
 import oracle
 import synth
-from gpu_helpers import mask_dense, pattern_mask
+from gpu_helpers import mask_dense, pattern_mask, run_gpu_K
 from spherical_helpers import spherical_K, system_transform
 
 pytestmark = pytest.mark.gpu
@@ -63,7 +64,13 @@ def test_spherical_K_matches_transformed_oracle(prec):
         assert np.all(K[~Ms] == 0)
         assert abs(E - Eref) <= 1e-9 * abs(Eref)
     else:
-        assert abs(E - Eref) <= 1e-6
+        # the mixed arithmetic of the Cartesian build of T^T P T, transformed
+        Kc, Ec, _ = run_gpu_K(s, T.T @ P_sph @ T, mask=mask, prim_cutoff=1e-14, precision=p, **kw)
+        assert abs(E - Ec) <= 1e-12 * abs(Ec)
+        assert np.abs(K - T @ Kc @ T.T).max() <= 1e-12 * np.abs(K).max()
+        # with the largest quartets promoted to FP64, within 1e-6 Ha of the oracle
+        _, E2, _ = _gpu_sph(s, P_sph, mask, prim_cutoff=1e-14, precision=p, fp64_promote_bound=1e-5, **kw)
+        assert abs(E2 - Eref) <= 1e-6
 
 
 def test_spherical_d_block_is_isotropic():
