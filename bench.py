@@ -82,18 +82,18 @@ DS_RSQRT = 1 + 3 * DS_MULF + 2 * DS_ADDF + 1      # seed, one Newton step: 37
 def ds_prologue_flops(L, kernel):
     """FP32 flops of the same prologue in double-single arithmetic
     (prologue_ds and boys_ds in boys_ds.cuh).  Argument and prefactor: p+q,
-    1/(p+q), rho, three PQ components with their squares, T, prefactor
-    (reciprocal square root and three products) = 204.  Boys: grid offset 12,
-    Taylor series of F_L 74; for L > 0 exp(-T) 66 and 25 per downward step.
-    Coulomb: 8 per G_m.  erfc: attenuation factor 49, f T 7, f^{1/2} 44, a
-    second Boys evaluation, 33 per G_m."""
-    base = DS_ADD + DS_RCP + 2 * DS_MUL + 3 * (6 + 2 + 3 + DS_MUL + DS_ADD) + DS_MUL + DS_RSQRT + DS_MUL + 2 * DS_MULF
+    (p+q)^{-1/2} and its square, rho, three PQ components with their squares,
+    T, prefactor (three products) = 203.  Boys: grid offset 12, Taylor series
+    of F_L 74; for L > 0 exp(-T) 66 and 25 per downward step.  Coulomb: 8 per
+    G_m.  erfc: attenuation factor f^{1/2} 62 and f 7, f T 7, a second Boys
+    evaluation, 33 per G_m."""
+    base = DS_ADD + DS_RSQRT + 3 * DS_MUL + 3 * (6 + 2 + 3 + DS_MUL + DS_ADD) + DS_MUL + DS_MUL + 2 * DS_MULF
     boys = 12 + 4 + DS_MULF + DS_ADD + 3 * (DS_MUL + DS_ADD)
     if L > 0:
         boys += 8 + DS_MULF + DS_ADDF + 2 * (DS_MUL + DS_ADDF) + DS_MUL + 2 + L * (2 * DS_MUL + DS_ADD)
     if kernel == 0:
         return base + boys + (L + 1) * (DS_MUL + 1)
-    atten = (DS_ADD + DS_RCP + DS_MUL) + DS_MUL + (DS_RSQRT + DS_MUL)
+    atten = (DS_ADD + DS_MUL + DS_RSQRT + DS_MUL) + DS_MUL + DS_MUL
     if kernel == 2:
         return base + atten + boys + (L + 1) * (3 * DS_MUL + 1)
     return base + atten + 2 * boys + (L + 1) * (3 * DS_MUL + DS_ADD + 1)

@@ -164,7 +164,8 @@ __device__ __forceinline__ void prologue_ds(const float* __restrict__ tab, int k
                                             float* PQf) {
   const ds p = {pb.pf, pb.plo}, q = {pk.pf, pk.plo};
   const ds s = ds_add(p, q);
-  const ds rs = ds_rcp(s);
+  const ds ys = ds_rsqrt(s);    // (p+q)^{-1/2}, for the prefactor
+  const ds rs = ds_mul(ys, ys);  // 1/(p+q)
   const ds rho = ds_mul(ds_mul(p, q), rs);
   ds pq2 = {0.f, 0.f};
 #pragma unroll
@@ -180,7 +181,7 @@ __device__ __forceinline__ void prologue_ds(const float* __restrict__ tab, int k
   // is the FP32 rounding of an accurate product (an FP32 product with an
   // approximate reciprocal square root would carry the same small relative
   // error into every integral)
-  const ds pref = ds_mulf(ds_mulf(ds_mul({3.498683548e+01f, 1.175513376e-06f}, ds_rsqrt(s)), pb.kpf), pk.kpf);
+  const ds pref = ds_mulf(ds_mulf(ds_mul({3.498683548e+01f, 1.175513376e-06f}, ys), pb.kpf), pk.kpf);
   ds F[L + 1];
   if (kernel != kErf) {
     boys_ds<L>(tab, T, F);
@@ -193,10 +194,12 @@ __device__ __forceinline__ void prologue_ds(const float* __restrict__ tab, int k
       return;
     }
   }
-  const ds f = ds_mul(w2, ds_rcp(ds_add(w2, rho)));
+  // f = w^2 / (w^2 + rho): f^{1/2} = w^2 (w^2 (w^2 + rho))^{-1/2}, f = (f^{1/2})^2
+  const ds c0 = ds_mul(w2, ds_rsqrt(ds_mul(w2, ds_add(w2, rho))));
+  const ds f = ds_mul(c0, c0);
   ds Fw[L + 1];
   boys_ds<L>(tab, ds_mul(f, T), Fw);
-  ds c = ds_mul(f, ds_rsqrt(f));  // f^{1/2}, then f^{m+1/2}
+  ds c = c0;  // f^{1/2}, then f^{m+1/2}
 #pragma unroll
   for (int m = 0; m <= L; ++m) {
     const ds cw = ds_mul(c, Fw[m]);
