@@ -176,7 +176,7 @@ __device__ __forceinline__ void prologue_ds(const float* __restrict__ tab, int k
     pq2 = ds_add(pq2, ds_mul(d, d));
   }
   const ds T = ds_mul(rho, pq2);
-  inv_s = rs.hi;
+  inv_s = __fadd_rn(rs.hi, rs.lo);  // rounded once (rs is an unnormalised product)
   // prefactor 2 pi^{5/2} K_ab K_cd / sqrt(p+q) in double-single, so that G_m
   // is the FP32 rounding of an accurate product (an FP32 product with an
   // approximate reciprocal square root would carry the same small relative
