@@ -793,7 +793,7 @@ def main():
     ap.add_argument("--serve-graph", type=int, default=0)
     ap.add_argument("--serve-incremental", type=int, default=1,
                     help="1: builds after a request's first from the density difference")
-    ap.add_argument("--serve-periodic-share", type=float, default=0.2,
+    ap.add_argument("--serve-periodic-share", type=float, default=0.1,
                     help="share of requests that are the periodic Si cell")
     ap.add_argument("--serve-periodic-cells", type=int, default=1,
                     help="conventional cells per axis of the served Si cell (8 atoms per cell)")

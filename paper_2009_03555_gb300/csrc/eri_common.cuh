@@ -110,6 +110,40 @@ __device__ __forceinline__ R reduce_scatter32(R (&v)[32]) {
   return v[0];
 }
 
+// Warp sum of one 32-target chunk of the split recursion: every lane holds
+// 32 values and lane j returns the sum over the lanes of v[j].  Default: the
+// butterfly reduce-scatter above.  With HFX_SMEM_REDUCE: a transposition
+// through `buf` (32 rows of 36 R in shared memory, 16-byte aligned): each
+// lane stores its row with vector stores and sums its column, trading the
+// butterfly's 62 selects and 31 shuffles for 8 (FP32) or 16 (FP64) vector
+// stores and 32 loads, bank-conflict free (row stride 36).
+constexpr int kChunkBufStride = 36;
+constexpr int kChunkBufElems = 32 * kChunkBufStride;
+template <typename R>
+__device__ __forceinline__ R chunk_reduce32(R (&v)[32], R* buf) {
+#ifdef HFX_SMEM_REDUCE
+  const int lane = threadIdx.x & 31;
+  R* row = buf + lane * kChunkBufStride;
+  if constexpr (sizeof(R) == 4) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      reinterpret_cast<float4*>(row)[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) reinterpret_cast<double2*>(row)[k] = make_double2(v[2 * k], v[2 * k + 1]);
+  }
+  __syncwarp();
+  R s = R(0);
+#pragma unroll
+  for (int j = 0; j < 32; ++j) s += buf[j * kChunkBufStride + lane];
+  __syncwarp();
+  return s;
+#else
+  (void)buf;
+  return reduce_scatter32<R>(v);
+#endif
+}
+
 // ---------------------------------------------------------- Boys function
 // F_m(T) = int_0^1 t^{2m} exp(-T t^2) dt.  For every top order L = 0..8 the
 // table holds, on the grid T_k = k / 16 (k = 0..960, T <= 60), the Taylor

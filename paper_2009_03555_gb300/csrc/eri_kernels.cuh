@@ -954,8 +954,29 @@ struct SplitLayout {
   static constexpr bool ACC_IN_WS = ACC_WORDS <= T::HRR_SLOTS - C::NACC;
   static constexpr int PER_WARP = T::HRR_SLOTS + 160 + (ACC_IN_WS ? 0 : ACC_WORDS);
   __device__ static R* acc_base(R* ws) { return ACC_IN_WS ? ws + (T::HRR_SLOTS - ACC_WORDS) : ws + T::HRR_SLOTS + 160; }
+#ifdef HFX_SMEM_REDUCE
+  static_assert(sizeof(R) == 0, "HFX_SPLIT_SMEM_ACC and HFX_SMEM_REDUCE both use the HRR workspace");
+#endif
+  __device__ static R* red_buf(R* ws) { return ws; }
 #else
-  static constexpr int PER_WARP = T::HRR_SLOTS + 160;  // HRR workspace + four P blocks
+  static constexpr int PER_WARP_BASE = T::HRR_SLOTS + 160;  // HRR workspace + four P blocks
+#ifdef HFX_SMEM_REDUCE
+  // chunk-reduction buffer: the idle HRR workspace when it is large enough
+  static constexpr bool RED_IN_WS = T::HRR_SLOTS >= kChunkBufElems;
+  static constexpr int PER_WARP_RAW = PER_WARP_BASE + (RED_IN_WS ? 0 : kChunkBufElems);
+#else
+  static constexpr int PER_WARP_RAW = PER_WARP_BASE;
+#endif
+  // 16-byte aligned per-warp regions
+  static constexpr int ALIGN = 16 / (int)sizeof(R);
+  static constexpr int PER_WARP = (PER_WARP_RAW + ALIGN - 1) / ALIGN * ALIGN;
+  __device__ static R* red_buf(R* ws) {
+#ifdef HFX_SMEM_REDUCE
+    return RED_IN_WS ? ws : ws + PER_WARP_BASE;
+#else
+    return ws;
+#endif
+  }
 #endif
   static constexpr size_t bytes() { return (size_t)SplitShape<C, R>::WARPS * PER_WARP * sizeof(R); }
 };
@@ -966,7 +987,7 @@ struct SplitLayout {
 template <class C, typename R>
 __device__ __forceinline__ void split_pass(const EriParams& a, const PrimPair* __restrict__ bprims,
                                            const PrimPair* __restrict__ kprims, int bpoff, int kpoff, int nk, int t,
-                                           R* acc, R* comp) {
+                                           R* acc, R* comp, R* red) {
   constexpr bool kMixed = sizeof(R) == 4;
   constexpr int NR = kMixed ? 1 : 2;
   constexpr int NG = C::L + 1;
@@ -1007,7 +1028,7 @@ __device__ __forceinline__ void split_pass(const EriParams& a, const PrimPair* _
   g.oo2pq = R(0.5) * rinv;
   g.rop = rop;
   g.roq = roq;
-  C::template vrr_split<R>(G, g, acc, comp);
+  C::template vrr_split<R>(G, g, acc, comp, red);
 }
 
 #ifdef HFX_CHECKED
@@ -1155,7 +1176,7 @@ __global__ void __launch_bounds__(SplitShape<C, R>::THREADS, SplitShape<C, R>::M
         __syncwarp();
         qn -= take;
         pdone += take;
-        split_pass<C, R>(eri_params(a), bprims, kprims, bpoff, kpoff, nk, t, acc, comp);
+        split_pass<C, R>(eri_params(a), bprims, kprims, bpoff, kpoff, nk, t, acc, comp, Lay::red_buf(ws));
       }
     }
     // C. lockstep classes: the round ends for the whole block, which stops
@@ -1202,7 +1223,11 @@ constexpr int kSchwarzWarps = 4;
 
 template <class C>
 struct SchwarzWarpLayout {
-  static constexpr int PER_WARP = C::COOP ? CoopLayout<C, double>::PER_WARP : C::Coop::HRR_SLOTS;
+  // HRR workspace (also the chunk-reduction buffer of HFX_SMEM_REDUCE builds,
+  // idle during the passes), 16-byte aligned per warp
+  static constexpr int RAW = C::COOP ? CoopLayout<C, double>::PER_WARP
+                                     : (C::Coop::HRR_SLOTS > kChunkBufElems ? C::Coop::HRR_SLOTS : kChunkBufElems);
+  static constexpr int PER_WARP = (RAW + 1) / 2 * 2;
   static constexpr size_t bytes() { return (size_t)kSchwarzWarps * PER_WARP * sizeof(double); }
 };
 
@@ -1213,7 +1238,7 @@ __global__ void __launch_bounds__(32 * kSchwarzWarps) k_schwarz_warp(const Schwa
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double* ws = reinterpret_cast<double*>(smem_raw) + warp * SchwarzWarpLayout<C>::PER_WARP;
-    const EriParams p{a.boys, nullptr, a.kernel, a.omega2, ds{0.f, 0.f}, -1.f};  // every primitive quartet
+    const EriParams p{a.boys, nullptr, a.kernel, a.omega2, ds{0.f, 0.f}, -1.f, 3.0e38f};  // every primitive quartet
     const unsigned short* __restrict__ outs = T::out();
     for (int i = blockIdx.x * kSchwarzWarps + warp; i < a.n_pairs; i += gridDim.x * kSchwarzWarps) {
       if (a.pair_class[i] != a.cls) continue;
@@ -1229,7 +1254,7 @@ __global__ void __launch_bounds__(32 * kSchwarzWarps) k_schwarz_warp(const Schwa
         const int nk = pr.pcnt > 0 ? pr.pcnt : 1, total = pr.pcnt * pr.pcnt;
         for (int t0 = 0; t0 < total; t0 += 32) {
           const int t = t0 + lane < total ? t0 + lane : -1;
-          split_pass<C, double>(p, a.prims, a.prims, pr.poff, pr.poff, nk, t, acc, comp);
+          split_pass<C, double>(p, a.prims, a.prims, pr.poff, pr.poff, nk, t, acc, comp, ws);
         }
         const unsigned short* __restrict__ perm = C::split_perm();
 #pragma unroll

@@ -246,7 +246,8 @@ def gen_class(ib, ik, la, lb, lc, ld):
         src.append(f"  __device__ static const unsigned short* split_perm() {{ return k{name}_perm; }}")
         src.append("  template <typename R>")
         src.append("  __device__ __forceinline__ static void vrr_split(const R* __restrict__ G, const VrrGeo<R>& g,")
-        src.append("                                                 R* __restrict__ acc, R* __restrict__ comp) {")
+        src.append("                                                 R* __restrict__ acc, R* __restrict__ comp,")
+        src.append("                                                 R* __restrict__ red) {")
         src.append("    const R PAx = g.PA[0], PAy = g.PA[1], PAz = g.PA[2];")
         src.append("    const R QCx = g.QC[0], QCy = g.QC[1], QCz = g.QC[2];")
         src.append("    const R WPx = g.WP[0], WPy = g.WP[1], WPz = g.WP[2];")
@@ -718,7 +719,7 @@ def gen_vrr_split(la, lb, lc, ld):
         vals = names + ["R(0)"] * (32 - len(names))
         lines.append("    {")
         lines.append("      R c_[32] = {" + ", ".join(vals) + "};")
-        lines.append(f"      kacc<R>(acc[{k}], comp[{k}], reduce_scatter32<R>(c_));")
+        lines.append(f"      kacc<R>(acc[{k}], comp[{k}], chunk_reduce32<R>(c_, red));")
         lines.append("    }")
     v.flops += len(targets)
     return lines, nch, v.flops, perm

@@ -36,8 +36,9 @@ template <typename R> struct VrrGeo { R PA[3], QC[3], WP[3], WQ[3]; R oo2p, oo2q
 template <typename R> inline void kacc(R& s, R& c, R v) { (void)c; s += v; }
 extern double* g_sink;
 extern int g_nchunk;
-// host stand-in for the warp reduce-scatter: record the chunk's 32 values
-template <typename R> inline R reduce_scatter32(R (&v)[32]) {
+// host stand-in for the warp chunk reduction: record the chunk's 32 values
+template <typename R> inline R chunk_reduce32(R (&v)[32], R* buf) {
+  (void)buf;
   for (int i = 0; i < 32; ++i) g_sink[g_nchunk * 32 + i] = (double)v[i];
   ++g_nchunk;
   return R(0);
@@ -85,7 +86,7 @@ extern "C" int vrr_split_{n}(const double* G, const double* q, double* sink) {{
   double acc[{n}::NCHUNK], comp[{n}::NCHUNK];
   for (int i = 0; i < {n}::NCHUNK; ++i) acc[i] = comp[i] = 0.0;
   g_sink = sink; g_nchunk = 0;
-  {n}::vrr_split<double>(G, geo_{n}(q), acc, comp);
+  {n}::vrr_split<double>(G, geo_{n}(q), acc, comp, nullptr);
   return g_nchunk;
 }}
 extern "C" const unsigned short* perm_{n}() {{ return {n}::split_perm(); }}
