@@ -84,11 +84,11 @@ def ds_prologue_flops(L, kernel):
     (prologue_ds and boys_ds in boys_ds.cuh).  Argument and prefactor: p+q,
     (p+q)^{-1/2} and its square, rho, three PQ components with their squares,
     T, prefactor (three products) = 203.  Boys: grid offset 12, Taylor series
-    of F_L 74; for L > 0 exp(-T) 66 and 25 per downward step.  Coulomb: 8 per
+    of F_L 58; for L > 0 exp(-T) 66 and 25 per downward step.  Coulomb: 8 per
     G_m.  erfc: attenuation factor f^{1/2} 62 and f 7, f T 7, a second Boys
     evaluation, 33 per G_m."""
     base = DS_ADD + DS_RSQRT + 3 * DS_MUL + 3 * (6 + 2 + 3 + DS_MUL + DS_ADD) + DS_MUL + DS_MUL + 2 * DS_MULF
-    boys = 12 + 4 + DS_MULF + DS_ADD + 3 * (DS_MUL + DS_ADD)
+    boys = 12 + 6 + DS_MULF + DS_ADD + 2 * (DS_MUL + DS_ADD)
     if L > 0:
         boys += 8 + DS_MULF + DS_ADDF + 2 * (DS_MUL + DS_ADDF) + DS_MUL + 2 + L * (2 * DS_MUL + DS_ADD)
     if kernel == 0:

@@ -102,9 +102,10 @@ __device__ __forceinline__ ds inv_odd(int m) {
 }
 
 // F_0..F_L at T (double-single).  T < 60: Taylor expansion of F_L about the
-// nearest grid point T_k (|x| = |T_k - T| <= 1/32; terms j = 4..6 in FP32,
-// j = 0..3 in double-single), exp(-T) = exp(-T_k) exp(x) (terms x^3.. in
-// FP32), downward recursion F_m = (2T F_{m+1} + exp(-T)) / (2m+1).
+// nearest grid point T_k (|x| = |T_k - T| <= 1/32; terms j = 3..6 in FP32,
+// at most 5e-6 of the sum, j = 0..2 in double-single), exp(-T) = exp(-T_k)
+// exp(x) (terms x^3.. in FP32), downward recursion
+// F_m = (2T F_{m+1} + exp(-T)) / (2m+1).
 // T >= 60: F_0 = sqrt(pi)/2 T^{-1/2}, F_{m+1} = F_m (2m+1) / (2T).
 template <int L>
 __device__ __forceinline__ void boys_ds(const float* __restrict__ tab, ds T, ds* F) {
@@ -122,8 +123,8 @@ __device__ __forceinline__ void boys_ds(const float* __restrict__ tab, ds T, ds*
     //                 c6 = q6e.x,y  exp(-T_k) = q6e.z,w
     float r = fmaf(q6e.x, x.hi, q45.z);
     r = fmaf(r, x.hi, q45.x);
-    ds f = ds_add(ds_mulf(x, r), {q23.z, q23.w});
-    f = ds_add(ds_mul(f, x), {q23.x, q23.y});
+    r = fmaf(r, x.hi, q23.z);
+    ds f = ds_add(ds_mulf(x, r), {q23.x, q23.y});
     f = ds_add(ds_mul(f, x), {q01.z, q01.w});
     f = ds_add(ds_mul(f, x), {q01.x, q01.y});
     F[L] = f;

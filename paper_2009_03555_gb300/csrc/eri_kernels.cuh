@@ -960,23 +960,23 @@ struct SplitLayout {
   __device__ static R* red_buf(R* ws) { return ws; }
 #else
   static constexpr int PER_WARP_BASE = T::HRR_SLOTS + 160;  // HRR workspace + four P blocks
+  // 16-byte alignment (the per-warp regions, and the reduction buffer, which
+  // takes vector stores)
+  static constexpr int ALIGN = 16 / (int)sizeof(R);
+  static constexpr int align_up(int n) { return (n + ALIGN - 1) / ALIGN * ALIGN; }
 #ifdef HFX_SMEM_REDUCE
-  // chunk-reduction buffer: the idle HRR workspace when it is large enough
+  // chunk-reduction buffer: the idle HRR workspace when it is large enough,
+  // otherwise after the P blocks at the next 16-byte boundary
   static constexpr bool RED_IN_WS = T::HRR_SLOTS >= kChunkBufElems;
-  static constexpr int PER_WARP_RAW = PER_WARP_BASE + (RED_IN_WS ? 0 : kChunkBufElems);
+  static constexpr int RED_OFF = RED_IN_WS ? 0 : align_up(PER_WARP_BASE);
+  static constexpr int PER_WARP_RAW = RED_IN_WS ? PER_WARP_BASE : RED_OFF + kChunkBufElems;
 #else
+  static constexpr int RED_OFF = 0;
   static constexpr int PER_WARP_RAW = PER_WARP_BASE;
 #endif
-  // 16-byte aligned per-warp regions
-  static constexpr int ALIGN = 16 / (int)sizeof(R);
-  static constexpr int PER_WARP = (PER_WARP_RAW + ALIGN - 1) / ALIGN * ALIGN;
-  __device__ static R* red_buf(R* ws) {
-#ifdef HFX_SMEM_REDUCE
-    return RED_IN_WS ? ws : ws + PER_WARP_BASE;
-#else
-    return ws;
-#endif
-  }
+  static constexpr int PER_WARP = align_up(PER_WARP_RAW);
+  static_assert(RED_OFF % ALIGN == 0 && PER_WARP % ALIGN == 0, "16-byte aligned shared-memory regions");
+  __device__ static R* red_buf(R* ws) { return ws + RED_OFF; }
 #endif
   static constexpr size_t bytes() { return (size_t)SplitShape<C, R>::WARPS * PER_WARP * sizeof(R); }
 };

@@ -66,11 +66,11 @@ def test_double_single_operation_costs(costs):
 
 
 def test_prologue_counts_grow_as_stated():
-    # erfc: the attenuation factor (76), a second Boys evaluation (86 + 66 + 25 L for L > 0) and 33 per
+    # erfc: the attenuation factor (76), a second Boys evaluation (70 + 66 + 25 L for L > 0) and 33 per
     # G_m on top of Coulomb's 8
     for L in range(1, 9):
         c, e = bench.ds_prologue_flops(L, 0), bench.ds_prologue_flops(L, 1)
-        assert e - c == 76 + (86 + 66 + 25 * L) + 25 * (L + 1)
+        assert e - c == 76 + (70 + 66 + 25 * L) + 25 * (L + 1)
         assert bench.ds_prologue_flops(L, 1) - bench.ds_prologue_flops(L - 1, 1) == (50 if L > 1 else 50 + 132) + 33
-    assert bench.ds_prologue_flops(6, 1) == 1091 and bench.ds_prologue_flops(8, 1) == 1257
+    assert bench.ds_prologue_flops(6, 1) == 1059 and bench.ds_prologue_flops(8, 1) == 1225
     assert bench.fp64_prologue_flops(8, 1) == 205
