@@ -133,11 +133,17 @@ __device__ __forceinline__ R chunk_reduce32(R (&v)[32], R* buf) {
     for (int k = 0; k < 16; ++k) reinterpret_cast<double2*>(row)[k] = make_double2(v[2 * k], v[2 * k + 1]);
   }
   __syncwarp();
-  R s = R(0);
+  // the column, summed as a pairwise tree (the butterfly's summation order
+  // and error growth)
+  R t[32];
 #pragma unroll
-  for (int j = 0; j < 32; ++j) s += buf[j * kChunkBufStride + lane];
+  for (int j = 0; j < 32; ++j) t[j] = buf[j * kChunkBufStride + lane];
   __syncwarp();
-  return s;
+#pragma unroll
+  for (int h = 16; h > 0; h >>= 1)
+#pragma unroll
+    for (int i = 0; i < h; ++i) t[i] += t[i + h];
+  return t[0];
 #else
   (void)buf;
   return reduce_scatter32<R>(v);
