@@ -21,9 +21,11 @@ FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", C
 # the exchange-build path and report (printf) and skip out-of-range accesses.
 if os.environ.get("HFX_CHECKED", "0") not in ("", "0"):
     FLAGS = FLAGS + ["-DHFX_CHECKED"]
-# HFX_NVCC_FLAGS: extra nvcc flags (e.g. -DHFX_SPLIT_SMEM_ACC for the split
-# kernels' accumulators in shared memory, -DHFX_LOCKSTEP_MIN_FLOPS=... for the
-# lockstep threshold); part of every object's digest.
+# HFX_NVCC_FLAGS: extra nvcc flags (e.g. -DHFX_SHFL_REDUCE for the butterfly
+# chunk reduction, -DHFX_SHFL_REDUCE -DHFX_SPLIT_SMEM_ACC for the split kernels'
+# accumulators in shared memory, -DHFX_LOCKSTEP_MIN_FLOPS=... for the lockstep
+# threshold, -DHFX_PT_MINB=... for the per-thread launch bound); part of every
+# object's digest.
 FLAGS = FLAGS + os.environ.get("HFX_NVCC_FLAGS", "").split()
 
 

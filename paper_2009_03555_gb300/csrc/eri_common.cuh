@@ -111,12 +111,17 @@ __device__ __forceinline__ R reduce_scatter32(R (&v)[32]) {
 }
 
 // Warp sum of one 32-target chunk of the split recursion: every lane holds
-// 32 values and lane j returns the sum over the lanes of v[j].  Default: the
-// butterfly reduce-scatter above.  With HFX_SMEM_REDUCE: a transposition
-// through `buf` (32 rows of 36 R in shared memory, 16-byte aligned): each
-// lane stores its row with vector stores and sums its column, trading the
-// butterfly's 62 selects and 31 shuffles for 8 (FP32) or 16 (FP64) vector
-// stores and 32 loads, bank-conflict free (row stride 36).
+// 32 values and lane j returns the sum over the lanes of v[j].  Default: a
+// transposition through `buf` (32 rows of 36 R in shared memory, 16-byte
+// aligned): each lane stores its row with vector stores and sums its column
+// as a pairwise tree, trading the butterfly's 62 selects and 31 shuffles for
+// 8 (FP32) or 16 (FP64) vector stores and 32 loads, bank-conflict free (row
+// stride 36); measured 3-13 % faster per split class on GB300, with the same
+// results to the last digits printed.  HFX_SHFL_REDUCE (build switch) selects
+// the butterfly reduce-scatter above.
+#ifndef HFX_SHFL_REDUCE
+#define HFX_SMEM_REDUCE
+#endif
 constexpr int kChunkBufStride = 36;
 constexpr int kChunkBufElems = 32 * kChunkBufStride;
 template <typename R>

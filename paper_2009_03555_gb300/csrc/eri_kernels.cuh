@@ -955,7 +955,7 @@ struct SplitLayout {
   static constexpr int PER_WARP = T::HRR_SLOTS + 160 + (ACC_IN_WS ? 0 : ACC_WORDS);
   __device__ static R* acc_base(R* ws) { return ACC_IN_WS ? ws + (T::HRR_SLOTS - ACC_WORDS) : ws + T::HRR_SLOTS + 160; }
 #ifdef HFX_SMEM_REDUCE
-  static_assert(sizeof(R) == 0, "HFX_SPLIT_SMEM_ACC and HFX_SMEM_REDUCE both use the HRR workspace");
+  static_assert(sizeof(R) == 0, "HFX_SPLIT_SMEM_ACC needs HFX_SHFL_REDUCE (both would use the HRR workspace)");
 #endif
   __device__ static R* red_buf(R* ws) { return ws; }
 #else
@@ -1223,7 +1223,7 @@ constexpr int kSchwarzWarps = 4;
 
 template <class C>
 struct SchwarzWarpLayout {
-  // HRR workspace (also the chunk-reduction buffer of HFX_SMEM_REDUCE builds,
+  // HRR workspace (also the chunk-reduction buffer of the shared-memory reduction,
   // idle during the passes), 16-byte aligned per warp
   static constexpr int RAW = C::COOP ? CoopLayout<C, double>::PER_WARP
                                      : (C::Coop::HRR_SLOTS > kChunkBufElems ? C::Coop::HRR_SLOTS : kChunkBufElems);
