@@ -56,3 +56,23 @@ def extended_system(per):
                         prim_off=np.concatenate([[0], np.cumsum(n_p)]).astype(np.int32),
                         alpha=np.asarray(home.alpha, dtype=np.float64)[take],
                         coef=np.asarray(home.coef, dtype=np.float64)[take])
+
+
+def oracle_rows_by_key(s, P, A, r_ext, r_P, **kw):
+    """Oracle rows keyed by extended atom (home atom, shift), and the per-cell
+    energy -1/2 sum P^G_{mu lambda} K^G_{mu lambda} over those rows."""
+    import oracle
+    K, ext, _ = oracle.K_periodic(s, P, A, r_ext, r_P, **kw)
+    nf = np.diff(s.atom_func_off)
+    hf = s.atom_func_off
+    blocks, E, c = {}, 0.0, 0
+    for a, n1, n2, n3 in ext:
+        key = (int(a), (int(n1), int(n2), int(n3)))
+        blk = K[:, c:c + nf[a]]
+        blocks[key] = blk
+        pos = s.atom_xyz[a] + np.array([n1, n2, n3], dtype=np.float64) @ A
+        for b in range(s.n_atoms):  # P^G rows: home block where the atoms are within r_P
+            if np.linalg.norm(s.atom_xyz[b] - pos) <= r_P:
+                E += -0.5 * float(np.sum(P[hf[b]:hf[b + 1], hf[a]:hf[a + 1]] * blk[hf[b]:hf[b + 1]]))
+        c += nf[a]
+    return blocks, E

@@ -16,7 +16,7 @@ import pytest
 
 import oracle
 import synth
-from periodic_helpers import extended_system, formed_blocks_error
+from periodic_helpers import extended_system, formed_blocks_error, oracle_rows_by_key
 
 pytestmark = pytest.mark.gpu
 
@@ -47,25 +47,6 @@ def gpu_periodic(s, P, A, r_ext, r_P, **opt_kw):
     assert abs(E - float(E_pre.item())) <= 1e-13 * abs(E)
     assert float(Kv[per.n_home_values:].abs().max()) == 0.0  # rows of image atoms
     return Kd[:per.n_home_bf].cpu().numpy(), E, per
-
-
-def oracle_rows_by_key(s, P, A, r_ext, r_P, **kw):
-    """Oracle rows keyed by extended atom (home atom, shift), and the per-cell
-    energy -1/2 sum P^G_{mu lambda} K^G_{mu lambda} over those rows."""
-    K, ext, _ = oracle.K_periodic(s, P, A, r_ext, r_P, **kw)
-    nf = np.diff(s.atom_func_off)
-    hf = s.atom_func_off
-    blocks, E, c = {}, 0.0, 0
-    for a, n1, n2, n3 in ext:
-        key = (int(a), (int(n1), int(n2), int(n3)))
-        blk = K[:, c:c + nf[a]]
-        blocks[key] = blk
-        pos = s.atom_xyz[a] + np.array([n1, n2, n3], dtype=np.float64) @ A
-        for b in range(s.n_atoms):  # P^G rows: home block where the atoms are within r_P
-            if np.linalg.norm(s.atom_xyz[b] - pos) <= r_P:
-                E += -0.5 * float(np.sum(P[hf[b]:hf[b + 1], hf[a]:hf[a + 1]] * blk[hf[b]:hf[b + 1]]))
-        c += nf[a]
-    return blocks, E
 
 
 KW = {"coulomb": dict(kernel=oracle.KERNEL_COULOMB, screen=False, density_screen=False),

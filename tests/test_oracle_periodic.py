@@ -196,3 +196,19 @@ def test_supercell_describes_the_same_crystal():
         np.testing.assert_allclose(v, b2[p][:nb], rtol=0, atol=1e-12 * np.abs(K1).max())
         compared += 1
     assert compared >= s.n_atoms + 2
+
+
+def test_per_cell_energy_converges_in_r_ext():
+    """Truncation of the image set: the home rows K^G_{mu lambda} need the
+    images sigma^H within the overlap range of every lambda^G in the density
+    pattern (at most r_P from the home cell), so the per-cell exchange energy
+    is converged once r_ext exceeds r_P by the overlap range.  With r_P = 4 bohr
+    on a small skewed cell (s and p shells): r_ext = r_P + 4 and r_P + 6 agree to
+    1e-8 of E_x, while r_ext = r_P + 2 still misses a part well above that."""
+    from periodic_helpers import oracle_rows_by_key
+    s = synth.periodic_cell(2, SKEW, sub=41, recipe={"C": [0, 1], "H": [0, 1]})
+    P = synth.periodic_density_matrix(s, cutoff=4.0, sub=41)
+    kw = dict(kernel=oracle.KERNEL_ERFC, screen=True, density_screen=True, tau=1e-10, eps=1e-10)
+    E = {rx: oracle_rows_by_key(s, P, SKEW, rx, 4.0, **kw)[1] for rx in (6.0, 8.0, 10.0)}
+    assert abs(E[10.0] - E[8.0]) <= 1e-8 * abs(E[10.0])
+    assert abs(E[10.0] - E[6.0]) > 1e-6 * abs(E[10.0])
