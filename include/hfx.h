@@ -359,6 +359,23 @@ long long hfx_periodic_images(const double* atom_xyz, int n_atoms, const double*
 hfx_status hfx_periodic_pack_host(const hfx_shell_desc* shells, int n_shells, int n_home_atoms, const int* ext_home,
                                   const hfx_pattern* ext_pattern, const double* P_home, double* val);
 
+/* Real-space density of the extended set from one density block per lattice
+ * vector (Eq. dm with a k-point grid: the caller forms
+ * P^L = (1/N_k) sum_k exp(-i k.L) P(k), real for a grid closed under k -> -k,
+ * with P^{-L} = (P^L)^T).  Every block (X, Y) of ext_pattern receives the
+ * home block P^{n_Y - n_X}(home(X), home(Y)), n the lattice shifts of the
+ * extended atoms (hfx_periodic_extend), from P_L[l] where L_shift[l] equals
+ * n_Y - n_X; a shift difference not in the list gives a zero block.  With one
+ * P_L for every shift difference this is hfx_periodic_pack_host.
+ * ext_shift: host, 3 per extended atom; L_shift: host, n_L x 3; P_L: host,
+ * n_L x nbf x nbf (home functions, row-major); val as for
+ * hfx_periodic_pack_host.  The exchange rows built from these values are
+ * K^G_{mu lambda} = sum_{N,H} P^{H-N} (mu^0 nu^N | lambda^G sigma^H) of
+ * Eq. H-HFX; the caller's Fourier sum over G gives K(k). */
+hfx_status hfx_periodic_pack_lattice_host(const hfx_shell_desc* shells, int n_shells, int n_home_atoms,
+                                          const int* ext_home, const int* ext_shift, const hfx_pattern* ext_pattern,
+                                          int n_L, const int* L_shift, const double* P_L, double* val);
+
 /* ---- Serving: continuous batching of independent requests -------------
  * No counterpart in the paper, whose runs build one system's K once per SCF
  * iteration; a server interleaves many such SCF-like runs on one GPU.

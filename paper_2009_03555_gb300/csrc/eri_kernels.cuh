@@ -163,8 +163,17 @@ __device__ __forceinline__ int contracted_quartet(const PairRec& bra, const Prim
   for (int ib = 0; ib < bra.pcnt; ++ib) {
     const PrimPair pb = bprims[bra.poff + ib];
     if (pb.bound * kmax < pr.lo) break;
+#ifdef HFX_PT_PREFETCH
+    // the next ket primitive pair is loaded while this one is evaluated
+    PrimPair pk_next = kprims[ket.poff];
+#endif
     for (int ik = 0; ik < ket.pcnt; ++ik) {
+#ifdef HFX_PT_PREFETCH
+      const PrimPair pk = pk_next;
+      if (ik + 1 < ket.pcnt) pk_next = kprims[ket.poff + ik + 1];
+#else
       const PrimPair pk = kprims[ket.poff + ik];
+#endif
       const float bb = pb.bound * pk.bound;
       if (bb < pr.lo) break;
       if (bb > pr.hi) continue;

@@ -157,6 +157,52 @@ long long hfx_distance_pattern(const double* atom_xyz, int n_atoms, double r_cut
   return nnz;
 }
 
+hfx_status hfx_periodic_pack_lattice_host(const hfx_shell_desc* shells, int n_shells, int n_home_atoms,
+                                          const int* ext_home, const int* ext_shift, const hfx_pattern* ext_pattern,
+                                          int n_L, const int* L_shift, const double* P_L, double* val) {
+  if (!shells || n_shells <= 0 || n_home_atoms <= 0 || !ext_home || !ext_shift || !ext_pattern ||
+      !ext_pattern->row_ptr || !ext_pattern->col || ext_pattern->n_atoms <= 0 || n_L < 0 ||
+      (n_L > 0 && (!L_shift || !P_L)) || !val)
+    return status_fail(HFX_ERR_INVALID_ARG, "hfx_periodic_pack_lattice_host: NULL or empty argument");
+  std::vector<long long> nf((size_t)n_home_atoms, 0), f0((size_t)n_home_atoms + 1, 0);
+  for (int s = 0; s < n_shells; ++s) {
+    const int at = shells[s].atom, l = shells[s].l;
+    if (at < 0 || at >= n_home_atoms || l < 0 || l > 2 || (s > 0 && at < shells[s - 1].atom))
+      return status_fail(HFX_ERR_INVALID_ARG, "hfx_periodic_pack_lattice_host: shells not grouped by home atom");
+    nf[(size_t)at] += n_cart(l);
+  }
+  for (int at = 0; at < n_home_atoms; ++at) f0[(size_t)at + 1] = f0[(size_t)at] + nf[(size_t)at];
+  const long long nbf = f0[(size_t)n_home_atoms];
+  const int n_ext = ext_pattern->n_atoms;
+  for (int X = 0; X < n_ext; ++X)
+    if (ext_home[X] < 0 || ext_home[X] >= n_home_atoms)
+      return status_fail(HFX_ERR_INVALID_ARG, "hfx_periodic_pack_lattice_host: ext_home out of range");
+  long long v = 0;
+  for (int X = 0; X < n_ext; ++X) {
+    if (ext_pattern->row_ptr[X] > ext_pattern->row_ptr[X + 1])
+      return status_fail(HFX_ERR_INVALID_ARG, "hfx_periodic_pack_lattice_host: row_ptr not ascending");
+    const int hx = ext_home[X];
+    for (int k = ext_pattern->row_ptr[X]; k < ext_pattern->row_ptr[X + 1]; ++k) {
+      const int Y = ext_pattern->col[k];
+      if (Y < 0 || Y >= n_ext)
+        return status_fail(HFX_ERR_INVALID_ARG, "hfx_periodic_pack_lattice_host: column out of range");
+      const int hy = ext_home[Y];
+      // P^{H-N}: the lattice vector from the cell of X (N) to the cell of Y (H)
+      int L = -1;
+      for (int l = 0; l < n_L && L < 0; ++l)
+        if (L_shift[3 * l] == ext_shift[3 * Y] - ext_shift[3 * X] &&
+            L_shift[3 * l + 1] == ext_shift[3 * Y + 1] - ext_shift[3 * X + 1] &&
+            L_shift[3 * l + 2] == ext_shift[3 * Y + 2] - ext_shift[3 * X + 2])
+          L = l;
+      const double* PL = L >= 0 ? P_L + (size_t)L * (size_t)nbf * (size_t)nbf : nullptr;
+      for (long long i = 0; i < nf[(size_t)hx]; ++i)
+        for (long long j = 0; j < nf[(size_t)hy]; ++j)
+          val[v++] = PL ? PL[(f0[(size_t)hx] + i) * nbf + f0[(size_t)hy] + j] : 0.0;
+    }
+  }
+  return HFX_OK;
+}
+
 hfx_status hfx_periodic_pack_host(const hfx_shell_desc* shells, int n_shells, int n_home_atoms, const int* ext_home,
                                   const hfx_pattern* ext_pattern, const double* P_home, double* val) {
   if (!shells || n_shells <= 0 || n_home_atoms <= 0 || !ext_home || !ext_pattern || !ext_pattern->row_ptr ||

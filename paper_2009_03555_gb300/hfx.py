@@ -86,7 +86,7 @@ EXPORTED = ["hfx_create_basis", "hfx_build_quartets", "hfx_value_count", "hfx_bu
             "hfx_server_step", "hfx_server_poll", "hfx_server_release", "hfx_server_get_info", "hfx_server_destroy",
             "hfx_server_cancel", "hfx_server_inject_setup_failure", "hfx_periodic_images", "hfx_periodic_pack_host",
             "hfx_create_basis_periodic", "hfx_basis_atoms", "hfx_periodic_extend", "hfx_distance_pattern",
-            "hfx_server_submit_periodic",
+            "hfx_server_submit_periodic", "hfx_periodic_pack_lattice_host",
             "hfx_destroy_basis", "hfx_destroy_quartets", "hfx_last_error"]
 
 _lib = None
@@ -172,6 +172,8 @@ def load(path: str = LIB_PATH):
     lib.hfx_periodic_images.argtypes = [V, I, V, D, LL, V, V]
     lib.hfx_periodic_pack_host.argtypes = [ctypes.POINTER(ShellDesc), I, I, V, ctypes.POINTER(Pattern), V, V]
     lib.hfx_create_basis_periodic.argtypes = [ctypes.POINTER(ShellDesc), I, V, I, V, D, V, PV]
+    lib.hfx_periodic_pack_lattice_host.argtypes = [ctypes.POINTER(ShellDesc), I, I, V, V, ctypes.POINTER(Pattern),
+                                                   I, V, V, V]
     lib.hfx_basis_atoms.argtypes = [V, V, V, V]
     lib.hfx_periodic_extend.argtypes = [V, I, V, D, LL, V, V, V]
     lib.hfx_distance_pattern.argtypes = [V, I, D, V, V, LL]
@@ -600,6 +602,19 @@ class Periodic:
     def quartets(self, opts: Opts, stream=None) -> "Quartets":
         """Basis and quartet lists of the cell on its density pattern."""
         return Quartets(self.basis(stream), opts, csr=(self.row_ptr, self.col), stream=stream)
+
+    def pack_lattice(self, L_shift, P_L) -> np.ndarray:
+        """Values of the real-space density from one home-cell block per lattice
+        vector (``L_shift``: n_L x 3 integer shifts, ``P_L``: n_L x nbf x nbf),
+        e.g. the Fourier sum of a k-point grid (host)."""
+        L = np.ascontiguousarray(L_shift, dtype=np.int32).reshape(-1, 3)
+        PL = np.ascontiguousarray(P_L, dtype=np.float64)
+        out = np.empty(self.n_values)
+        _check(load().hfx_periodic_pack_lattice_host(self._home_descs, len(self.home.shell_l),
+                                                     int(self.home.n_atoms), _ptr(self.ext_home),
+                                                     _ptr(self.ext_shift), ctypes.byref(self.pattern), int(L.shape[0]),
+                                                     _ptr(L), _ptr(PL), _ptr(out)))
+        return out
 
     def pack(self, P_home) -> np.ndarray:
         """Values of the real-space density on the extended pattern (host)."""

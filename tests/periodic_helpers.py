@@ -76,3 +76,39 @@ def oracle_rows_by_key(s, P, A, r_ext, r_P, **kw):
                 E += -0.5 * float(np.sum(P[hf[b]:hf[b + 1], hf[a]:hf[a + 1]] * blk[hf[b]:hf[b + 1]]))
         c += nf[a]
     return blocks, E
+
+
+def kgrid_lattice_density(P0, Ppi, shifts):
+    """Real-space densities of a two-point k grid along the first lattice
+    vector, k in {0, pi}: P^L = (P(0) + cos(pi n1) P(pi)) / 2 for each lattice
+    shift L = (n1, n2, n3) (Eq. dm as a Fourier sum over the grid).  Returns the
+    distinct shifts (n_L x 3) and the stacked P^L."""
+    L = np.unique(np.asarray(shifts, dtype=np.int32).reshape(-1, 3), axis=0)
+    PL = np.stack([0.5 * (P0 + np.cos(np.pi * n[0]) * Ppi) for n in L])
+    return L, PL
+
+
+def extended_density(per, P_of_shift, r_P):
+    """Dense density of the extended set from the definition: block (X, Y) is
+    P^{n_Y - n_X}(home X, home Y) where the atoms are at most r_P apart."""
+    ef = per.system.atom_func_off
+    hf = per.home.atom_func_off
+    x = per.system.atom_xyz
+    Pe = np.zeros((per.system.n_bf, per.system.n_bf))
+    for X in range(per.system.n_atoms):
+        for Y in range(per.system.n_atoms):
+            if np.linalg.norm(x[X] - x[Y]) > r_P:
+                continue
+            hx, hy = per.ext_home[X], per.ext_home[Y]
+            PL = P_of_shift(tuple(int(v) for v in per.ext_shift[Y] - per.ext_shift[X]))
+            Pe[ef[X]:ef[X + 1], ef[Y]:ef[Y + 1]] = PL[hf[hx]:hf[hx + 1], hf[hy]:hf[hy + 1]]
+    return Pe
+
+
+def shift_differences(per):
+    """Every lattice-shift difference n_Y - n_X over the pattern's blocks."""
+    out = set()
+    for X in range(len(per.ext_home)):
+        for Y in per.col[per.row_ptr[X]:per.row_ptr[X + 1]]:
+            out.add(tuple(int(v) for v in per.ext_shift[Y] - per.ext_shift[X]))
+    return np.array(sorted(out), dtype=np.int32)

@@ -109,3 +109,43 @@ def test_home_cell_quartets_only():
     h = per.n_home_values
     scale = float(Km[:h].abs().max())
     assert float((Kp[:h] - Km[:h]).abs().max()) <= 1e-12 * scale
+
+
+@pytest.mark.parametrize("kname", ["coulomb", "erfc"])
+def test_kpoint_density_rows(kname):
+    """A two-point k grid (k = 0 and pi along a1): the real-space densities
+    P^L = (P(0) + cos(pi n1) P(pi)) / 2 packed per lattice shift
+    (hfx_periodic_pack_lattice_host), built on the periodic basis, against the
+    oracle's molecular exchange of the extended set with the density of the
+    definition P^{H-N}: home rows on the formed blocks (FP64, 1e-10) and the
+    per-cell energy."""
+    import torch
+    from paper_2009_03555_gb300 import hfx
+    from periodic_helpers import extended_density, kgrid_lattice_density, shift_differences
+    A, r_ext, r_P = SKEW, 5.0, 4.0
+    s = synth.periodic_cell(3, A, sub=36, recipe=D_RECIPE)
+    P0 = synth.periodic_density_matrix(s, cutoff=r_P, sub=36)
+    Ppi = synth.periodic_density_matrix(s, cutoff=r_P, sub=37)
+    per = hfx.Periodic(s, A, r_ext=r_ext, r_P=r_P)
+    Lk, PL = kgrid_lattice_density(P0, Ppi, shift_differences(per))
+    kw = KW[kname]
+    hk = dict(kernel={"coulomb": hfx.HFX_KERNEL_COULOMB, "erfc": hfx.HFX_KERNEL_ERFC}[kname], screen=kw["screen"],
+              density_screen=kw["density_screen"], precision=hfx.HFX_PREC_FP64)
+    q = per.quartets(hfx.make_opts(**hk))
+    dev = torch.device("cuda")
+    Pv = torch.from_numpy(per.pack_lattice(Lk, PL)).to(dev)
+    Kv = torch.empty_like(Pv)
+    q.build_K(Pv, Kv)
+    E = q.exchange_energy(Pv, Kv)
+    Kd = torch.empty((per.system.n_bf, per.system.n_bf), dtype=torch.float64, device=dev)
+    q.unpack(Kv, Kd)
+    torch.cuda.synchronize()
+    K = Kd[:per.n_home_bf].cpu().numpy()
+    e = extended_system(per)
+    Pe = extended_density(per, lambda n: 0.5 * (P0 + np.cos(np.pi * n[0]) * Ppi), r_P)
+    Km, _ = oracle.build_K(oracle.Basis(e), Pe, **kw)
+    md = synth.expand_atom_mask(e, per.mask)[:per.n_home_bf]
+    assert np.abs((K - Km[:per.n_home_bf]) * md).max() <= 1e-10
+    assert np.all(K[~md] == 0)
+    E_ref = -0.5 * float(np.sum(Pe[:per.n_home_bf] * Km[:per.n_home_bf] * md))
+    assert abs(E - E_ref) <= 1e-9 * abs(E_ref)

@@ -143,3 +143,28 @@ def test_pack_rejects_bad_home_index(hfx):
     per.ext_home[-1] = s.n_atoms  # out of range
     with pytest.raises(hfx.HFXError, match="ext_home"):
         per.pack(synth.periodic_density_matrix(s, cutoff=4.0, sub=23))
+
+
+def test_lattice_density_pack(hfx):
+    """hfx_periodic_pack_lattice_host: one P^L per shift difference equal to
+    P_home gives the Gamma-point pack; a two-point k grid gives the blocks of
+    the definition P^{n_Y - n_X}(home X, home Y), zero where a shift is not
+    listed."""
+    from periodic_helpers import extended_density, kgrid_lattice_density, shift_differences
+    s = synth.periodic_cell(2, SKEW, sub=24, recipe=D_RECIPE)
+    P = synth.periodic_density_matrix(s, cutoff=4.0, sub=24)
+    per = hfx.Periodic(s, SKEW, r_ext=5.0, r_P=4.0)
+    L = shift_differences(per)
+    assert len(L) > 1
+    np.testing.assert_array_equal(per.pack_lattice(L, np.stack([P] * len(L))), per.pack(P))
+    P0 = synth.periodic_density_matrix(s, cutoff=4.0, sub=25)
+    Ppi = synth.periodic_density_matrix(s, cutoff=4.0, sub=26)
+    Lk, PL = kgrid_lattice_density(P0, Ppi, L)
+    v = per.pack_lattice(Lk, PL)
+    Pe = extended_density(per, lambda n: 0.5 * (P0 + np.cos(np.pi * n[0]) * Ppi), 4.0)
+    ref = hfx._SystemInput(extended_system(per), per.mask).pack(Pe)
+    np.testing.assert_array_equal(v, ref)
+    # a shift left out of the list gives zero blocks
+    keep = np.any(Lk != Lk[0], axis=1)
+    v2 = per.pack_lattice(Lk[keep], PL[keep])
+    assert np.count_nonzero(v2) < np.count_nonzero(v)
