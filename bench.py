@@ -37,10 +37,29 @@ import synth  # noqa: E402
 # `traffic` scales it to the timed launch; a kernel changed since its capture
 # has no entry (traffic null).
 DRAM_BYTES_PER_PRIM_QUARTET = {
-    # The captures in profiles/ (k_build_K_split<Cls2221, float>: 0.317 B,
-    # k_build_K_split<Cls2222, double>: 12.6 KB per primitive quartet) predate
-    # the grouped target order of the split recursion, so no kernel has a
-    # current entry.
+    # profiles/dram_build_K_50atom.md: one warm-up build of the 50-atom cluster
+    "k_build_K<Cls0000, float>": 0.05258,
+    "k_build_K<Cls1000, float>": 0.03656,
+    "k_build_K<Cls1010, float>": 0.0251,
+    "k_build_K<Cls1100, float>": 0.03909,
+    "k_build_K<Cls1110, float>": 0.0248,
+    "k_build_K<Cls1111, float>": 0.1049,
+    "k_build_K<Cls2000, float>": 0.04949,
+    "k_build_K<Cls2010, float>": 0.03082,
+    "k_build_K<Cls2011, float>": 0.03659,
+    "k_build_K<Cls2020, float>": 0.06164,
+    "k_build_K<Cls2100, float>": 0.04697,
+    "k_build_K<Cls2110, float>": 0.04442,
+    "k_build_K_split<Cls2111, float>": 0.03736,
+    "k_build_K_split<Cls2120, float>": 0.04573,
+    "k_build_K_split<Cls2121, float>": 0.05519,
+    "k_build_K<Cls2200, float>": 0.09022,
+    "k_build_K_split<Cls2210, float>": 0.06666,
+    "k_build_K_split<Cls2211, float>": 0.07952,
+    "k_build_K_split<Cls2220, float>": 0.0914,
+    "k_build_K_split<Cls2221, float>": 0.08442,
+    "k_build_K_split<Cls2222, float>": 8.617,
+    "k_build_K_split<Cls2222, double>": 1481,
 }
 
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 80.5: 128 FP32 FMA/clk/SM at the 2070 MHz max clock
@@ -305,6 +324,8 @@ def run_ours(args, rank, world):
                 "peak_source": "derived: 152 SMs x (128 FP32 | 2 FP64) FMA/clk x 2070 MHz",
                 "traffic": (round(bpq * st.n_prim_quartets_pass[p][c]) if bpq is not None else None),
                 "traffic_unit": "bytes per launch",
+                "traffic_source": ("ncu dram__bytes_read+write of the 50-atom launch per primitive quartet, "
+                                   "times this launch's primitive quartets" if bpq is not None else None),
                 "launch_ms": round(t, 3), "share_of_build": round(t / st.ms_last_build, 4)}
     per_class = []
     for p in range(2):

@@ -219,8 +219,10 @@ hfx_status hfx_boys_eval(hfx_basis* basis, int precision, int mmax, int n, const
  * E_x: device pointer to one double, written asynchronously on `stream`.
  * Scratch is a static device array of 2^16 doubles (512 KiB, held on every
  * GPU that loads the library until exit); n_values above 2^28 is rejected with
- * HFX_ERR_INVALID_ARG.  The first call on a device looks up the array's device
- * address (no allocation); make that first call before any stream capture.
+ * HFX_ERR_INVALID_ARG.  Every call looks up the array's device address
+ * (cudaGetSymbolAddress, no allocation), so a device reset in between is
+ * harmless; the first call on a device may load the module, so make it
+ * before any stream capture.
  * Every call shares the array, so calls that overlap on the GPU race: serialise
  * them.  The reduction order is fixed (two passes, no atomics). */
 hfx_status hfx_exchange_energy_noalloc(const double* P_val, const double* K_val, long long n_values, double* E_x,

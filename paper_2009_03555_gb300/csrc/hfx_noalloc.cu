@@ -18,7 +18,6 @@
 // several host threads) race on it and must be serialised by the caller.
 #include <cuda_runtime.h>
 
-#include <mutex>
 #include <string>
 
 #include "hfx.h"
@@ -34,12 +33,6 @@ constexpr long long kValuesPerBlock = 4096;  // 16 values per thread
 
 static __device__ __align__(256) double g_partials[kNoAllocMaxPartials];
 
-
-// Device address of g_partials per device, looked up once with that device
-// current (the host-side symbol is only a stand-in for the device address).
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-double* g_ptr[kMaxDevices] = {};
 
 hfx_status noalloc_fail(hfx_status s, const std::string& m) {
   hfx_set_last_error(m);
@@ -96,22 +89,13 @@ hfx_status hfx_exchange_energy_noalloc(const double* P_val, const double* K_val,
     return noalloc_fail(HFX_ERR_INVALID_ARG,
                         "n_values exceeds the no-allocation limit of " +
                             std::to_string((long long)kNoAllocMaxPartials * kValuesPerBlock) + " values");
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return noalloc_fail(HFX_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-  if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(HFX_ERR_UNSUPPORTED, "device index too large");
-  double* partial = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_ptr[dev]) {
-      void* p = nullptr;
-      e = cudaGetSymbolAddress(&p, g_partials);
-      if (e != cudaSuccess)
-        return noalloc_fail(HFX_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-      g_ptr[dev] = static_cast<double*>(p);
-    }
-    partial = g_ptr[dev];
-  }
+  // the array's device address on the current device (the host-side symbol
+  // only stands in for it), asked for on every call: after a device reset
+  // the module can be loaded again at another address
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_partials);
+  if (e != cudaSuccess) return noalloc_fail(HFX_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+  double* partial = static_cast<double*>(p);
   cudaStream_t s = (cudaStream_t)stream;
   if (nb > 0) k_dot_partials<<<(unsigned)nb, kNoAllocThreads, 0, s>>>(n_values, P_val, K_val, partial);
   k_dot_final<<<1, kNoAllocThreads, 0, s>>>((int)nb, partial, E_x);
