@@ -24,8 +24,10 @@ if os.environ.get("HFX_CHECKED", "0") not in ("", "0"):
 # HFX_NVCC_FLAGS: extra nvcc flags (e.g. -DHFX_SHFL_REDUCE for the butterfly
 # chunk reduction, -DHFX_SHFL_REDUCE -DHFX_SPLIT_SMEM_ACC for the split kernels'
 # accumulators in shared memory, -DHFX_LOCKSTEP_MIN_FLOPS=... for the lockstep
-# threshold, -DHFX_PT_MINB=... for the per-thread launch bound); part of every
-# object's digest.
+# threshold, -DHFX_PT_MINB=... for the per-thread launch bound,
+# -DHFX_PT_PREFETCH=0|1 for the ket prefetch of every per-thread class instead
+# of the per-class choice, -DHFX_SPLIT64_MAX_WARPS=4 for 4-warp FP64 split
+# blocks, -DHFX_LOCKSTEP64=0 for FP64 split kernels without lockstep rounds); part of every object's digest.
 FLAGS = FLAGS + os.environ.get("HFX_NVCC_FLAGS", "").split()
 
 

@@ -99,6 +99,10 @@ struct EriParams {
   float prim_hi;   // ... and those above this (the other pass of a promotion per primitive quartet)
 };
 
+#ifndef HFX_PT_PREFETCH
+#define HFX_PT_PREFETCH -1  // ket primitive-pair prefetch: -1 per class (C::PT_PREFETCH), 0 never, 1 always
+#endif
+
 // The primitive quartets of one quartet that a launch evaluates: bound
 // products bound_ab bound_cd in [lo, hi] (see quartet_prim_range).
 struct PrimRange {
@@ -152,6 +156,7 @@ __device__ __forceinline__ int contracted_quartet(const PairRec& bra, const Prim
                                                   ds w2, PrimRange pr, R* __restrict__ out) {
   constexpr bool kMixed = sizeof(R) == 4;
   constexpr int NR = kMixed ? 1 : 2;
+  constexpr bool kPrefetch = HFX_PT_PREFETCH < 0 ? C::PT_PREFETCH : HFX_PT_PREFETCH > 0;
   R acc[C::NACC], comp[C::NACC];
 #pragma unroll
   for (int i = 0; i < C::NACC; ++i) {
@@ -163,17 +168,21 @@ __device__ __forceinline__ int contracted_quartet(const PairRec& bra, const Prim
   for (int ib = 0; ib < bra.pcnt; ++ib) {
     const PrimPair pb = bprims[bra.poff + ib];
     if (pb.bound * kmax < pr.lo) break;
-#ifdef HFX_PT_PREFETCH
-    // the next ket primitive pair is loaded while this one is evaluated
-    PrimPair pk_next = kprims[ket.poff];
-#endif
+    // classes with C::PT_PREFETCH load the next ket primitive pair while this
+    // one is evaluated (measured per class: faster where it costs no
+    // occupancy); HFX_PT_PREFETCH=0/1 turns it off/on for every class
+    PrimPair pk_next;
+    if constexpr (kPrefetch) {
+      if (ket.pcnt > 0) pk_next = kprims[ket.poff];
+    }
     for (int ik = 0; ik < ket.pcnt; ++ik) {
-#ifdef HFX_PT_PREFETCH
-      const PrimPair pk = pk_next;
-      if (ik + 1 < ket.pcnt) pk_next = kprims[ket.poff + ik + 1];
-#else
-      const PrimPair pk = kprims[ket.poff + ik];
-#endif
+      PrimPair pk;
+      if constexpr (kPrefetch) {
+        pk = pk_next;
+        if (ik + 1 < ket.pcnt) pk_next = kprims[ket.poff + ik + 1];
+      } else {
+        pk = kprims[ket.poff + ik];
+      }
       const float bb = pb.bound * pk.bound;
       if (bb < pr.lo) break;
       if (bb > pr.hi) continue;
@@ -935,17 +944,30 @@ __global__ void __launch_bounds__(kThreadsCoop) k_build_K_coop(const BuildArgs a
 #ifndef HFX_MID_WARPS
 #define HFX_MID_WARPS 4
 #endif
+// Opt-in cap on the warps per block of the FP64 warp-split kernels
+// (HFX_SPLIT64_MAX_WARPS=4: the FP64 (dd|dd) pass in 4-warp blocks, its shape
+// before the horizontal recursion reused its workspace slots).
+#ifndef HFX_SPLIT64_MAX_WARPS
+#define HFX_SPLIT64_MAX_WARPS 8
+#endif
+// HFX_LOCKSTEP64=0: the FP64 warp-split kernels without lockstep rounds.
+#ifndef HFX_LOCKSTEP64
+#define HFX_LOCKSTEP64 1
+#endif
 template <class C, typename R>
 struct SplitShape {
-  static constexpr bool LOCKSTEP = C::VRR_FLOPS >= HFX_LOCKSTEP_MIN_FLOPS;
+  static constexpr bool LOCKSTEP = C::VRR_FLOPS >= HFX_LOCKSTEP_MIN_FLOPS && (sizeof(R) == 4 || HFX_LOCKSTEP64);
   // a horizontal-recursion workspace above 32 KB per warp leaves room for
-  // 4-warp blocks only: (dd|dd) in FP64 (6254 slots x 8 B); in FP32 its eight
-  // warps take 205 KB of shared memory, like the FP64 four
+  // 4-warp blocks only.  With its slots reused once their values are dead no
+  // class needs that much ((dd|dd): 2844 slots, 22 KB in FP64), so the FP64
+  // (dd|dd) pass runs eight warps per SM (188 KB of shared memory) like FP32
   static constexpr bool BIG_HRR = C::Coop::HRR_SLOTS * sizeof(R) > 4096 * sizeof(double);
-  static constexpr int WARPS = (C::VRR_FLOPS >= HFX_WIDE_MIN_FLOPS && !BIG_HRR) ? 8
-                               : ((LOCKSTEP && !BIG_HRR) ? HFX_MID_WARPS : 4);
+  static constexpr int WARPS_UNCAPPED = (C::VRR_FLOPS >= HFX_WIDE_MIN_FLOPS && !BIG_HRR) ? 8
+                                        : ((LOCKSTEP && !BIG_HRR) ? HFX_MID_WARPS : 4);
+  static constexpr bool CAPPED = sizeof(R) == 8 && WARPS_UNCAPPED > HFX_SPLIT64_MAX_WARPS;
+  static constexpr int WARPS = CAPPED ? HFX_SPLIT64_MAX_WARPS : WARPS_UNCAPPED;
   static constexpr int THREADS = 32 * WARPS;
-  static constexpr int MIN_BLOCKS = (WARPS >= 8 || BIG_HRR) ? 1 : 3;
+  static constexpr int MIN_BLOCKS = (WARPS >= 8 || BIG_HRR || CAPPED) ? 1 : 3;
 };
 
 template <class C, typename R>

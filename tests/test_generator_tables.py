@@ -53,18 +53,22 @@ def test_hrr_tables(cls):
     na, nb, nc, nd = (len(g.comps(l)) for l in cls)
     assert len(t["outs"]) == na * nb * nc * nd
     assert len(set(t["outs"])) == len(t["outs"]) and max(t["outs"]) < hs
+    # slots are reused once their value is dead, so a level may write a slot
+    # that held an accumulator or an earlier node; the lanes run one level in
+    # parallel, so no level may read a slot it writes, nor write one twice
     written = set(range(nacc))
     offs = t["hlev_off"]
     assert offs[0] == offs[1] == 0 and offs[t["n_hlev"] + 1] == len(t["hnodes"])
     for lev in range(1, t["n_hlev"] + 1):
         level = [_decode(n) for n in t["hnodes"][offs[lev]:offs[lev + 1]]]
-        dsts = {d for d, *_ in level}
+        dsts = [d for d, *_ in level]
+        assert len(dsts) == len(set(dsts))
         for dst, kind, axis, s1, s2 in level:
-            assert nacc <= dst < hs and s1 < hs and s2 < hs
+            assert 0 <= dst < hs and s1 < hs and s2 < hs
             assert kind in (2, 3) and axis in (0, 1, 2)
             assert s1 in written and s2 in written  # written by an earlier level or an accumulator
             assert s1 not in dsts and s2 not in dsts
-        written |= dsts
+        written |= set(dsts)
 
     # numerical: table interpretation against the recursion written out
     rng = np.random.default_rng(sum(10 ** k * l for k, l in enumerate(cls)))
