@@ -118,6 +118,10 @@ def ds_prologue_flops(L, kernel):
     return base + atten + 2 * boys + (L + 1) * (3 * DS_MUL + DS_ADD + 1)
 
 
+def ncart(l):
+    return (l + 1) * (l + 2) // 2
+
+
 def class_flops(ci, n_q, n_pq, kernel, fp32):
     """(fp64 flops, fp32 flops) of one class launch with n_q quartets and n_pq
     primitive quartets."""
@@ -341,6 +345,17 @@ def run_ours(args, rank, world):
                                   "ms": round(t, 3), "quartets": int(st.n_quartets_pass[p][c]),
                                   "prim_quartets": int(st.n_prim_quartets_pass[p][c]),
                                   "alu_frac": round(frac, 4)})
+    # the exchange scatter, fused into the class kernels: per canonical quartet
+    # the four P blocks read and the four K blocks read-modified-written (FP64),
+    # NA NC + NB ND + NB NC + NA ND elements each; its time is not separable
+    # from the integrals', so the rate is these bytes over the whole build
+    scatter_bytes = 0
+    for p in range(2):
+        for c in range(hfx.N_CLASSES):
+            if st.n_quartets_pass[p][c] > 0:
+                ci = hfx.hfx_get_class_info(c)
+                na, nb, nc, nd = (ncart(l) for l in (ci.la, ci.lb, ci.lc, ci.ld))
+                scatter_bytes += st.n_quartets_pass[p][c] * (na * nc + nb * nd + nb * nc + na * nd) * (8 + 16)
     n_q = int(sum(st.n_quartets_computed))
     n_pq = int(sum(st.n_prim_quartets_pass[0]) + sum(st.n_prim_quartets_pass[1]))
     if shard:  # this rank's share: the build's counts are the sums over the ranks
@@ -372,6 +387,10 @@ def run_ours(args, rank, world):
         "gpu_launches": args.steps * (5 + sum(1 for p in range(2) for c in range(hfx.N_CLASSES)
                                             if st.n_quartets_pass[p][c] > 0 or st.ms_class_pass[p][c] > 0)),
         "clocks": clocks, "e2e": e2e, "roofline": roof, "per_class": per_class,
+        "scatter": {"bytes_per_build": int(scatter_bytes),
+                    "achieved_gbs": round(scatter_bytes / (ms * 1e-3) / 1e9, 1),
+                    "what": "P reads + K read-modify-write of the four exchange blocks per canonical quartet (FP64), "
+                            "fused into the class kernels and served from L2; rate over the whole build time"},
         "vs_fp64": fp64,
     }
     return res, s, q
