@@ -22,7 +22,7 @@ FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", C
 if os.environ.get("HFX_CHECKED", "0") not in ("", "0"):
     FLAGS = FLAGS + ["-DHFX_CHECKED"]
 # HFX_NVCC_FLAGS: extra nvcc flags (e.g. -DHFX_SHFL_REDUCE for the butterfly
-# chunk reduction, -DHFX_SHFL_REDUCE -DHFX_SPLIT_SMEM_ACC for the split kernels'
+# chunk reduction, -DHFX_SPLIT_SMEM_ACC for every FP32 split class's
 # accumulators in shared memory, -DHFX_LOCKSTEP_MIN_FLOPS=... for the lockstep
 # threshold, -DHFX_PT_MINB=... for the per-thread launch bound,
 # -DHFX_PT_PREFETCH=0|1 for the ket prefetch of every per-thread class instead

@@ -970,46 +970,48 @@ struct SplitShape {
   static constexpr int MIN_BLOCKS = (WARPS >= 8 || BIG_HRR || CAPPED) ? 1 : 3;
 };
 
+// Split classes with C::SPLIT_SMEM_ACC keep their FP32 chunk accumulators
+// and compensations in shared memory instead of registers (chosen per class
+// by timing: it removes the register spill of (dp|pp)); HFX_SPLIT_SMEM_ACC
+// moves them there for every FP32 class.  (The FP64 (dd|dd) pass has no room
+// for them beside eight warps' workspaces.)
 template <class C, typename R>
 struct SplitLayout {
   using T = typename C::Coop;
 #ifdef HFX_SPLIT_SMEM_ACC
-  // Opt-in build (-DHFX_SPLIT_SMEM_ACC): the chunk accumulators and their
-  // compensations live in shared memory instead of registers, lane-major with
-  // an odd stride (no bank conflicts).  They sit at the top of the HRR
-  // workspace when they fit above its NACC accumulator slots (the workspace is
-  // idle until the epilogue, which copies them down before the recursion
-  // writes there), otherwise after the P blocks.
-  static constexpr int ACC_STRIDE = C::NCHUNK | 1;
-  static constexpr int ACC_WORDS = 2 * 32 * ACC_STRIDE;
-  static constexpr bool ACC_IN_WS = ACC_WORDS <= T::HRR_SLOTS - C::NACC;
-  static constexpr int PER_WARP = T::HRR_SLOTS + 160 + (ACC_IN_WS ? 0 : ACC_WORDS);
-  __device__ static R* acc_base(R* ws) { return ACC_IN_WS ? ws + (T::HRR_SLOTS - ACC_WORDS) : ws + T::HRR_SLOTS + 160; }
-#ifdef HFX_SMEM_REDUCE
-  static_assert(sizeof(R) == 0, "HFX_SPLIT_SMEM_ACC needs HFX_SHFL_REDUCE (both would use the HRR workspace)");
-#endif
-  __device__ static R* red_buf(R* ws) { return ws; }
+  static constexpr bool SMEM_ACC = sizeof(R) == 4;
 #else
-  static constexpr int PER_WARP_BASE = T::HRR_SLOTS + 160;  // HRR workspace + four P blocks
+  static constexpr bool SMEM_ACC = sizeof(R) == 4 && C::SPLIT_SMEM_ACC;
+#endif
   // 16-byte alignment (the per-warp regions, and the reduction buffer, which
   // takes vector stores)
   static constexpr int ALIGN = 16 / (int)sizeof(R);
   static constexpr int align_up(int n) { return (n + ALIGN - 1) / ALIGN * ALIGN; }
+  static constexpr int PER_WARP_BASE = T::HRR_SLOTS + 160;  // HRR workspace + four P blocks
 #ifdef HFX_SMEM_REDUCE
   // chunk-reduction buffer: the idle HRR workspace when it is large enough,
   // otherwise after the P blocks at the next 16-byte boundary
   static constexpr bool RED_IN_WS = T::HRR_SLOTS >= kChunkBufElems;
   static constexpr int RED_OFF = RED_IN_WS ? 0 : align_up(PER_WARP_BASE);
-  static constexpr int PER_WARP_RAW = RED_IN_WS ? PER_WARP_BASE : RED_OFF + kChunkBufElems;
+  static constexpr int RED_END = RED_IN_WS ? PER_WARP_BASE : RED_OFF + kChunkBufElems;
 #else
   static constexpr int RED_OFF = 0;
-  static constexpr int PER_WARP_RAW = PER_WARP_BASE;
+  static constexpr int RED_END = PER_WARP_BASE;
 #endif
-  static constexpr int PER_WARP = align_up(PER_WARP_RAW);
-  static_assert(RED_OFF % ALIGN == 0 && PER_WARP % ALIGN == 0, "16-byte aligned shared-memory regions");
+  // shared-memory accumulators and compensations: lane-major with an odd
+  // stride (no bank conflicts), after everything else (the HRR workspace holds
+  // the reduction buffer during the passes and the recursion in the epilogue,
+  // which reads the accumulators)
+  static constexpr int ACC_STRIDE = C::NCHUNK | 1;
+  static constexpr int ACC_WORDS = SMEM_ACC ? 2 * 32 * ACC_STRIDE : 0;
+  static constexpr int ACC_OFF = align_up(RED_END);
+  static constexpr int PER_WARP = align_up(ACC_OFF + ACC_WORDS);
+  static_assert(RED_OFF % ALIGN == 0 && ACC_OFF % ALIGN == 0 && PER_WARP % ALIGN == 0,
+                "16-byte aligned shared-memory regions");
   __device__ static R* red_buf(R* ws) { return ws + RED_OFF; }
-#endif
+  __device__ static R* acc_base(R* ws) { return ws + ACC_OFF; }
   static constexpr size_t bytes() { return (size_t)SplitShape<C, R>::WARPS * PER_WARP * sizeof(R); }
+  static_assert(bytes() <= 227 * 1024, "split-kernel shared memory per block");
 };
 
 // One pass: prologue and vertical recursion of primitive quartet t of the
@@ -1110,12 +1112,9 @@ __global__ void __launch_bounds__(SplitShape<C, R>::THREADS, SplitShape<C, R>::M
   bool have = false;
   int bi = 0, ki = 0, bpoff = 0, kpoff = 0, nk = 1, total = 0, t0 = 0, qn = 0;
   PrimRange pr_q{a.eps_prim, 3.0e38f};  // primitive quartets of the current quartet this launch takes
-#ifdef HFX_SPLIT_SMEM_ACC
-  R* const acc = Lay::acc_base(ws) + lane * Lay::ACC_STRIDE;
-  R* const comp = acc + 32 * Lay::ACC_STRIDE;
-#else
-  R acc[C::NCHUNK], comp[C::NCHUNK];
-#endif
+  R acc_r[Lay::SMEM_ACC ? 1 : C::NCHUNK], comp_r[Lay::SMEM_ACC ? 1 : C::NCHUNK];
+  R* const acc = Lay::SMEM_ACC ? Lay::acc_base(ws) + lane * Lay::ACC_STRIDE : acc_r;
+  R* const comp = Lay::SMEM_ACC ? Lay::acc_base(ws) + (32 + lane) * Lay::ACC_STRIDE : comp_r;
   for (;;) {
     // A. the next shell quartet: next kept ket of the window, next window of
     //    the batch, or the next batch from the queue (Algorithms 1-3)
