@@ -27,7 +27,9 @@ if os.environ.get("HFX_CHECKED", "0") not in ("", "0"):
 # threshold, -DHFX_PT_MINB=... for the per-thread launch bound,
 # -DHFX_PT_PREFETCH=0|1 for the ket prefetch of every per-thread class instead
 # of the per-class choice, -DHFX_SPLIT64_MAX_WARPS=4 for 4-warp FP64 split
-# blocks, -DHFX_LOCKSTEP64=0 for FP64 split kernels without lockstep rounds); part of every object's digest.
+# blocks, -DHFX_LOCKSTEP64=0 for FP64 split kernels without lockstep rounds,
+# -DHFX_WIDE_WARPS=8|12|16 and -DHFX_MID_WARPS_F32=... for the warps per
+# lockstep block of the FP32 split classes); part of every object's digest.
 FLAGS = FLAGS + os.environ.get("HFX_NVCC_FLAGS", "").split()
 
 

@@ -950,22 +950,45 @@ __global__ void __launch_bounds__(kThreadsCoop) k_build_K_coop(const BuildArgs a
 #ifndef HFX_SPLIT64_MAX_WARPS
 #define HFX_SPLIT64_MAX_WARPS 8
 #endif
+// Warps per lockstep block of the FP32 wide classes (from HFX_WIDE_MIN_FLOPS
+// recursion flops up) and mid classes, unless the class sets its own
+// (C::SPLIT_WARPS).  Blocks of more than eight warps run at <= 168 (12 warps)
+// or <= 128 (16) registers with the chunk accumulators in shared memory.
+// Measured on GB300 (100-atom HSE build): 12-warp blocks against 8 make
+// (dd|dp) 25 %, (dd|pp) 25 %, (dd|ds) 15 % and (dp|dp) 12 % faster; more warps
+// share each stretch of the instruction stream and hide each other's fetch.
+#ifndef HFX_WIDE_WARPS
+#define HFX_WIDE_WARPS 12
+#endif
+#ifndef HFX_MID_WARPS_F32
+#define HFX_MID_WARPS_F32 HFX_MID_WARPS
+#endif
 // HFX_LOCKSTEP64=0: the FP64 warp-split kernels without lockstep rounds.
 #ifndef HFX_LOCKSTEP64
 #define HFX_LOCKSTEP64 1
 #endif
 template <class C, typename R>
 struct SplitShape {
-  static constexpr bool LOCKSTEP = C::VRR_FLOPS >= HFX_LOCKSTEP_MIN_FLOPS && (sizeof(R) == 4 || HFX_LOCKSTEP64);
+  static constexpr bool F32 = sizeof(R) == 4;
+  static constexpr bool LOCKSTEP = C::VRR_FLOPS >= HFX_LOCKSTEP_MIN_FLOPS && (F32 || HFX_LOCKSTEP64);
   // a horizontal-recursion workspace above 32 KB per warp leaves room for
   // 4-warp blocks only.  With its slots reused once their values are dead no
   // class needs that much ((dd|dd): 2844 slots, 22 KB in FP64), so the FP64
   // (dd|dd) pass runs eight warps per SM (188 KB of shared memory) like FP32
   static constexpr bool BIG_HRR = C::Coop::HRR_SLOTS * sizeof(R) > 4096 * sizeof(double);
-  static constexpr int WARPS_UNCAPPED = (C::VRR_FLOPS >= HFX_WIDE_MIN_FLOPS && !BIG_HRR) ? 8
-                                        : ((LOCKSTEP && !BIG_HRR) ? HFX_MID_WARPS : 4);
-  static constexpr bool CAPPED = sizeof(R) == 8 && WARPS_UNCAPPED > HFX_SPLIT64_MAX_WARPS;
-  static constexpr int WARPS = CAPPED ? HFX_SPLIT64_MAX_WARPS : WARPS_UNCAPPED;
+  static constexpr bool WIDE = C::VRR_FLOPS >= HFX_WIDE_MIN_FLOPS && !BIG_HRR;
+  static constexpr bool MID = LOCKSTEP && !WIDE && !BIG_HRR;
+  static constexpr int RULE = WIDE ? (F32 ? HFX_WIDE_WARPS : 8) : (MID ? (F32 ? HFX_MID_WARPS_F32 : HFX_MID_WARPS) : 4);
+  static constexpr int WANT = (F32 && C::SPLIT_WARPS > 0) ? C::SPLIT_WARPS : RULE;
+  // bound on the per-warp shared memory of a block with the accumulators in
+  // shared memory (the layout below): more than eight warps only where the
+  // block fits
+  static constexpr size_t BIG_PER_WARP = (size_t)C::Coop::HRR_SLOTS + 160 + 4 +
+                                         (C::Coop::HRR_SLOTS >= kChunkBufElems ? 0 : kChunkBufElems + 4) +
+                                         2 * 32 * (C::NCHUNK | 1) + 4;
+  static constexpr int WARPS_FIT = (WANT > 8 && WANT * BIG_PER_WARP * sizeof(R) > 227 * 1024) ? 8 : WANT;
+  static constexpr bool CAPPED = !F32 && WARPS_FIT > HFX_SPLIT64_MAX_WARPS;
+  static constexpr int WARPS = CAPPED ? HFX_SPLIT64_MAX_WARPS : WARPS_FIT;
   static constexpr int THREADS = 32 * WARPS;
   static constexpr int MIN_BLOCKS = (WARPS >= 8 || BIG_HRR || CAPPED) ? 1 : 3;
 };
@@ -981,7 +1004,7 @@ struct SplitLayout {
 #ifdef HFX_SPLIT_SMEM_ACC
   static constexpr bool SMEM_ACC = sizeof(R) == 4;
 #else
-  static constexpr bool SMEM_ACC = sizeof(R) == 4 && C::SPLIT_SMEM_ACC;
+  static constexpr bool SMEM_ACC = sizeof(R) == 4 && (C::SPLIT_SMEM_ACC || SplitShape<C, R>::WARPS > 8);
 #endif
   // 16-byte alignment (the per-warp regions, and the reduction buffer, which
   // takes vector stores)

@@ -97,6 +97,9 @@ PT_PREFETCH = {(0, 0, 0, 0), (1, 0, 1, 0), (1, 1, 0, 0), (1, 1, 1, 0), (2, 0, 0,
 # (measured, 100-atom HSE build: (dp|pp) 3.8 % faster, spill-free at 153
 # registers; (dd|dd) unchanged, (dp|dp) 3.5 % slower).
 SPLIT_SMEM_ACC = {(2, 1, 1, 1)}
+# FP32 warp-split classes with their own warps per block (0 or absent: the
+# kernel's rule by recursion size).
+SPLIT_WARPS = {}
 
 
 class VRR:
@@ -276,6 +279,7 @@ def gen_class(ib, ik, la, lb, lc, ld):
     src.append(f"  static constexpr int PT_MIN_BLOCKS = {PT_MIN_BLOCKS.get((la, lb, lc, ld), 1)};")
     src.append(f"  static constexpr bool PT_PREFETCH = {'true' if (la, lb, lc, ld) in PT_PREFETCH else 'false'};")
     src.append(f"  static constexpr bool SPLIT_SMEM_ACC = {'true' if (la, lb, lc, ld) in SPLIT_SMEM_ACC else 'false'};")
+    src.append(f"  static constexpr int SPLIT_WARPS = {SPLIT_WARPS.get((la, lb, lc, ld), 0)};")
     inl = "__forceinline__" if len(v.E) * len(v.F) <= INLINE_MAX_ACC else "__noinline__"
     src.append("  template <typename R>")
     src.append(f"  __device__ {inl} static void vrr(const R* __restrict__ G, const VrrGeo<R>& g, R* __restrict__ acc,")

@@ -139,6 +139,65 @@ def test_single_s_shell():
     assert K[0, 0] == pytest.approx(Kref[0, 0], rel=1e-14)
 
 
+def _joined(a, b):
+    """Systems a and b as one system (b's atoms after a's)."""
+    return synth.System(name=a.name + "+" + b.name, atom_Z=np.concatenate([a.atom_Z, b.atom_Z]),
+                        atom_xyz=np.concatenate([a.atom_xyz, b.atom_xyz]),
+                        shell_atom=np.concatenate([a.shell_atom, b.shell_atom + a.n_atoms]).astype(np.int32),
+                        shell_l=np.concatenate([a.shell_l, b.shell_l]).astype(np.int32),
+                        prim_off=np.concatenate([a.prim_off, b.prim_off[1:] + a.prim_off[-1]]).astype(np.int32),
+                        alpha=np.concatenate([a.alpha, b.alpha]), coef=np.concatenate([a.coef, b.coef]))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_disconnected_molecules(prec):
+    """Two HSE clusters 200 bohr apart with a block-diagonal density pattern: no
+    shell pair spans the gap (its Schwarz bound underflows) and every cross
+    quartet has P_scr = 0, so K is the two clusters' own exchange matrices side
+    by side, each equal to the build of that cluster alone (to the rounding of
+    the FP64 accumulation order), and the build computes exactly the two
+    clusters' quartets.  FP64: also against the oracle on each cluster."""
+    from paper_2009_03555_gb300 import hfx
+    a, b = synth.ch_cluster(4, 21), synth.ch_cluster(3, 22)
+    Pa, Pb = synth.density_matrix(a, 21), synth.density_matrix(b, 22)
+    s = _joined(a, b.translated([200.0, 0.0, 0.0]))
+    na, nfa = a.n_atoms, a.n_bf
+    P = np.zeros((s.n_bf, s.n_bf))
+    P[:nfa, :nfa], P[nfa:, nfa:] = Pa, Pb
+    mask = np.zeros((s.n_atoms, s.n_atoms), dtype=bool)
+    mask[:na, :na] = True
+    mask[na:, na:] = True
+    precision = hfx.HFX_PREC_FP64 if prec == "fp64" else hfx.HFX_PREC_MIXED
+    kw = dict(kernel=hfx.HFX_KERNEL_ERFC, omega=0.11, screen=True, tau=1e-8, density_screen=True, eps=1e-8,
+              precision=precision)
+    K, E, q = run_gpu_K(s, P, mask, **kw)
+    Ka, Ea, qa = run_gpu_K(a, Pa, **kw)
+    Kb, Eb, qb = run_gpu_K(b, Pb, **kw)
+    n = sum(q.stats().n_quartets_computed)
+    assert n == sum(qa.stats().n_quartets_computed) + sum(qb.stats().n_quartets_computed)
+    assert np.all(K[:nfa, nfa:] == 0) and np.all(K[nfa:, :nfa] == 0)
+    scale = max(np.abs(Ka).max(), np.abs(Kb).max())
+    assert np.abs(K[:nfa, :nfa] - Ka).max() <= 1e-12 * scale
+    assert np.abs(K[nfa:, nfa:] - Kb).max() <= 1e-12 * scale
+    assert abs(E - (Ea + Eb)) <= 1e-12 * abs(Ea + Eb)
+    if prec == "fp64":
+        okw = dict(kernel=oracle.KERNEL_ERFC, omega=0.11, screen=True, tau=1e-8, density_screen=True, eps=1e-8)
+        Kra, n_a = oracle.build_K(oracle.Basis(a), Pa, **okw)
+        Krb, n_b = oracle.build_K(oracle.Basis(b), Pb, **okw)
+        assert n == n_a + n_b
+        assert np.abs(Ka - Kra).max() <= 1e-10 and np.abs(Kb - Krb).max() <= 1e-10
+
+
+def test_empty_basis_is_rejected():
+    from paper_2009_03555_gb300 import hfx
+    empty = synth.System(name="empty", atom_Z=np.zeros(0, dtype=np.int32), atom_xyz=np.zeros((0, 3)),
+                         shell_atom=np.zeros(0, dtype=np.int32), shell_l=np.zeros(0, dtype=np.int32),
+                         prim_off=np.zeros(1, dtype=np.int32), alpha=np.zeros(0), coef=np.zeros(0))
+    with pytest.raises(hfx.HFXError) as ei:
+        hfx.Basis(empty)
+    assert ei.value.status == 1
+
+
 def test_errors_are_reported():
     from paper_2009_03555_gb300 import hfx
     s = synth.ch_cluster(2, 5)
