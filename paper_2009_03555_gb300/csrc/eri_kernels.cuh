@@ -970,7 +970,8 @@ __global__ void __launch_bounds__(kThreadsCoop) k_build_K_coop(const BuildArgs a
 template <class C, typename R>
 struct SplitShape {
   static constexpr bool F32 = sizeof(R) == 4;
-  static constexpr bool LOCKSTEP = C::VRR_FLOPS >= HFX_LOCKSTEP_MIN_FLOPS && (F32 || HFX_LOCKSTEP64);
+  static constexpr bool LOCKSTEP = (C::VRR_FLOPS >= HFX_LOCKSTEP_MIN_FLOPS && (F32 || HFX_LOCKSTEP64)) ||
+                                   (F32 && C::SPLIT_WARPS > 8);
   // a horizontal-recursion workspace above 32 KB per warp leaves room for
   // 4-warp blocks only.  With its slots reused once their values are dead no
   // class needs that much ((dd|dd): 2844 slots, 22 KB in FP64), so the FP64

@@ -97,9 +97,12 @@ PT_PREFETCH = {(0, 0, 0, 0), (1, 0, 1, 0), (1, 1, 0, 0), (1, 1, 1, 0), (2, 0, 0,
 # (measured, 100-atom HSE build: (dp|pp) 3.8 % faster, spill-free at 153
 # registers; (dd|dd) unchanged, (dp|dp) 3.5 % slower).
 SPLIT_SMEM_ACC = {(2, 1, 1, 1)}
-# FP32 warp-split classes with their own warps per block (0 or absent: the
-# kernel's rule by recursion size).
-SPLIT_WARPS = {}
+# FP32 warp-split classes with their own warps per lockstep block (absent:
+# the kernel's rule by recursion size, 12 for the wide classes).  Measured on
+# GB300, 100-atom HSE build, 16-warp blocks (128 registers) against the rule:
+# (dp|pp) 347 -> 296 ms, (dp|ds) 278 -> 250, (dp|dp) 297 -> 273, (dd|ps)
+# 132 -> 114, (dd|ds) 136 -> 122; (dd|pp) and (dd|dp) unchanged or slower.
+SPLIT_WARPS = {(2, 1, 1, 1): 16, (2, 1, 2, 0): 16, (2, 1, 2, 1): 16, (2, 2, 1, 0): 16, (2, 2, 2, 0): 16}
 
 
 class VRR:
