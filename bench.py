@@ -38,28 +38,28 @@ import synth  # noqa: E402
 # has no entry (traffic null).
 DRAM_BYTES_PER_PRIM_QUARTET = {
     # profiles/dram_build_K_50atom.md: one warm-up build of the 50-atom cluster
-    "k_build_K<Cls0000, float>": 0.05352,
-    "k_build_K<Cls1000, float>": 0.03638,
-    "k_build_K<Cls1010, float>": 0.02615,
-    "k_build_K<Cls1100, float>": 0.03996,
-    "k_build_K<Cls1110, float>": 0.0249,
-    "k_build_K<Cls1111, float>": 0.1061,
-    "k_build_K<Cls2000, float>": 0.04965,
-    "k_build_K<Cls2010, float>": 0.03119,
-    "k_build_K<Cls2011, float>": 0.03759,
-    "k_build_K<Cls2020, float>": 0.06206,
-    "k_build_K<Cls2100, float>": 0.04702,
-    "k_build_K<Cls2110, float>": 0.04505,
-    "k_build_K_split<Cls2111, float>": 0.03736,
-    "k_build_K_split<Cls2120, float>": 0.04436,
-    "k_build_K_split<Cls2121, float>": 0.05583,
-    "k_build_K<Cls2200, float>": 0.09199,
-    "k_build_K_split<Cls2210, float>": 0.06642,
-    "k_build_K_split<Cls2211, float>": 0.07927,
-    "k_build_K_split<Cls2220, float>": 0.09086,
-    "k_build_K_split<Cls2221, float>": 0.08598,
-    "k_build_K_split<Cls2222, float>": 8.983,
-    "k_build_K_split<Cls2222, double>": 1304,
+    "k_build_K<Cls0000, float>": 0.05342,
+    "k_build_K<Cls1000, float>": 0.03609,
+    "k_build_K<Cls1010, float>": 0.02604,
+    "k_build_K<Cls1100, float>": 0.03824,
+    "k_build_K<Cls1110, float>": 0.02461,
+    "k_build_K<Cls1111, float>": 0.1059,
+    "k_build_K<Cls2000, float>": 0.05024,
+    "k_build_K<Cls2010, float>": 0.03031,
+    "k_build_K<Cls2011, float>": 0.03828,
+    "k_build_K<Cls2020, float>": 0.06374,
+    "k_build_K<Cls2100, float>": 0.046,
+    "k_build_K<Cls2110, float>": 0.04523,
+    "k_build_K_split<Cls2111, float>": 0.03641,
+    "k_build_K_split<Cls2120, float>": 0.04537,
+    "k_build_K_split<Cls2121, float>": 0.06032,
+    "k_build_K<Cls2200, float>": 0.09295,
+    "k_build_K_split<Cls2210, float>": 0.0679,
+    "k_build_K_split<Cls2211, float>": 0.0767,
+    "k_build_K_split<Cls2220, float>": 0.09629,
+    "k_build_K_split<Cls2221, float>": 0.08678,
+    "k_build_K_split<Cls2222, float>": 8.583,
+    "k_build_K_split<Cls2222, double>": 1259,
 }
 
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 80.5: 128 FP32 FMA/clk/SM at the 2070 MHz max clock
