@@ -928,10 +928,12 @@ __global__ void __launch_bounds__(kThreadsCoop) k_build_K_coop(const BuildArgs a
 // (or the epilogue of a finished quartet, or finds its next quartet), then the
 // block meets at a barrier.  The passes of one round start together and run
 // the same code, so one instruction stream serves the whole block.  Shapes
-// (measured on GB300, 100-atom HSE build): the longest recursions run one
-// 8-warp block per SM (they need 255 registers anyway); shorter ones run
-// three 4-warp blocks per SM at <= 168 registers, in lockstep from
-// HFX_LOCKSTEP_MIN_FLOPS recursion flops up.
+// (measured on GB300, 100-atom HSE build; SplitShape): in FP32 one 12- or
+// 16-warp lockstep block per SM, the chunk accumulators in shared memory so
+// that the recursion fits 168 or 128 registers; the FP32 (dd|dd) pass and the
+// FP64 kernels one 8-warp block at 255 registers; recursions below
+// HFX_LOCKSTEP_MIN_FLOPS flops without a class setting of their own, three
+// independent 4-warp blocks per SM at <= 168 registers.
 #ifndef HFX_LOCKSTEP_MIN_FLOPS
 #define HFX_LOCKSTEP_MIN_FLOPS 1400
 #endif
