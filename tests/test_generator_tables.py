@@ -180,3 +180,23 @@ def test_vrr_tables(cls):
     v = g.VRR(la, lb, lc, ld)
     ref = np.array([r(e, f, 0) for e in v.E for f in v.F])
     np.testing.assert_allclose(got, ref, rtol=1e-10, atol=1e-12 * np.abs(ref).max())
+
+
+def test_per_class_settings_name_classes_of_the_right_kernel():
+    """The generator's per-class tables name real classes of the kernel they
+    configure: launch bounds and ket prefetch only per-thread classes (fewer
+    than SPLIT_MIN_ACC contracted accumulators), warps per block and
+    shared-memory accumulators only warp-split classes, with 12 or 16 warps."""
+    g = _gen()
+    classes = {tuple(c) for c in _classes()}
+    assert len(classes) == 21
+
+    def nacc(c):
+        v = g.VRR(*c)
+        return len(v.E) * len(v.F)
+
+    for c in list(g.PT_MIN_BLOCKS) + list(g.PT_PREFETCH):
+        assert c in classes and nacc(c) < g.SPLIT_MIN_ACC, c
+    for c in list(g.SPLIT_WARPS) + list(g.SPLIT_SMEM_ACC):
+        assert c in classes and nacc(c) >= g.SPLIT_MIN_ACC, c
+    assert set(g.SPLIT_WARPS.values()) <= {12, 16}
